@@ -1,0 +1,174 @@
+/*
+ * crsolve.h -- C ABI of a GB300 (sm_103a) solver for Hermitian positive
+ * definite block-tridiagonal linear systems by classic cyclic reduction.
+ *
+ * The system (Sec. 1, eq. Axb and eq. Data):
+ *     [ A_1  B_1^H                ] [x_1]   [y_1]
+ *     [ B_1  A_2   B_2^H          ] [x_2] = [y_2]
+ *     [      ...   ...    ...     ] [...]   [...]
+ *     [            B_{N-1} A_N    ] [x_N]   [y_N]
+ * with A_j, B_j complex m x m and x_j, y_j complex m x k.  The method reduces
+ * the even-indexed half by the block formulas of Sec. 2 (eq. Formulas, with
+ * the boundary auxiliaries B_0 = B_N = 0, A_0 = A_{N+1} = I), forms every
+ * Hermitian product through a Cholesky factor as Sec. 4 prescribes, recurses
+ * until one block is left (solved by Cholesky), and recovers the odd unknowns
+ * by back-substitution from the odd block rows of eq. Axb.  A Cholesky pivot
+ * that is not > 0 reports the matrix as not positive definite (Sec. 2,
+ * "Determination of Positive Definiteness").
+ *
+ * Conventions shared by every entry point
+ *   - Element type crsolve_z: interleaved complex double, 16 bytes, the same
+ *     bytes as torch.complex128, numpy complex128 and cuDoubleComplex.
+ *   - Layouts, all row-major and contiguous:
+ *       A [N][m][m]   only the lower triangle of each A_j is read, and only
+ *                     the real part of its diagonal;
+ *       B [N-1][m][m] B_j sits at block position (j+1, j);
+ *       y, x [N][m][k].
+ *   - Device pointers must be 16-byte aligned device memory of the current
+ *     device.  The library never retains A, B or y beyond the stream work
+ *     that a call enqueues.
+ *   - Every call is asynchronous on the given CUDA stream (NULL = legacy
+ *     default stream) unless stated otherwise.  Argument errors are found on
+ *     the host, return a negative code and enqueue nothing.
+ *   - Breakdown (not positive definite) is found on the device; it is read
+ *     back by crsolve_info_get.  After a breakdown, crsolve_solve and
+ *     crsolve_backward write NaN into x / gy.
+ *   - Device memory: the library allocates none for the plan.  The caller
+ *     asks for the workspace size, allocates it (e.g. a torch tensor) and
+ *     binds it; the plan owns its contents until crsolve_destroy.
+ */
+#ifndef CRSOLVE_H
+#define CRSOLVE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct { double re, im; } crsolve_z;
+typedef struct crsolve_plan_s *crsolve_plan;
+
+enum crsolve_status {
+    CRSOLVE_OK = 0,
+    CRSOLVE_NOT_PD = 1,          /* a Cholesky pivot was not > 0 (or NaN) */
+    CRSOLVE_EINVAL = -1,         /* bad argument: size, null or misaligned pointer */
+    CRSOLVE_ENOMEM = -2,         /* workspace missing or too small */
+    CRSOLVE_ECUDA = -3,          /* a CUDA runtime call failed */
+    CRSOLVE_ETIMEOUT = -4,       /* a bounded device-side wait gave up */
+    CRSOLVE_ENOTFACTORED = -5,   /* solve/backward before a factor */
+    CRSOLVE_EUNSUPPORTED = -6    /* m or k outside the supported range */
+};
+
+enum crsolve_precision {
+    CRSOLVE_FP64 = 0,            /* every step in FP64 */
+    CRSOLVE_MIXED = 1            /* FP32 factor + FP64 residual and refinement */
+};
+
+/* plan flags */
+#define CRSOLVE_PLAN_HOST_STAGING 1u  /* workspace also holds device copies of A, B, y, x
+                                         for crsolve_solve_host */
+
+/* Largest block size m and right-hand-side width k the kernels accept. */
+#define CRSOLVE_MAX_M 64
+#define CRSOLVE_MAX_K 4096
+
+typedef struct {
+    int32_t status;     /* CRSOLVE_OK or CRSOLVE_NOT_PD */
+    int32_t level;      /* 0-based reduction level of the first breakdown */
+    int64_t block;      /* 1-based block index within that level */
+    int64_t orig_block; /* 1-based index of that block in the original system
+                           (block * 2^level: even block 2j at one level is block
+                           j at the next) */
+} crsolve_info;
+
+/*
+ * crsolve_plan_create -- describe one system shape (host only, no CUDA call).
+ *   N >= 1 blocks of size 1 <= m <= CRSOLVE_MAX_M; right-hand sides of width
+ *   up to kmax (1 <= kmax <= CRSOLVE_MAX_K); precision from crsolve_precision;
+ *   flags from CRSOLVE_PLAN_*.  The plan is tied to the current device.
+ * Returns CRSOLVE_OK, CRSOLVE_EINVAL or CRSOLVE_EUNSUPPORTED.
+ */
+int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision,
+                        uint32_t flags, crsolve_plan *out_plan);
+
+/* Bytes of device workspace the plan needs (per-level factors, the reduced
+ * systems, scratch and, with CRSOLVE_PLAN_HOST_STAGING, input/output copies). */
+int crsolve_workspace_bytes(crsolve_plan p, size_t *bytes);
+
+/* Bind caller-owned device memory (256-byte aligned, >= crsolve_workspace_bytes)
+ * to the plan.  The caller frees it after crsolve_destroy. */
+int crsolve_set_workspace(crsolve_plan p, void *dev_ptr, size_t bytes);
+
+/*
+ * crsolve_factor -- the reduction sweep of Sec. 2 on device data.
+ *   A [N][m][m], B [N-1][m][m] (B may be NULL iff N == 1).  For every level it
+ *   factors the odd diagonal blocks (Cholesky with breakdown test), forms
+ *   P_i = L_i^{-1} B_{i-1}, Q_i = L_i^{-1} B_i^H and the half-size even system
+ *   V_j = A_{2j} - Q_{2j-1}^H Q_{2j-1} - P_{2j+1}^H P_{2j+1},
+ *   F_j = -Q_{2j+1}^H P_{2j+1} (eq. Formulas with the Sec. 4 product rule),
+ *   and keeps L, P, Q of every level in the workspace for later solves.
+ * Returns CRSOLVE_OK once enqueued; breakdown is reported by crsolve_info_get.
+ */
+int crsolve_factor(crsolve_plan p, const crsolve_z *A, const crsolve_z *B, void *stream);
+
+/*
+ * crsolve_solve -- x = A^{-1} y with the stored factorisation.
+ *   y, x [N][m][k] device, 1 <= k <= kmax, x must not alias y.  Down sweep:
+ *   r_i = L_i^{-1} y_i, v_j = y_{2j} - Q_{2j-1}^H r_{2j-1} - P_{2j+1}^H r_{2j+1}
+ *   (eq. Formulas); up sweep: x_i = L_i^{-H}(r_i - P_i x_{i-1} - Q_i x_{i+1}).
+ * Returns CRSOLVE_ENOTFACTORED before the first crsolve_factor.
+ */
+int crsolve_solve(crsolve_plan p, int32_t k, const crsolve_z *y, crsolve_z *x, void *stream);
+
+/*
+ * crsolve_backward -- adjoint of x = A^{-1} y for a real loss L.
+ *   Given x (the solve's result) and gx = dL/dx (PyTorch's complex gradient
+ *   convention, dL/dRe + i dL/dIm), writes
+ *     gy  = A^{-1} gx   (a re-solve with the stored factors; A is Hermitian),
+ *     gA_j = -1/2 (gy_j x_j^H + x_j gy_j^H)   (projected onto Hermitian
+ *            matrices: the gradient for Hermitian perturbations of A_j),
+ *     gB_j = -(gy_{j+1} x_j^H + x_{j+1} gy_j^H)   (B_j enters at (j+1,j) and
+ *            as B_j^H at (j,j+1)).
+ *   gA [N][m][m] and gB [N-1][m][m] may be NULL.  The paper has no adjoint;
+ *   these are the derivatives of the system of eq. Axb.
+ */
+int crsolve_backward(crsolve_plan p, int32_t k, const crsolve_z *x, const crsolve_z *gx,
+                     crsolve_z *gy, crsolve_z *gA, crsolve_z *gB, void *stream);
+
+/*
+ * crsolve_solve_host -- factor and solve with HOST buffers: copies A, B, y
+ * from host memory (pinned for full speed) into the plan's staging area,
+ * factors, solves, copies x back to host memory and synchronises the stream.
+ * Needs a plan created with CRSOLVE_PLAN_HOST_STAGING.  Returns CRSOLVE_OK or
+ * CRSOLVE_NOT_PD (then x holds NaN), or a negative error.
+ */
+int crsolve_solve_host(crsolve_plan p, int32_t k, const crsolve_z *A_host,
+                       const crsolve_z *B_host, const crsolve_z *y_host, crsolve_z *x_host,
+                       void *stream);
+
+/* Synchronises the stream and reports the factorisation's breakdown status. */
+int crsolve_info_get(crsolve_plan p, crsolve_info *out, void *stream);
+
+/* Frees the host-side plan (not the caller's workspace). */
+int crsolve_destroy(crsolve_plan p);
+
+/* Static description of a status code. */
+const char *crsolve_strerror(int code);
+
+/* Number of levels of the plan (floor(log2 N) + 1) and the level sizes. */
+int crsolve_plan_levels(crsolve_plan p, int32_t *nlev, int64_t *sizes /* [nlev] or NULL */);
+
+/*
+ * crsolve_debug_level_system -- device pointers of the reduced system
+ * (A^(l), B^(l)) of level l >= 1 inside the bound workspace, for tests that
+ * compare each level with the oracle.  Valid after crsolve_factor.
+ */
+int crsolve_debug_level_system(crsolve_plan p, int32_t level, const crsolve_z **A_l,
+                               const crsolve_z **B_l);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CRSOLVE_H */

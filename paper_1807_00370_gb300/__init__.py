@@ -1,0 +1,17 @@
+"""GB300-native (sm_103a) cyclic-reduction solver for Hermitian positive
+definite block-tridiagonal systems (Neuenhofen, "Review of Cyclic Reduction
+for Parallel Solution of Hermitian Positive Definite Block-Tridiagonal
+Linear Systems").
+
+The CUDA library libcrsolve.so (C ABI in include/crsolve.h) does all the
+work; ``api`` is a thin ctypes binding with the same names.  Importing this
+package does not load the library; the first call does, and fails loudly if
+it cannot.
+"""
+from .api import (CRSolveFn, NotPositiveDefinite, Plan, crsolve_backward, crsolve_debug_level_system,
+                  crsolve_factor, crsolve_info_get, crsolve_plan_create, crsolve_plan_levels,
+                  crsolve_solve, crsolve_solve_host, solve)
+
+__all__ = ["CRSolveFn", "NotPositiveDefinite", "Plan", "crsolve_backward", "crsolve_debug_level_system",
+           "crsolve_factor", "crsolve_info_get", "crsolve_plan_create", "crsolve_plan_levels",
+           "crsolve_solve", "crsolve_solve_host", "solve"]

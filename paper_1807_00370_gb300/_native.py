@@ -1,0 +1,97 @@
+"""ctypes loader for libcrsolve.so (the C ABI of include/crsolve.h).
+
+There is no fallback: if the library is missing or cannot be loaded, every
+entry point raises.  Argument marshalling only; all arithmetic runs in the
+library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+_lock = threading.Lock()
+_lib = None
+
+CRSOLVE_OK = 0
+CRSOLVE_NOT_PD = 1
+CRSOLVE_EINVAL = -1
+CRSOLVE_ENOMEM = -2
+CRSOLVE_ECUDA = -3
+CRSOLVE_ETIMEOUT = -4
+CRSOLVE_ENOTFACTORED = -5
+CRSOLVE_EUNSUPPORTED = -6
+CRSOLVE_FP64 = 0
+CRSOLVE_MIXED = 1
+CRSOLVE_PLAN_HOST_STAGING = 1
+CRSOLVE_MAX_M = 64
+CRSOLVE_MAX_K = 4096
+
+# every symbol include/crsolve.h declares: name -> (restype, argtypes)
+_P = ctypes.c_void_p
+_I64, _I32, _U32, _SZ = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_size_t
+
+
+class CrsolveInfo(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("level", ctypes.c_int32),
+                ("block", ctypes.c_int64), ("orig_block", ctypes.c_int64)]
+
+
+SIGNATURES = {
+    "crsolve_plan_create": (ctypes.c_int, [_I64, _I32, _I32, _I32, _U32, ctypes.POINTER(_P)]),
+    "crsolve_workspace_bytes": (ctypes.c_int, [_P, ctypes.POINTER(_SZ)]),
+    "crsolve_set_workspace": (ctypes.c_int, [_P, _P, _SZ]),
+    "crsolve_factor": (ctypes.c_int, [_P, _P, _P, _P]),
+    "crsolve_solve": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
+    "crsolve_backward": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _P, _P]),
+    "crsolve_solve_host": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _P]),
+    "crsolve_info_get": (ctypes.c_int, [_P, ctypes.POINTER(CrsolveInfo), _P]),
+    "crsolve_destroy": (ctypes.c_int, [_P]),
+    "crsolve_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "crsolve_plan_levels": (ctypes.c_int, [_P, ctypes.POINTER(_I32), _P]),
+    "crsolve_debug_level_system": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+}
+
+
+class CrsolveError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} (code {code})")
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libcrsolve.so (building it first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing and _build.is_stale():
+            _build.build()
+        if not os.path.exists(_build.LIB):
+            raise RuntimeError(f"libcrsolve.so not built ({_build.LIB}); run paper_1807_00370_gb300.build.build()")
+        lib = ctypes.CDLL(_build.LIB)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().crsolve_strerror(int(code)).decode()
+    except Exception:  # noqa: BLE001 - error text only
+        return "unknown"
+
+
+def check(code: int, where: str) -> int:
+    if code < 0:
+        raise CrsolveError(code, where)
+    return code

@@ -1,0 +1,220 @@
+"""Python binding of the C ABI (include/crsolve.h), same names as the C calls.
+
+PyTorch provides device memory (the plan's workspace and the result tensors)
+and streams; every step of the solver runs in libcrsolve's CUDA kernels.
+Tensors are complex128 and contiguous:
+  A [N, m, m] (lower triangle read), B [N-1, m, m], y and x [N, m, k].
+"""
+from __future__ import annotations
+
+import ctypes
+
+import torch
+
+from . import _native as nat
+
+__all__ = ["Plan", "crsolve_plan_create", "crsolve_factor", "crsolve_solve", "crsolve_backward",
+           "crsolve_info_get", "crsolve_solve_host", "crsolve_plan_levels",
+           "crsolve_debug_level_system", "solve", "CRSolveFn", "NotPositiveDefinite"]
+
+
+class NotPositiveDefinite(RuntimeError):
+    """Raised by the high-level helpers when a Cholesky pivot failed."""
+
+    def __init__(self, info):
+        self.info = info
+        super().__init__(f"matrix is not positive definite: first breakdown at level {info['level']}, "
+                         f"block {info['block']} (original block {info['orig_block']})")
+
+
+def _vp(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need(t, shape, name, device=None, cpu=False):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if t.dtype != torch.complex128:
+        raise TypeError(f"{name} must be complex128, got {t.dtype}")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if cpu:
+        if t.device.type != "cpu":
+            raise ValueError(f"{name} must be a host tensor")
+    elif t.device.type != "cuda" or (device is not None and t.device != device):
+        raise ValueError(f"{name} must live on {device or 'a CUDA device'}")
+
+
+class Plan:
+    """One system shape (N blocks of m x m, right-hand sides up to kmax wide)
+    with its device workspace (a torch uint8 tensor owned by this object)."""
+
+    def __init__(self, N: int, m: int, kmax: int, precision: int = nat.CRSOLVE_FP64,
+                 flags: int = 0, device=None):
+        lib = nat.load()
+        if not torch.cuda.is_available():
+            raise RuntimeError("crsolve needs a CUDA device")
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None
+                                   else torch.device(device).index or 0)
+        self.N, self.m, self.kmax, self.precision, self.flags = int(N), int(m), int(kmax), int(precision), int(flags)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            nat.check(lib.crsolve_plan_create(self.N, self.m, self.kmax, self.precision, self.flags,
+                                              ctypes.byref(self._h)), "crsolve_plan_create")
+            nbytes = ctypes.c_size_t()
+            nat.check(lib.crsolve_workspace_bytes(self._h, ctypes.byref(nbytes)), "crsolve_workspace_bytes")
+            self.workspace_bytes = int(nbytes.value)
+            self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
+            nat.check(lib.crsolve_set_workspace(self._h, _vp(self.workspace), self.workspace.numel()),
+                      "crsolve_set_workspace")
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            nat.load().crsolve_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:  # noqa: BLE001 - interpreter shutdown
+            pass
+
+
+def crsolve_plan_create(N, m, kmax, precision=nat.CRSOLVE_FP64, flags=0, device=None) -> Plan:
+    return Plan(N, m, kmax, precision, flags, device)
+
+
+def crsolve_factor(plan: Plan, A: torch.Tensor, B: torch.Tensor | None, stream=None) -> None:
+    N, m = plan.N, plan.m
+    _need(A, (N, m, m), "A", plan.device)
+    if N > 1:
+        _need(B, (N - 1, m, m), "B", plan.device)
+    with torch.cuda.device(plan.device):
+        nat.check(nat.load().crsolve_factor(plan.handle, _vp(A), _vp(B) if N > 1 else None, _stream(stream)),
+                  "crsolve_factor")
+
+
+def crsolve_solve(plan: Plan, y: torch.Tensor, x: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    N, m = plan.N, plan.m
+    k = y.shape[-1] if y.dim() == 3 else -1
+    _need(y, (N, m, k), "y", plan.device)
+    if x is None:
+        x = torch.empty_like(y)
+    _need(x, (N, m, k), "x", plan.device)
+    with torch.cuda.device(plan.device):
+        nat.check(nat.load().crsolve_solve(plan.handle, k, _vp(y), _vp(x), _stream(stream)), "crsolve_solve")
+    return x
+
+
+def crsolve_backward(plan: Plan, x: torch.Tensor, gx: torch.Tensor, want_gA: bool = True,
+                     want_gB: bool = True, stream=None):
+    N, m = plan.N, plan.m
+    k = x.shape[-1]
+    _need(x, (N, m, k), "x", plan.device)
+    _need(gx, (N, m, k), "gx", plan.device)
+    gy = torch.empty_like(gx)
+    gA = torch.empty((N, m, m), dtype=torch.complex128, device=plan.device) if want_gA else None
+    gB = torch.empty((N - 1, m, m), dtype=torch.complex128, device=plan.device) if (want_gB and N > 1) else None
+    with torch.cuda.device(plan.device):
+        nat.check(nat.load().crsolve_backward(plan.handle, k, _vp(x), _vp(gx), _vp(gy), _vp(gA), _vp(gB),
+                                              _stream(stream)), "crsolve_backward")
+    return gy, gA, gB
+
+
+def crsolve_info_get(plan: Plan, stream=None) -> dict:
+    info = nat.CrsolveInfo()
+    with torch.cuda.device(plan.device):
+        nat.check(nat.load().crsolve_info_get(plan.handle, ctypes.byref(info), _stream(stream)),
+                  "crsolve_info_get")
+    return {"status": info.status, "level": info.level, "block": info.block, "orig_block": info.orig_block}
+
+
+def crsolve_solve_host(plan: Plan, A: torch.Tensor, B: torch.Tensor | None, y: torch.Tensor,
+                       x: torch.Tensor | None = None, stream=None):
+    """Host tensors in and out (pinned for full copy speed).  Returns (x, status)."""
+    N, m = plan.N, plan.m
+    k = y.shape[-1]
+    _need(A, (N, m, m), "A", cpu=True)
+    if N > 1:
+        _need(B, (N - 1, m, m), "B", cpu=True)
+    _need(y, (N, m, k), "y", cpu=True)
+    if x is None:
+        x = torch.empty_like(y, pin_memory=y.is_pinned())
+    _need(x, (N, m, k), "x", cpu=True)
+    with torch.cuda.device(plan.device):
+        rc = nat.check(nat.load().crsolve_solve_host(plan.handle, k, _vp(A), _vp(B) if N > 1 else None,
+                                                     _vp(y), _vp(x), _stream(stream)), "crsolve_solve_host")
+    return x, rc
+
+
+def crsolve_plan_levels(plan: Plan):
+    lib = nat.load()
+    n = ctypes.c_int32()
+    nat.check(lib.crsolve_plan_levels(plan.handle, ctypes.byref(n), None), "crsolve_plan_levels")
+    sizes = (ctypes.c_int64 * n.value)()
+    nat.check(lib.crsolve_plan_levels(plan.handle, ctypes.byref(n), sizes), "crsolve_plan_levels")
+    return [int(s) for s in sizes]
+
+
+def crsolve_debug_level_system(plan: Plan, level: int):
+    """Copies of the reduced system (A^(l), B^(l)) of a level >= 1 (tests only)."""
+    pa, pb = ctypes.c_void_p(), ctypes.c_void_p()
+    nat.check(nat.load().crsolve_debug_level_system(plan.handle, int(level), ctypes.byref(pa), ctypes.byref(pb)),
+              "crsolve_debug_level_system")
+    sizes = crsolve_plan_levels(plan)
+    Nl, m = sizes[level], plan.m
+    base = plan.workspace.data_ptr()
+    ws = plan.workspace.view(torch.uint8)
+    a0, b0 = pa.value - base, pb.value - base
+    A = ws[a0:a0 + Nl * m * m * 16].view(torch.complex128).reshape(Nl, m, m).clone()
+    B = ws[b0:b0 + max(Nl - 1, 0) * m * m * 16].view(torch.complex128).reshape(max(Nl - 1, 0), m, m).clone()
+    return A, B
+
+
+def solve(A: torch.Tensor, B: torch.Tensor | None, y: torch.Tensor, check: bool = True) -> torch.Tensor:
+    """x = A^{-1} y for one system on the tensors' CUDA device."""
+    N, m, _ = A.shape
+    plan = Plan(N, m, y.shape[-1], device=A.device)
+    crsolve_factor(plan, A, B)
+    x = crsolve_solve(plan, y)
+    if check:
+        info = crsolve_info_get(plan)
+        if info["status"] != 0:
+            raise NotPositiveDefinite(info)
+    return x
+
+
+class CRSolveFn(torch.autograd.Function):
+    """x = A^{-1} y with the cyclic-reduction solver; backward by
+    crsolve_backward (a Hermitian re-solve with the stored factors and fused
+    outer products).  A_j is treated as Hermitian: its gradient is projected
+    onto Hermitian matrices."""
+
+    @staticmethod
+    def forward(ctx, A, B, y):
+        N, m, _ = A.shape
+        plan = Plan(N, m, y.shape[-1], device=A.device)
+        crsolve_factor(plan, A.contiguous(), None if B is None else B.contiguous())
+        x = crsolve_solve(plan, y.contiguous())
+        ctx.plan = plan
+        ctx.save_for_backward(x)
+        ctx.has_B = B is not None
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        (x,) = ctx.saved_tensors
+        gy, gA, gB = crsolve_backward(ctx.plan, x, gx.contiguous(), ctx.needs_input_grad[0],
+                                      ctx.needs_input_grad[1] and ctx.has_B)
+        return gA, gB, gy if ctx.needs_input_grad[2] else None

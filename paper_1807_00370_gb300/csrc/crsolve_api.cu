@@ -1,0 +1,324 @@
+// crsolve_api.cu -- the C ABI declared in include/crsolve.h: plans, the
+// workspace layout, and the level schedule of classic cyclic reduction.
+//
+// Level schedule: N_0 = N, N_{l+1} = floor(N_l / 2), down to N_L = 1.  Level l
+// has ceil(N_l/2) odd blocks (factored and eliminated) and floor(N_l/2) even
+// blocks (the next level).  Every block row of the original system is an odd
+// block at exactly one level, so the factorisation does N block Cholesky
+// factorisations in total.
+#include <cstdint>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "crsolve.h"
+#include "cr_launch.h"
+
+using crs::z2;
+
+namespace {
+
+struct LevelPlan {
+    int64_t Nl, no, ne;
+    size_t offL, offInv, offZ;       // stored factor of the odd blocks
+    size_t offAn, offBn;             // next level system (l + 1)
+    size_t offR, offYn, offXn;       // solve: r of this level, y and x of level l + 1
+};
+
+}  // namespace
+
+struct crsolve_plan_s {
+    int64_t N = 0;
+    int m = 0, kmax = 0, precision = 0, mt = 0, device = 0, nsm = 0;
+    uint32_t flags = 0;
+    std::vector<LevelPlan> lev;
+    size_t offStatus = 0, offWl = 0, offWr = 0, offCl = 0, offCr = 0;
+    size_t offSA = 0, offSB = 0, offSY = 0, offSX = 0;
+    size_t total = 0;
+    char *ws = nullptr;
+    size_t ws_bytes = 0;
+    bool factored = false;
+    bool prepared = false;
+};
+
+namespace {
+
+size_t take(size_t &cursor, size_t bytes) {
+    const size_t off = cursor;
+    cursor += (bytes + 255) & ~(size_t)255;
+    return off;
+}
+
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
+crs::LevelArgs level_args(const crsolve_plan_s *p, int l, const z2 *A0, const z2 *B0) {
+    const LevelPlan &L = p->lev[l];
+    crs::LevelArgs a{};
+    a.Nl = L.Nl; a.no = L.no; a.ne = L.ne;
+    a.m = p->m; a.level = l;
+    char *ws = p->ws;
+    a.A = (l == 0) ? A0 : reinterpret_cast<const z2 *>(ws + p->lev[l - 1].offAn);
+    a.B = (l == 0) ? B0 : reinterpret_cast<const z2 *>(ws + p->lev[l - 1].offBn);
+    a.L = reinterpret_cast<z2 *>(ws + L.offL);
+    a.inv = reinterpret_cast<double *>(ws + L.offInv);
+    a.Z = reinterpret_cast<z2 *>(ws + L.offZ);
+    a.Wl = reinterpret_cast<z2 *>(ws + p->offWl);
+    a.Wr = reinterpret_cast<z2 *>(ws + p->offWr);
+    a.An = reinterpret_cast<z2 *>(ws + L.offAn);
+    a.Bn = reinterpret_cast<z2 *>(ws + L.offBn);
+    a.r = reinterpret_cast<z2 *>(ws + L.offR);
+    a.cl = reinterpret_cast<z2 *>(ws + p->offCl);
+    a.cr = reinterpret_cast<z2 *>(ws + p->offCr);
+    a.yn = reinterpret_cast<z2 *>(ws + L.offYn);
+    a.xn = reinterpret_cast<const z2 *>(ws + L.offXn);
+    a.status = reinterpret_cast<unsigned long long *>(ws + p->offStatus);
+    return a;
+}
+
+int ensure_prepared(crsolve_plan_s *p) {
+    if (p->prepared) return CRSOLVE_OK;
+    if (crs::prepare_kernels(p->mt) != cudaSuccess) return CRSOLVE_ECUDA;
+    p->prepared = true;
+    return CRSOLVE_OK;
+}
+
+int check_device(const crsolve_plan_s *p) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CRSOLVE_ECUDA;
+    return dev == p->device ? CRSOLVE_OK : CRSOLVE_EINVAL;
+}
+
+int do_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
+    if (cudaMemsetAsync(p->ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    for (int l = 0; l < (int)p->lev.size(); ++l) {
+        crs::LevelArgs a = level_args(p, l, A, B);
+        if (crs::launch_factor_level(p->mt, a, p->nsm, s) != cudaSuccess) return CRSOLVE_ECUDA;
+    }
+    p->factored = true;
+    return CRSOLVE_OK;
+}
+
+int do_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
+    const int nlev = (int)p->lev.size();
+    for (int l = 0; l < nlev; ++l) {
+        crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
+        a.k = k;
+        a.y = (l == 0) ? y : reinterpret_cast<const z2 *>(p->ws + p->lev[l - 1].offYn);
+        if (crs::launch_solve_down_level(p->mt, a, p->nsm, s) != cudaSuccess) return CRSOLVE_ECUDA;
+    }
+    for (int l = nlev - 1; l >= 0; --l) {
+        crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
+        a.k = k;
+        a.x = (l == 0) ? x : reinterpret_cast<z2 *>(p->ws + p->lev[l - 1].offXn);
+        if (crs::launch_solve_up_level(p->mt, a, p->nsm, s) != cudaSuccess) return CRSOLVE_ECUDA;
+    }
+    return CRSOLVE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, uint32_t flags,
+                        crsolve_plan *out_plan) {
+    if (!out_plan) return CRSOLVE_EINVAL;
+    *out_plan = nullptr;
+    if (N < 1 || m < 1 || kmax < 1) return CRSOLVE_EINVAL;
+    if (m > CRSOLVE_MAX_M || kmax > CRSOLVE_MAX_K) return CRSOLVE_EUNSUPPORTED;
+    if (precision != CRSOLVE_FP64) return CRSOLVE_EUNSUPPORTED;
+    if (flags & ~(uint32_t)CRSOLVE_PLAN_HOST_STAGING) return CRSOLVE_EINVAL;
+    crsolve_plan_s *p = new (std::nothrow) crsolve_plan_s();
+    if (!p) return CRSOLVE_ENOMEM;
+    p->N = N; p->m = m; p->kmax = kmax; p->precision = precision; p->flags = flags;
+    p->mt = crs::pick_mt(m);
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+        delete p;
+        return CRSOLVE_ECUDA;
+    }
+    const size_t zsz = sizeof(crsolve_z), mm = (size_t)m * m, mk = (size_t)m * kmax;
+    size_t cur = 0;
+    p->offStatus = take(cur, 256);
+    int64_t Nl = N;
+    while (true) {
+        LevelPlan L{};
+        L.Nl = Nl; L.no = (Nl + 1) / 2; L.ne = Nl / 2;
+        L.offL = take(cur, L.no * mm * zsz);
+        L.offInv = take(cur, L.no * (size_t)m * sizeof(double));
+        L.offZ = take(cur, L.no * 2 * mm * zsz);
+        L.offR = take(cur, L.no * mk * zsz);
+        L.offAn = take(cur, L.ne * mm * zsz);
+        L.offBn = take(cur, (L.ne > 1 ? L.ne - 1 : 0) * mm * zsz);
+        L.offYn = take(cur, L.ne * mk * zsz);
+        L.offXn = take(cur, L.ne * mk * zsz);
+        p->lev.push_back(L);
+        if (Nl == 1) break;
+        Nl /= 2;
+    }
+    const int64_t no0 = (N + 1) / 2;
+    p->offWl = take(cur, no0 * mm * zsz);
+    p->offWr = take(cur, no0 * mm * zsz);
+    p->offCl = take(cur, no0 * mk * zsz);
+    p->offCr = take(cur, no0 * mk * zsz);
+    if (flags & CRSOLVE_PLAN_HOST_STAGING) {
+        p->offSA = take(cur, N * mm * zsz);
+        p->offSB = take(cur, (N - 1) * mm * zsz);
+        p->offSY = take(cur, N * mk * zsz);
+        p->offSX = take(cur, N * mk * zsz);
+    }
+    p->total = cur;
+    *out_plan = p;
+    return CRSOLVE_OK;
+}
+
+int crsolve_workspace_bytes(crsolve_plan p, size_t *bytes) {
+    if (!p || !bytes) return CRSOLVE_EINVAL;
+    *bytes = p->total;
+    return CRSOLVE_OK;
+}
+
+int crsolve_set_workspace(crsolve_plan p, void *dev_ptr, size_t bytes) {
+    if (!p || !dev_ptr || ((uintptr_t)dev_ptr & 255u)) return CRSOLVE_EINVAL;
+    if (bytes < p->total) return CRSOLVE_ENOMEM;
+    p->ws = static_cast<char *>(dev_ptr);
+    p->ws_bytes = bytes;
+    p->factored = false;
+    return CRSOLVE_OK;
+}
+
+int crsolve_factor(crsolve_plan p, const crsolve_z *A, const crsolve_z *B, void *stream) {
+    if (!p || !A || (p->N > 1 && !B)) return CRSOLVE_EINVAL;
+    if (!aligned16(A) || (B && !aligned16(B))) return CRSOLVE_EINVAL;
+    if (!p->ws) return CRSOLVE_ENOMEM;
+    int rc = check_device(p);
+    if (rc) return rc;
+    if ((rc = ensure_prepared(p))) return rc;
+    return do_factor(p, reinterpret_cast<const z2 *>(A), reinterpret_cast<const z2 *>(B),
+                     static_cast<cudaStream_t>(stream));
+}
+
+int crsolve_solve(crsolve_plan p, int32_t k, const crsolve_z *y, crsolve_z *x, void *stream) {
+    if (!p || !y || !x || k < 1) return CRSOLVE_EINVAL;
+    if (k > p->kmax) return CRSOLVE_EUNSUPPORTED;
+    if (!aligned16(y) || !aligned16(x) || (const void *)y == (const void *)x) return CRSOLVE_EINVAL;
+    if (!p->ws) return CRSOLVE_ENOMEM;
+    if (!p->factored) return CRSOLVE_ENOTFACTORED;
+    int rc = check_device(p);
+    if (rc) return rc;
+    if ((rc = ensure_prepared(p))) return rc;
+    return do_solve(p, k, reinterpret_cast<const z2 *>(y), reinterpret_cast<z2 *>(x),
+                    static_cast<cudaStream_t>(stream));
+}
+
+int crsolve_backward(crsolve_plan p, int32_t k, const crsolve_z *x, const crsolve_z *gx, crsolve_z *gy,
+                     crsolve_z *gA, crsolve_z *gB, void *stream) {
+    if (!p || !x || !gx || !gy || k < 1) return CRSOLVE_EINVAL;
+    if (k > p->kmax) return CRSOLVE_EUNSUPPORTED;
+    if (!aligned16(x) || !aligned16(gx) || !aligned16(gy) || (gA && !aligned16(gA)) ||
+        (gB && !aligned16(gB)))
+        return CRSOLVE_EINVAL;
+    if ((const void *)gx == (const void *)gy) return CRSOLVE_EINVAL;
+    if (p->N == 1) gB = nullptr;
+    if (!p->ws) return CRSOLVE_ENOMEM;
+    if (!p->factored) return CRSOLVE_ENOTFACTORED;
+    int rc = check_device(p);
+    if (rc) return rc;
+    if ((rc = ensure_prepared(p))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = do_solve(p, k, reinterpret_cast<const z2 *>(gx), reinterpret_cast<z2 *>(gy), s))) return rc;
+    if (crs::launch_adjoint_outer(p->N, p->m, k, reinterpret_cast<const z2 *>(x),
+                                  reinterpret_cast<const z2 *>(gy), reinterpret_cast<z2 *>(gA),
+                                  reinterpret_cast<z2 *>(gB), p->nsm, s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    const unsigned long long *st = reinterpret_cast<const unsigned long long *>(p->ws + p->offStatus);
+    const size_t mm = (size_t)p->m * p->m;
+    if (gA && crs::launch_nan_if_failed(reinterpret_cast<z2 *>(gA), p->N * (int64_t)mm, st, p->nsm, s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    if (gB && crs::launch_nan_if_failed(reinterpret_cast<z2 *>(gB), (p->N - 1) * (int64_t)mm, st, p->nsm, s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    return CRSOLVE_OK;
+}
+
+int crsolve_solve_host(crsolve_plan p, int32_t k, const crsolve_z *A_host, const crsolve_z *B_host,
+                       const crsolve_z *y_host, crsolve_z *x_host, void *stream) {
+    if (!p || !A_host || !y_host || !x_host || (p->N > 1 && !B_host) || k < 1) return CRSOLVE_EINVAL;
+    if (!(p->flags & CRSOLVE_PLAN_HOST_STAGING)) return CRSOLVE_EINVAL;
+    if (k > p->kmax) return CRSOLVE_EUNSUPPORTED;
+    if (!p->ws) return CRSOLVE_ENOMEM;
+    int rc = check_device(p);
+    if (rc) return rc;
+    if ((rc = ensure_prepared(p))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t zsz = sizeof(crsolve_z), mm = (size_t)p->m * p->m, mk = (size_t)p->m * k;
+    z2 *dA = reinterpret_cast<z2 *>(p->ws + p->offSA), *dB = reinterpret_cast<z2 *>(p->ws + p->offSB);
+    z2 *dy = reinterpret_cast<z2 *>(p->ws + p->offSY), *dx = reinterpret_cast<z2 *>(p->ws + p->offSX);
+    if (cudaMemcpyAsync(dA, A_host, p->N * mm * zsz, cudaMemcpyHostToDevice, s) != cudaSuccess) return CRSOLVE_ECUDA;
+    if (p->N > 1 && cudaMemcpyAsync(dB, B_host, (p->N - 1) * mm * zsz, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    if (cudaMemcpyAsync(dy, y_host, p->N * mk * zsz, cudaMemcpyHostToDevice, s) != cudaSuccess) return CRSOLVE_ECUDA;
+    if ((rc = do_factor(p, dA, p->N > 1 ? dB : nullptr, s))) return rc;
+    if ((rc = do_solve(p, k, dy, dx, s))) return rc;
+    if (cudaMemcpyAsync(x_host, dx, p->N * mk * zsz, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CRSOLVE_ECUDA;
+    unsigned long long st = 0;
+    if (cudaMemcpyAsync(&st, p->ws + p->offStatus, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CRSOLVE_ECUDA;
+    return st == CRS_NO_FAIL ? CRSOLVE_OK : CRSOLVE_NOT_PD;
+}
+
+int crsolve_info_get(crsolve_plan p, crsolve_info *out, void *stream) {
+    if (!p || !out) return CRSOLVE_EINVAL;
+    if (!p->ws) return CRSOLVE_ENOMEM;
+    if (!p->factored) return CRSOLVE_ENOTFACTORED;
+    unsigned long long st = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&st, p->ws + p->offStatus, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return CRSOLVE_ECUDA;
+    if (st == CRS_NO_FAIL) {
+        *out = crsolve_info{CRSOLVE_OK, 0, 0, 0};
+    } else {
+        const int level = (int)(st >> 40);
+        const int64_t block = (int64_t)(st & ((1ull << 40) - 1));
+        *out = crsolve_info{CRSOLVE_NOT_PD, level, block, block << level};
+    }
+    return CRSOLVE_OK;
+}
+
+int crsolve_destroy(crsolve_plan p) {
+    delete p;
+    return CRSOLVE_OK;
+}
+
+const char *crsolve_strerror(int code) {
+    switch (code) {
+        case CRSOLVE_OK: return "ok";
+        case CRSOLVE_NOT_PD: return "matrix is not positive definite (Cholesky breakdown)";
+        case CRSOLVE_EINVAL: return "invalid argument";
+        case CRSOLVE_ENOMEM: return "workspace missing or too small";
+        case CRSOLVE_ECUDA: return "CUDA runtime error";
+        case CRSOLVE_ETIMEOUT: return "device-side wait timed out";
+        case CRSOLVE_ENOTFACTORED: return "plan has not been factored";
+        case CRSOLVE_EUNSUPPORTED: return "unsupported size or precision";
+        default: return "unknown status";
+    }
+}
+
+int crsolve_plan_levels(crsolve_plan p, int32_t *nlev, int64_t *sizes) {
+    if (!p || !nlev) return CRSOLVE_EINVAL;
+    *nlev = (int32_t)p->lev.size();
+    if (sizes)
+        for (size_t l = 0; l < p->lev.size(); ++l) sizes[l] = p->lev[l].Nl;
+    return CRSOLVE_OK;
+}
+
+int crsolve_debug_level_system(crsolve_plan p, int32_t level, const crsolve_z **A_l, const crsolve_z **B_l) {
+    if (!p || !A_l || !B_l || level < 1 || level >= (int32_t)p->lev.size()) return CRSOLVE_EINVAL;
+    if (!p->ws) return CRSOLVE_ENOMEM;
+    *A_l = reinterpret_cast<const crsolve_z *>(p->ws + p->lev[level - 1].offAn);
+    *B_l = reinterpret_cast<const crsolve_z *>(p->ws + p->lev[level - 1].offBn);
+    return CRSOLVE_OK;
+}
+
+}  // extern "C"

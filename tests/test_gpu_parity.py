@@ -1,0 +1,171 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances.  The FP64 path and the oracle are both backward stable with
+backward error about c * m * log2(N) * 2^-53 (~1e-14 here); on the default
+generator kappa <= ~10, so their relative difference is bounded by ~1e-13 and
+the tests assert 1e-12.  On the kappa ~ 1e6 systems the bound stated for the
+solver, relative error <= 1e-10, is asserted.  Breakdown flags must match
+exactly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synthetic
+import paper_1807_00370_gb300 as crs
+from tests.gpu_helpers import rel_err, to_dev
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+def run(A, B, y):
+    N, m, k = y.shape
+    dA, dB, dy = to_dev(A, B if N > 1 else None, y)
+    plan = crs.Plan(N, m, k)
+    crs.crsolve_factor(plan, dA, dB)
+    x = crs.crsolve_solve(plan, dy)
+    info = crs.crsolve_info_get(plan)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), info, plan
+
+
+def test_config0_small_system(cuda_ok):
+    """N = 64, m = 4, k = 1 with the standard generator."""
+    A, B, y = synthetic.gen_system(64, 4, 1, seed=0)
+    x, info, _ = run(A, B, y)
+    xo, io = oracle.cr_solve(A, B, y)
+    assert info == io
+    assert rel_err(x, xo) <= TOL
+
+
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5, 7, 8, 9, 12, 16, 20, 32, 33, 48, 64])
+def test_every_block_size(cuda_ok, m):
+    N = 37 if m <= 16 else 11
+    A, B, y = synthetic.gen_system(N, m, 3, seed=m)
+    x, info, _ = run(A, B, y)
+    xo, io = oracle.cr_solve(A, B, y)
+    assert info == io and info["status"] == 0
+    assert rel_err(x, xo) <= TOL
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7, 8, 9, 15, 16, 17, 31, 33, 63, 64, 65, 127, 128, 129,
+                               255, 257, 1000, 1023, 1024, 1025, 4093, 4096, 4097])
+def test_uneven_sizes_span_tiles_and_ragged_tails(cuda_ok, N):
+    A, B, y = synthetic.gen_system(N, 8, 4, seed=N)
+    x, info, _ = run(A, B, y)
+    xo, io = oracle.cr_solve(A, B, y)
+    assert info == io and info["status"] == 0
+    assert rel_err(x, xo) <= TOL
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 16, 17, 33, 40])
+def test_rhs_widths_and_column_chunks(cuda_ok, k):
+    for m in (4, 16, 64):
+        N = 50 if m < 64 else 9
+        A, B, y = synthetic.gen_system(N, m, k, seed=k + m)
+        x, info, _ = run(A, B, y)
+        xo, _ = oracle.cr_solve(A, B, y)
+        assert rel_err(x, xo) <= TOL, (m, k)
+
+
+@pytest.mark.parametrize("N,m", [(2, 1), (9, 4), (64, 8), (300, 16), (33, 32)])
+def test_each_level_system_matches_oracle(cuda_ok, N, m):
+    """The reduced system (A^(l), B^(l)) of every level against the oracle's
+    level reduction applied to the oracle's previous level; the stored blocks
+    are exactly Hermitian."""
+    A, B, y = synthetic.gen_system(N, m, 1, seed=N * m)
+    _, _, plan = run(A, B, y)
+    levels = crs.crsolve_plan_levels(plan)
+    Ao, Bo = A, B
+    for l in range(1, len(levels)):
+        lev = oracle.cr_level(Ao, Bo)
+        Ao, Bo = lev["An"], lev["Bn"]
+        Ag, Bg = crs.crsolve_debug_level_system(plan, l)
+        Ag, Bg = Ag.cpu().numpy(), Bg.cpu().numpy()
+        assert np.array_equal(Ag, np.conj(np.swapaxes(Ag, 1, 2))), l
+        assert np.abs(Ag - Ao).max() <= 1e-13 * np.abs(Ao).max(), l
+        if Bo.size:
+            assert np.abs(Bg - Bo).max() <= 1e-13 * max(np.abs(Bo).max(), 1.0), l
+
+
+def test_lower_triangle_only_and_real_diagonal(cuda_ok):
+    A, B, y = synthetic.gen_system(21, 6, 2, seed=3)
+    A2 = A.copy()
+    iu = np.triu_indices(6, 1)
+    A2[:, iu[0], iu[1]] = 5e3 - 1e3j
+    A2[:, np.arange(6), np.arange(6)] += 3j
+    x1, _, _ = run(A, B, y)
+    x2, _, _ = run(A2, B, y)
+    assert np.array_equal(x1, x2)
+
+
+@pytest.mark.parametrize("p,m", [(3, 2), (6, 8), (10, 4)])
+def test_breakdown_flag_and_location(cuda_ok, p, m):
+    N = 1 << p
+    for seed in range(20):
+        A, B, y = synthetic.gen_system(N, m, 2, seed=seed)
+        Ai = synthetic.make_indefinite(A)
+        if np.linalg.eigvalsh(Ai[N // 2 - 1]).min() < 0:
+            break
+    x, info, _ = run(Ai, B, y)
+    _, io = oracle.cr_solve(Ai, B, y)
+    assert info == io == {"status": 1, "level": p - 1, "block": 1, "orig_block": N // 2}
+    assert np.isnan(x).all()
+
+
+def test_breakdown_flags_match_on_random_tiny_systems(cuda_ok):
+    rng = np.random.default_rng(99)
+    for trial in range(60):
+        N = int(rng.integers(1, 40))
+        m = int(rng.integers(1, 9))
+        A, B, y = synthetic.gen_system(N, m, 1, seed=5000 + trial, shift=0.3)
+        A = A.copy()
+        A[int(rng.integers(0, N))] -= float(rng.uniform(0, 4)) * np.eye(m)
+        _, info, _ = run(A, B, y)
+        _, io = oracle.cr_solve(A, B, y)
+        assert info["status"] == io["status"], (trial, info, io)
+        if io["status"]:
+            assert info == io
+
+
+def test_nan_input_reports_breakdown(cuda_ok):
+    A, B, y = synthetic.gen_system(40, 4, 1, seed=4)
+    A[10, 2, 2] = np.nan
+    x, info, _ = run(A, B, y)
+    _, io = oracle.cr_solve(A, B, y)
+    assert info == io
+    assert np.isnan(x).all()
+
+
+def test_refactor_and_resolve_reuse_the_plan(cuda_ok):
+    A, B, y = synthetic.gen_system(100, 8, 3, seed=1)
+    A2, B2, y2 = synthetic.gen_system(100, 8, 3, seed=2)
+    dA, dB, dy, dA2, dB2, dy2 = to_dev(A, B, y, A2, B2, y2)
+    plan = crs.Plan(100, 8, 3)
+    crs.crsolve_factor(plan, dA, dB)
+    x1 = crs.crsolve_solve(plan, dy)
+    x1b = crs.crsolve_solve(plan, dy2)
+    crs.crsolve_factor(plan, dA2, dB2)
+    x2 = crs.crsolve_solve(plan, dy2)
+    assert rel_err(x1, oracle.cr_solve(A, B, y)[0]) <= TOL
+    assert rel_err(x1b, oracle.cr_solve(A, B, y2)[0]) <= TOL
+    assert rel_err(x2, oracle.cr_solve(A2, B2, y2)[0]) <= TOL
+
+
+def test_solve_host_buffers(cuda_ok):
+    A, B, y = synthetic.gen_system(333, 8, 4, seed=8)
+    plan = crs.Plan(333, 8, 4, flags=1)
+    tA, tB, ty = (torch.from_numpy(a).pin_memory() for a in (A, B, y))
+    x, rc = crs.crsolve_solve_host(plan, tA, tB, ty)
+    assert rc == 0
+    assert rel_err(x.numpy(), oracle.cr_solve(A, B, y)[0]) <= TOL
+
+
+def test_solve_before_factor_is_an_error(cuda_ok):
+    plan = crs.Plan(8, 4, 1)
+    y = torch.zeros((8, 4, 1), dtype=torch.complex128, device="cuda")
+    with pytest.raises(RuntimeError, match="not been factored"):
+        crs.crsolve_solve(plan, y)
