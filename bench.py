@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the FP64 cyclic-reduction solver on GB300.
+
+One step = crsolve_factor + crsolve_solve of one synthetic Hermitian positive
+definite block-tridiagonal system: N = 2^20 blocks, m = 8, k = 4, complex128,
+generated by synthetic.gen_system (seed 1000).  The metric is block-rows/s =
+N / (factor + solve time), inputs resident in HBM (A alone is 1 GiB, far
+larger than the 126 MB L2, so no L2 flush is needed between steps).
+
+Prints one JSON line (rank 0).  Extra keys:
+  roofline      the dominant kernel (k_factor_odd, all levels) against the FP64
+                pipe: algorithmic flops / CUDA-event time of its launches
+  e2e           the same metric through crsolve_solve_host (pinned host
+                buffers, H2D + factor + solve + D2H inside the timed region)
+  cpu_baseline  the CPU oracle on the host cores on a bounded sample
+  clocks        nvidia-smi samples taken during the timed region
+
+--impl reference times the CPU oracle alone (the reference arm).
+Under torchrun (N > 1) every rank solves its own independent system (weak
+scaling; the only collectives are the timing barrier and max).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic  # noqa: E402
+
+N_BLOCKS, M, K_RHS = 1 << 20, 8, 4
+SEED = 1000
+WORKLOAD = f"plain CR, one HPD block-tridiagonal system: N=2^20 blocks, m={M}, k={K_RHS}, complex128"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# GB300: 2 FP64 FMA per clock per SM (measured by a DFMA throughput probe at
+# ~1.9 DFMA/clk/SM), 152 SMs, 2070 MHz maximum SM clock
+FP64_FMA_PER_CLK_SM, N_SM, SM_MAX_MHZ = 2, 152, 2070.0
+FP64_PEAK_GFLOPS = FP64_FMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ / 1e3
+
+
+def flops_factor_per_odd_block(m: int) -> float:
+    """Algorithmic flops of one odd block in the factor sweep (complex, 8 real
+    flops per multiply-add): Cholesky m^3/6, L^{-1}[B|B^H] m^3, lower triangle
+    of the 2m x 2m product Z^H Z 2m^3 (leading order)."""
+    return 8.0 * (m ** 3 / 6.0 + m ** 3 + 2.0 * m ** 3)
+
+
+def flops_solve_per_odd_block(m: int, k: int) -> float:
+    """Forward solve m^2 k/2, Z^H r 2 m^2 k, Z x 2 m^2 k, backward solve m^2 k/2."""
+    return 8.0 * 5.0 * m * m * k
+
+
+def flops_per_block_row(m: int, k: int) -> float:
+    # every block row is an odd block at exactly one level
+    return flops_factor_per_odd_block(m) + flops_solve_per_odd_block(m, k)
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) of SM clock and throttle reasons."""
+
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index, self.rows, self.proc, self.t0, self.t1 = index, [], None, None, None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), line.strip()))
+
+    def mark(self, begin: bool):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait(timeout=5)
+        self.thread.join(timeout=2)
+        sms, maxs, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ts, line in self.rows:
+            if self.t0 is not None and not (self.t0 - 0.2 <= ts <= (self.t1 or ts) + 0.2):
+                continue
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sms.append(float(parts[1]))
+                maxs.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sms) if sms else None,
+                "sm_max_mhz": max(maxs) if maxs else None,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def cpu_oracle_sample(seconds: float = 12.0, n_sample: int = 1 << 17):
+    """The CPU oracle as it stands on the host cores, on a bounded sample of
+    the workload (the same recipe with fewer blocks).  Returns (value, cores,
+    sample description, (A, B, y, x_oracle))."""
+    import oracle
+    A, B, y = synthetic.gen_system(n_sample, M, K_RHS, seed=SEED)
+    cores = oracle.max_threads()
+    x, info = oracle.cr_solve(A, B, y)       # warm-up, also the reference x of the sample
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        oracle.cr_solve(A, B, y)
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    value = n_sample * reps / el
+    desc = f"{reps} oracle solves (factor+solve) of an N=2^{n_sample.bit_length() - 1} system, m={M}, k={K_RHS}, {el:.1f} s"
+    return value, cores, desc, (A, B, y, x)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    n_sample = 1 << 16
+    A, B, y = synthetic.gen_system(n_sample, M, K_RHS, seed=SEED)
+    for _ in range(args.warmup):
+        oracle.cr_solve(A, B, y)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.cr_solve(A, B, y)
+    el = time.perf_counter() - t0
+    value = n_sample * args.steps / el
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": "block-rows/s", "value": value, "unit": "block-rows/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": f"N=2^16 blocks per step (bounded sample of the workload)"},
+            "cpu_baseline": {"value": value, "unit": "block-rows/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{args.steps} oracle solves of an N=2^16, m={M}, k={K_RHS} system"},
+            "e2e": {"value": value, "unit": "block-rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--log2n", type=int, default=20,
+                    help="log2 of the block count (smaller cases are for profiling only)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1807_00370_gb300 as crs
+    global N_BLOCKS, WORKLOAD
+    if args.log2n != 20:
+        N_BLOCKS = 1 << args.log2n
+        WORKLOAD = WORKLOAD.replace("N=2^20", f"N=2^{args.log2n}")
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    A, B, y = synthetic.gen_system(N_BLOCKS, M, K_RHS, seed=SEED + rank)
+    dA, dB, dy = (torch.from_numpy(a).to(dev) for a in (A, B, y))
+    plan = crs.Plan(N_BLOCKS, M, K_RHS, flags=0 if args.no_e2e else 1)
+    dx = torch.empty_like(dy)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        crs.crsolve_factor(plan, dA, dB)
+        crs.crsolve_solve(plan, dy, dx)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    info = crs.crsolve_info_get(plan)
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(1.0)
+    launches0 = crs.crsolve_launch_count(plan)
+    crs.crsolve_timing_enable(plan, True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark(True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark(False)
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    recs = crs.crsolve_timing_read(plan)
+    crs.crsolve_timing_enable(plan, False)
+    launches = crs.crsolve_launch_count(plan) - launches0
+    if ws > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # per-kernel breakdown and the dominant kernel's roofline (FP64 pipe)
+    by_kind = {}
+    for kind, level, units, kms in recs:
+        d = by_kind.setdefault(kind, {"ms": 0.0, "launches": 0, "units": 0})
+        d["ms"] += kms
+        d["launches"] += 1
+        d["units"] += units
+    fac = by_kind.get("factor_odd", {"ms": 0.0, "units": 0, "launches": 0})
+    fac_flops = fac["units"] * flops_factor_per_odd_block(M)
+    achieved = fac_flops / (fac["ms"] * 1e-3) / 1e12 if fac["ms"] else None
+    peak_tf = FP64_PEAK_GFLOPS / 1e3
+    step_flops = N_BLOCKS * flops_per_block_row(M, K_RHS)
+    ms_step = ms / args.steps
+    value = ws * N_BLOCKS * args.steps / (ms * 1e-3)
+
+    # measurement-side residual check (torch ops, not part of the solver)
+    with torch.no_grad():
+        Ah = torch.tril(dA, -1)
+        Ah = Ah + Ah.conj().transpose(1, 2) + torch.diag_embed(torch.diagonal(dA, dim1=1, dim2=2).real.to(dA.dtype))
+        r = dy - torch.bmm(Ah, dx)
+        r[1:] -= torch.bmm(dB, dx[:-1])
+        r[:-1] -= torch.bmm(dB.conj().transpose(1, 2), dx[1:])
+        normA = (Ah.abs().sum(2).max() + 2 * dB.abs().sum(2).max()).item()
+        eta = (r.abs().amax() / (normA * dx.abs().amax())).item()
+
+    e2e = None
+    if not args.no_e2e:
+        tA, tB, ty = (torch.from_numpy(a).pin_memory() for a in (A, B, y))
+        tx = torch.empty_like(ty).pin_memory()
+        crs.crsolve_solve_host(plan, tA, tB, ty, tx)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            crs.crsolve_solve_host(plan, tA, tB, ty, tx)
+        el = time.perf_counter() - t0
+        e2e = {"value": N_BLOCKS * args.e2e_steps / el * ws, "unit": "block-rows/s",
+               "h2d_bytes_per_step": int(tA.numel() + tB.numel() + ty.numel()) * 16,
+               "d2h_bytes_per_step": int(tx.numel()) * 16 + 8, "steps": args.e2e_steps}
+
+    cpu = None
+    sample_err = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        v, cores, desc, (sA, sB, sy, sx) = cpu_oracle_sample()
+        cpu = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle", "sample": desc}
+        # the GPU on the same sample, for the error at which the rate is quoted
+        xs = crs.solve(*(torch.from_numpy(a).to(dev) for a in (sA, sB, sy))).cpu().numpy()
+        sample_err = float(np.linalg.norm(xs - sx) / np.linalg.norm(sx))
+
+    if rank == 0:
+        line = {
+            "metric": "block-rows/s", "value": value, "unit": "block-rows/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "N": N_BLOCKS, "m": M, "k": K_RHS, "seed": SEED,
+                       "l2": "inputs larger than L2 (A alone 1 GiB), no flush", "parallelism":
+                       f"{ws} independent system(s), one per GPU"},
+            "roofline": {"bound": "alu", "kernel": "k_factor_odd<8>, all levels",
+                         "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": (achieved / peak_tf) if achieved else None, "traffic": None,
+                         "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived)",
+                         "flops_per_unit": flops_factor_per_odd_block(M), "units": fac["units"] // args.steps,
+                         "launches_per_step": fac["launches"] // args.steps},
+            "step_roofline": {"flops_per_step": step_flops, "achieved": step_flops / (ms_step * 1e-3) / 1e12,
+                              "frac": step_flops / (ms_step * 1e-3) / 1e12 / peak_tf},
+            "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] // args.steps}
+                        for k, v in by_kind.items()},
+            "error": {"residual_eta": eta, "sample_rel_err_vs_oracle": sample_err, "bound": 1e-10},
+            "breakdown": info,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

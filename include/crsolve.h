@@ -157,6 +157,37 @@ int crsolve_destroy(crsolve_plan p);
 /* Static description of a status code. */
 const char *crsolve_strerror(int code);
 
+/* ---- instrumentation (the paper has no counterpart; used by the benchmark) ---- */
+
+enum crsolve_kernel_kind {
+    CRSOLVE_K_FACTOR_ODD = 0,      /* Cholesky + P, Q + Z^H Z of a level's odd blocks */
+    CRSOLVE_K_FACTOR_EVEN = 1,     /* next level's diagonal blocks */
+    CRSOLVE_K_SOLVE_DOWN_ODD = 2,  /* r = L^{-1} y and Z^H r of a level's odd blocks */
+    CRSOLVE_K_SOLVE_DOWN_EVEN = 3, /* next level's right-hand side */
+    CRSOLVE_K_SOLVE_UP = 4,        /* back-substitution of a level */
+    CRSOLVE_K_ADJOINT = 5,         /* gA, gB outer products */
+    CRSOLVE_K_NANFILL = 6          /* NaN fill of gA / gB after a breakdown */
+};
+
+typedef struct {
+    int32_t kind;    /* crsolve_kernel_kind */
+    int32_t level;   /* reduction level (0 for kernels outside the sweep) */
+    int64_t units;   /* blocks the launch processed (odd or even blocks of the level) */
+    float ms;        /* duration between CUDA events recorded around the launch */
+} crsolve_kernel_time;
+
+/* With enable != 0, every kernel the plan launches is bracketed by CUDA events
+ * recorded on the launch stream; records accumulate until read.  Not for use
+ * inside stream capture. */
+int crsolve_timing_enable(crsolve_plan p, int32_t enable);
+
+/* Waits for the recorded events and returns up to cap records (oldest first)
+ * in out, the number available in *count; then clears the records. */
+int crsolve_timing_read(crsolve_plan p, crsolve_kernel_time *out, int32_t cap, int32_t *count);
+
+/* Kernels this plan has launched since it was created. */
+int crsolve_launch_count(crsolve_plan p, int64_t *count);
+
 /* Number of levels of the plan (floor(log2 N) + 1) and the level sizes. */
 int crsolve_plan_levels(crsolve_plan p, int32_t *nlev, int64_t *sizes /* [nlev] or NULL */);
 

@@ -39,6 +39,14 @@ class CrsolveInfo(ctypes.Structure):
                 ("block", ctypes.c_int64), ("orig_block", ctypes.c_int64)]
 
 
+class CrsolveKernelTime(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("level", ctypes.c_int32),
+                ("units", ctypes.c_int64), ("ms", ctypes.c_float)]
+
+
+KERNEL_KINDS = {0: "factor_odd", 1: "factor_even", 2: "solve_down_odd", 3: "solve_down_even",
+                4: "solve_up", 5: "adjoint_outer", 6: "nan_fill"}
+
 SIGNATURES = {
     "crsolve_plan_create": (ctypes.c_int, [_I64, _I32, _I32, _I32, _U32, ctypes.POINTER(_P)]),
     "crsolve_workspace_bytes": (ctypes.c_int, [_P, ctypes.POINTER(_SZ)]),
@@ -52,6 +60,9 @@ SIGNATURES = {
     "crsolve_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "crsolve_plan_levels": (ctypes.c_int, [_P, ctypes.POINTER(_I32), _P]),
     "crsolve_debug_level_system": (ctypes.c_int, [_P, _I32, ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "crsolve_timing_enable": (ctypes.c_int, [_P, _I32]),
+    "crsolve_timing_read": (ctypes.c_int, [_P, ctypes.POINTER(CrsolveKernelTime), _I32, ctypes.POINTER(_I32)]),
+    "crsolve_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
 }
 
 

@@ -15,7 +15,8 @@ from . import _native as nat
 
 __all__ = ["Plan", "crsolve_plan_create", "crsolve_factor", "crsolve_solve", "crsolve_backward",
            "crsolve_info_get", "crsolve_solve_host", "crsolve_plan_levels",
-           "crsolve_debug_level_system", "solve", "CRSolveFn", "NotPositiveDefinite"]
+           "crsolve_debug_level_system", "crsolve_timing_enable", "crsolve_timing_read",
+           "crsolve_launch_count", "solve", "CRSolveFn", "NotPositiveDefinite"]
 
 
 class NotPositiveDefinite(RuntimeError):
@@ -180,6 +181,24 @@ def crsolve_debug_level_system(plan: Plan, level: int):
     A = ws[a0:a0 + Nl * m * m * 16].view(torch.complex128).reshape(Nl, m, m).clone()
     B = ws[b0:b0 + max(Nl - 1, 0) * m * m * 16].view(torch.complex128).reshape(max(Nl - 1, 0), m, m).clone()
     return A, B
+
+
+def crsolve_timing_enable(plan: Plan, enable: bool = True) -> None:
+    nat.check(nat.load().crsolve_timing_enable(plan.handle, 1 if enable else 0), "crsolve_timing_enable")
+
+
+def crsolve_timing_read(plan: Plan, cap: int = 1 << 16):
+    """Per-kernel records [(kind, level, units, ms)] since the last read."""
+    buf = (nat.CrsolveKernelTime * cap)()
+    n = ctypes.c_int32()
+    nat.check(nat.load().crsolve_timing_read(plan.handle, buf, cap, ctypes.byref(n)), "crsolve_timing_read")
+    return [(nat.KERNEL_KINDS[buf[i].kind], buf[i].level, buf[i].units, buf[i].ms) for i in range(min(n.value, cap))]
+
+
+def crsolve_launch_count(plan: Plan) -> int:
+    c = ctypes.c_int64()
+    nat.check(nat.load().crsolve_launch_count(plan.handle, ctypes.byref(c)), "crsolve_launch_count")
+    return int(c.value)
 
 
 def solve(A: torch.Tensor, B: torch.Tensor | None, y: torch.Tensor, check: bool = True) -> torch.Tensor:

@@ -20,10 +20,14 @@ size_t factor_smem_bytes(int mt, int nb);
 size_t solve_smem_bytes(int mt, int nb, int kc, bool up);
 cudaError_t prepare_kernels(int mt);                 // raise shared-memory limits once per device
 
-// One reduction level of the factor sweep: odd-block kernel, then even-block kernel.
-cudaError_t launch_factor_level(int mt, const LevelArgs &a, int nsm, cudaStream_t s);
-// Down sweep of one level (r, and the next level's right-hand side).
-cudaError_t launch_solve_down_level(int mt, const LevelArgs &a, int nsm, cudaStream_t s);
+// Factor sweep of one level: the odd-block kernel (Cholesky, P, Q, Z^H Z),
+// then the even-block kernel (the next level's diagonal blocks).
+cudaError_t launch_factor_odd(int mt, const LevelArgs &a, int nsm, cudaStream_t s);
+cudaError_t launch_factor_even(const LevelArgs &a, int nsm, cudaStream_t s);
+// Down sweep of one level: r and Z^H r on the odd blocks, then the next
+// level's right-hand side on the even blocks.
+cudaError_t launch_solve_down_odd(int mt, const LevelArgs &a, int nsm, cudaStream_t s);
+cudaError_t launch_solve_down_even(const LevelArgs &a, int nsm, cudaStream_t s);
 // Up sweep of one level (x of this level from the next level's x).
 cudaError_t launch_solve_up_level(int mt, const LevelArgs &a, int nsm, cudaStream_t s);
 // Adjoint outer products gA, gB from x and gy.

@@ -462,27 +462,21 @@ static unsigned grid_1d(int64_t items, int nsm) {
 }
 
 template <int MT>
-static cudaError_t factor_level_mt(LevelArgs a, int nsm, cudaStream_t s) {
+static cudaError_t factor_odd_mt(LevelArgs a, int nsm, cudaStream_t s) {
     const TileShape ts = tile_shape(MT);
     a.nb = level_nb(ts.nb_factor, a.no, nsm);
     const unsigned grid = (unsigned)((a.no + a.nb - 1) / a.nb);
     k_factor_odd<MT><<<grid, ts.threads, factor_smem_bytes(MT, a.nb), s>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || a.ne == 0) return e;
-    k_factor_even<<<grid_1d(a.ne * (a.m * (a.m + 1) / 2), nsm), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 template <int MT>
-static cudaError_t solve_down_mt(LevelArgs a, int nsm, cudaStream_t s) {
+static cudaError_t solve_down_odd_mt(LevelArgs a, int nsm, cudaStream_t s) {
     const TileShape ts = tile_shape(MT);
     a.nb = level_nb(ts.nb_solve, a.no, nsm);
     a.kc = a.k < ts.kc_max ? a.k : ts.kc_max;
     const dim3 grid((unsigned)((a.no + a.nb - 1) / a.nb), (unsigned)((a.k + a.kc - 1) / a.kc));
     k_solve_down_odd<MT><<<grid, ts.threads, solve_smem_bytes(MT, a.nb, a.kc, false), s>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess || a.ne == 0) return e;
-    k_solve_down_even<<<grid_1d(a.ne * a.m * a.k, nsm), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -506,11 +500,21 @@ static cudaError_t solve_up_mt(LevelArgs a, int nsm, cudaStream_t s) {
         default: return cudaErrorInvalidValue;      \
     }
 
-cudaError_t launch_factor_level(int mt, const LevelArgs &a, int nsm, cudaStream_t s) {
-    CRS_DISPATCH(factor_level_mt, mt, a, nsm, s)
+cudaError_t launch_factor_odd(int mt, const LevelArgs &a, int nsm, cudaStream_t s) {
+    CRS_DISPATCH(factor_odd_mt, mt, a, nsm, s)
 }
-cudaError_t launch_solve_down_level(int mt, const LevelArgs &a, int nsm, cudaStream_t s) {
-    CRS_DISPATCH(solve_down_mt, mt, a, nsm, s)
+cudaError_t launch_factor_even(const LevelArgs &a, int nsm, cudaStream_t s) {
+    if (a.ne == 0) return cudaSuccess;
+    k_factor_even<<<grid_1d(a.ne * (a.m * (a.m + 1) / 2), nsm), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+cudaError_t launch_solve_down_odd(int mt, const LevelArgs &a, int nsm, cudaStream_t s) {
+    CRS_DISPATCH(solve_down_odd_mt, mt, a, nsm, s)
+}
+cudaError_t launch_solve_down_even(const LevelArgs &a, int nsm, cudaStream_t s) {
+    if (a.ne == 0) return cudaSuccess;
+    k_solve_down_even<<<grid_1d(a.ne * a.m * a.k, nsm), 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 cudaError_t launch_solve_up_level(int mt, const LevelArgs &a, int nsm, cudaStream_t s) {
     CRS_DISPATCH(solve_up_mt, mt, a, nsm, s)

@@ -39,6 +39,13 @@ struct crsolve_plan_s {
     size_t ws_bytes = 0;
     bool factored = false;
     bool prepared = false;
+    // instrumentation
+    bool timing = false;
+    struct Rec { int kind, level; int64_t units; cudaEvent_t e0, e1; };
+    std::vector<Rec> recs;
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    int64_t launches = 0;
 };
 
 namespace {
@@ -88,12 +95,46 @@ int check_device(const crsolve_plan_s *p) {
     return dev == p->device ? CRSOLVE_OK : CRSOLVE_EINVAL;
 }
 
+cudaEvent_t next_event(crsolve_plan_s *p) {
+    if (p->pool_used == p->pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        p->pool.push_back(e);
+    }
+    return p->pool[p->pool_used++];
+}
+
+// Launch one kernel through fn(), counting it and, when timing is on,
+// bracketing it with events on stream s.
+template <class F>
+int launch(crsolve_plan_s *p, int kind, int level, int64_t units, cudaStream_t s, F &&fn) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (p->timing) {
+        e0 = next_event(p);
+        e1 = next_event(p);
+        if (!e0 || !e1 || cudaEventRecord(e0, s) != cudaSuccess) return CRSOLVE_ECUDA;
+    }
+    if (fn() != cudaSuccess) return CRSOLVE_ECUDA;
+    p->launches += 1;
+    if (p->timing) {
+        if (cudaEventRecord(e1, s) != cudaSuccess) return CRSOLVE_ECUDA;
+        p->recs.push_back({kind, level, units, e0, e1});
+    }
+    return CRSOLVE_OK;
+}
+
 int do_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
     if (cudaMemsetAsync(p->ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
         return CRSOLVE_ECUDA;
+    int rc;
     for (int l = 0; l < (int)p->lev.size(); ++l) {
-        crs::LevelArgs a = level_args(p, l, A, B);
-        if (crs::launch_factor_level(p->mt, a, p->nsm, s) != cudaSuccess) return CRSOLVE_ECUDA;
+        const crs::LevelArgs a = level_args(p, l, A, B);
+        if ((rc = launch(p, CRSOLVE_K_FACTOR_ODD, l, a.no, s,
+                         [&] { return crs::launch_factor_odd(p->mt, a, p->nsm, s); })))
+            return rc;
+        if (a.ne > 0 && (rc = launch(p, CRSOLVE_K_FACTOR_EVEN, l, a.ne, s,
+                                     [&] { return crs::launch_factor_even(a, p->nsm, s); })))
+            return rc;
     }
     p->factored = true;
     return CRSOLVE_OK;
@@ -101,17 +142,25 @@ int do_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
 
 int do_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     const int nlev = (int)p->lev.size();
+    int rc;
     for (int l = 0; l < nlev; ++l) {
         crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
         a.k = k;
         a.y = (l == 0) ? y : reinterpret_cast<const z2 *>(p->ws + p->lev[l - 1].offYn);
-        if (crs::launch_solve_down_level(p->mt, a, p->nsm, s) != cudaSuccess) return CRSOLVE_ECUDA;
+        if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s,
+                         [&] { return crs::launch_solve_down_odd(p->mt, a, p->nsm, s); })))
+            return rc;
+        if (a.ne > 0 && (rc = launch(p, CRSOLVE_K_SOLVE_DOWN_EVEN, l, a.ne, s,
+                                     [&] { return crs::launch_solve_down_even(a, p->nsm, s); })))
+            return rc;
     }
     for (int l = nlev - 1; l >= 0; --l) {
         crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
         a.k = k;
         a.x = (l == 0) ? x : reinterpret_cast<z2 *>(p->ws + p->lev[l - 1].offXn);
-        if (crs::launch_solve_up_level(p->mt, a, p->nsm, s) != cudaSuccess) return CRSOLVE_ECUDA;
+        if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, l, a.no, s,
+                         [&] { return crs::launch_solve_up_level(p->mt, a, p->nsm, s); })))
+            return rc;
     }
     return CRSOLVE_OK;
 }
@@ -227,16 +276,23 @@ int crsolve_backward(crsolve_plan p, int32_t k, const crsolve_z *x, const crsolv
     if ((rc = ensure_prepared(p))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if ((rc = do_solve(p, k, reinterpret_cast<const z2 *>(gx), reinterpret_cast<z2 *>(gy), s))) return rc;
-    if (crs::launch_adjoint_outer(p->N, p->m, k, reinterpret_cast<const z2 *>(x),
-                                  reinterpret_cast<const z2 *>(gy), reinterpret_cast<z2 *>(gA),
-                                  reinterpret_cast<z2 *>(gB), p->nsm, s) != cudaSuccess)
-        return CRSOLVE_ECUDA;
+    if (!gA && !gB) return CRSOLVE_OK;
+    if ((rc = launch(p, CRSOLVE_K_ADJOINT, 0, p->N, s, [&] {
+             return crs::launch_adjoint_outer(p->N, p->m, k, reinterpret_cast<const z2 *>(x),
+                                              reinterpret_cast<const z2 *>(gy), reinterpret_cast<z2 *>(gA),
+                                              reinterpret_cast<z2 *>(gB), p->nsm, s);
+         })))
+        return rc;
     const unsigned long long *st = reinterpret_cast<const unsigned long long *>(p->ws + p->offStatus);
-    const size_t mm = (size_t)p->m * p->m;
-    if (gA && crs::launch_nan_if_failed(reinterpret_cast<z2 *>(gA), p->N * (int64_t)mm, st, p->nsm, s) != cudaSuccess)
-        return CRSOLVE_ECUDA;
-    if (gB && crs::launch_nan_if_failed(reinterpret_cast<z2 *>(gB), (p->N - 1) * (int64_t)mm, st, p->nsm, s) != cudaSuccess)
-        return CRSOLVE_ECUDA;
+    const int64_t mm = (int64_t)p->m * p->m;
+    if (gA && (rc = launch(p, CRSOLVE_K_NANFILL, 0, p->N, s, [&] {
+                   return crs::launch_nan_if_failed(reinterpret_cast<z2 *>(gA), p->N * mm, st, p->nsm, s);
+               })))
+        return rc;
+    if (gB && (rc = launch(p, CRSOLVE_K_NANFILL, 0, p->N - 1, s, [&] {
+                   return crs::launch_nan_if_failed(reinterpret_cast<z2 *>(gB), (p->N - 1) * mm, st, p->nsm, s);
+               })))
+        return rc;
     return CRSOLVE_OK;
 }
 
@@ -287,7 +343,40 @@ int crsolve_info_get(crsolve_plan p, crsolve_info *out, void *stream) {
 }
 
 int crsolve_destroy(crsolve_plan p) {
+    if (!p) return CRSOLVE_EINVAL;
+    for (cudaEvent_t e : p->pool) cudaEventDestroy(e);
     delete p;
+    return CRSOLVE_OK;
+}
+
+int crsolve_timing_enable(crsolve_plan p, int32_t enable) {
+    if (!p) return CRSOLVE_EINVAL;
+    p->timing = enable != 0;
+    p->recs.clear();
+    p->pool_used = 0;
+    return CRSOLVE_OK;
+}
+
+int crsolve_timing_read(crsolve_plan p, crsolve_kernel_time *out, int32_t cap, int32_t *count) {
+    if (!p || !count || (cap > 0 && !out)) return CRSOLVE_EINVAL;
+    *count = (int32_t)p->recs.size();
+    for (size_t i = 0; i < p->recs.size(); ++i) {
+        const auto &r = p->recs[i];
+        if (cudaEventSynchronize(r.e1) != cudaSuccess) return CRSOLVE_ECUDA;
+        if ((int32_t)i < cap) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, r.e0, r.e1) != cudaSuccess) return CRSOLVE_ECUDA;
+            out[i] = crsolve_kernel_time{r.kind, r.level, r.units, ms};
+        }
+    }
+    p->recs.clear();
+    p->pool_used = 0;
+    return CRSOLVE_OK;
+}
+
+int crsolve_launch_count(crsolve_plan p, int64_t *count) {
+    if (!p || !count) return CRSOLVE_EINVAL;
+    *count = p->launches;
     return CRSOLVE_OK;
 }
 
