@@ -17,7 +17,11 @@ typedef double2 z2;
 
 __device__ __forceinline__ z2 zmk(double re, double im) { return make_double2(re, im); }
 __device__ __forceinline__ z2 zconj(z2 a) { return make_double2(a.x, -a.y); }
-__device__ __forceinline__ z2 zneg(z2 a) { return make_double2(-a.x, -a.y); }
+// negation by flipping sign bits (integer pipe, no FP64 instruction)
+__device__ __forceinline__ double dneg_bits(double v) {
+    return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+}
+__device__ __forceinline__ z2 zneg(z2 a) { return make_double2(dneg_bits(a.x), dneg_bits(a.y)); }
 __device__ __forceinline__ z2 zscale(z2 a, double s) { return make_double2(a.x * s, a.y * s); }
 __device__ __forceinline__ z2 zsub(z2 a, z2 b) { return make_double2(a.x - b.x, a.y - b.y); }
 

@@ -108,13 +108,17 @@ __global__ void __launch_bounds__(256) k_factor_odd(LevelArgs a) {
     }
     __syncthreads();
 
-    // Cholesky, left-looking by columns; items (block, row >= c)
+    // Cholesky, left-looking by columns.  Pass 1 of column c: the pivots
+    // (one item per block, in warps of their own so that the sqrt path does
+    // not diverge from the off-diagonal path), then the unscaled entries
+    // below the pivot.  Pass 2 scales them by 1 / pivot.
+    const int dpad = (nbh + 31) & ~31;
     for (int c = 0; c < m; ++c) {
-        const int cnt = m - c;
-        for (int e = tid; e < nbh * cnt; e += NT) {
-            const int b = e / cnt, r = c + (e - b * cnt);
-            z2 *Lb = sL + b * MT * MT;
-            if (r == c) {
+        const int below = m - c - 1;
+        for (int e = tid; e < dpad + nbh * below; e += NT) {
+            if (e < nbh) {
+                const int b = e;
+                z2 *Lb = sL + b * MT * MT;
                 double d = Lb[c * MT + c].x;
                 for (int s = 0; s < c; ++s) {
                     const z2 l = Lb[c * MT + s];
@@ -125,15 +129,17 @@ __global__ void __launch_bounds__(256) k_factor_odd(LevelArgs a) {
                 const double iv = rsqrt(d);
                 sInv[b * MT + c] = iv;
                 Lb[c * MT + c] = zmk(d * iv, 0.0);
-            } else {
+            } else if (e >= dpad) {
+                const int e2 = e - dpad, b = e2 / below, r = c + 1 + (e2 - b * below);
+                z2 *Lb = sL + b * MT * MT;
                 z2 u = Lb[r * MT + c];
                 for (int s = 0; s < c; ++s) zmsub_cb(u, Lb[r * MT + s], Lb[c * MT + s]);
                 Lb[r * MT + c] = u;
             }
         }
         __syncthreads();
-        for (int e = tid; e < nbh * (cnt - 1); e += NT) {
-            const int b = e / (cnt - 1), r = c + 1 + (e - b * (cnt - 1));
+        for (int e = tid; e < nbh * below; e += NT) {
+            const int b = e / below, r = c + 1 + (e - b * below);
             z2 *p = sL + (b * MT + r) * MT + c;
             *p = zscale(*p, sInv[b * MT + c]);
         }
@@ -163,25 +169,44 @@ __global__ void __launch_bounds__(256) k_factor_odd(LevelArgs a) {
         a.Z[(t0 + b) * (int64_t)(m * m2) + rem] = sZ[(b * MT + r) * LDZ + c];
     }
 
-    // lower triangle of Z^H Z, one item per entry (uniform cost: the diagonal
-    // entries take the same complex path and drop their imaginary part)
-    const int nh = m2 * (m2 + 1) / 2;
-    for (int e = tid; e < nbh * nh; e += NT) {
-        const int b = e / nh, f = e - b * nh;
-        const int p = tri_row(f), q = f - p * (p + 1) / 2;
-        const int64_t t = t0 + b, pos = 2 * t;
-        const bool hasL = pos >= 1, hasR = pos + 1 < a.Nl;
-        const int kind = (p < m) ? 0 : (q >= m ? 1 : 2);  // P^H P, Q^H Q, Q^H P
-        if (kind == 0 ? !hasL : (kind == 1 ? !hasR : !(hasL && hasR))) continue;
-        const z2 *Zb = sZ + b * MT * LDZ;
-        z2 acc = zmk(0.0, 0.0);
+    // Lower triangle of Z^H Z.  The 2m real diagonal entries of each block
+    // come first, in warps of their own (2 FMA per term instead of 4), then
+    // the strictly lower entries (one complex dot product of length m each).
+    // Parts: rows/cols < m give P^H P, both >= m give Q^H Q, row >= m > col
+    // gives Q^H P = -F.
+    const int ndiag = nbh * m2, dpadh = (ndiag + 31) & ~31, noff = m2 * (m2 - 1) / 2;
+    for (int e = tid; e < dpadh + nbh * noff; e += NT) {
+        if (e < ndiag) {
+            const int b = e / m2, p = e - b * m2;
+            const int64_t t = t0 + b, pos = 2 * t;
+            if (p < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
+            const z2 *Zb = sZ + b * MT * LDZ;
+            double d = 0.0;
 #pragma unroll
-        for (int s = 0; s < MT; ++s)
-            if (s < m) zmac_ca(acc, Zb[s * LDZ + p], Zb[s * LDZ + q]);
-        if (p == q) acc.y = 0.0;
-        if (kind == 0) a.Wl[t * mm + p * m + q] = acc;
-        else if (kind == 1) a.Wr[t * mm + (p - m) * m + (q - m)] = acc;
-        else a.Bn[(t - 1) * mm + (p - m) * m + q] = zneg(acc);
+            for (int s = 0; s < MT; ++s)
+                if (s < m) {
+                    const z2 v = Zb[s * LDZ + p];
+                    d = fma(v.x, v.x, d);
+                    d = fma(v.y, v.y, d);
+                }
+            if (p < m) a.Wl[t * mm + p * m + p] = zmk(d, 0.0);
+            else a.Wr[t * mm + (p - m) * m + (p - m)] = zmk(d, 0.0);
+        } else if (e >= dpadh) {
+            const int e2 = e - dpadh, b = e2 / noff, g = e2 - b * noff;
+            const int p = tri_row(g) + 1, q = g - p * (p - 1) / 2;   // p > q
+            const int64_t t = t0 + b, pos = 2 * t;
+            const bool hasL = pos >= 1, hasR = pos + 1 < a.Nl;
+            const int kind = (p < m) ? 0 : (q >= m ? 1 : 2);  // P^H P, Q^H Q, Q^H P
+            if (kind == 0 ? !hasL : (kind == 1 ? !hasR : !(hasL && hasR))) continue;
+            const z2 *Zb = sZ + b * MT * LDZ;
+            z2 acc = zmk(0.0, 0.0);
+#pragma unroll
+            for (int s = 0; s < MT; ++s)
+                if (s < m) zmac_ca(acc, Zb[s * LDZ + p], Zb[s * LDZ + q]);
+            if (kind == 0) a.Wl[t * mm + p * m + q] = acc;
+            else if (kind == 1) a.Wr[t * mm + (p - m) * m + (q - m)] = acc;
+            else a.Bn[(t - 1) * mm + (p - m) * m + q] = zneg(acc);
+        }
     }
 }
 
