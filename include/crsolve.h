@@ -160,10 +160,12 @@ const char *crsolve_strerror(int code);
 /* ---- instrumentation (the paper has no counterpart; used by the benchmark) ---- */
 
 enum crsolve_kernel_kind {
-    CRSOLVE_K_FACTOR_ODD = 0,      /* Cholesky + P, Q + Z^H Z of a level's odd blocks */
-    CRSOLVE_K_FACTOR_EVEN = 1,     /* next level's diagonal blocks */
-    CRSOLVE_K_SOLVE_DOWN_ODD = 2,  /* r = L^{-1} y and Z^H r of a level's odd blocks */
-    CRSOLVE_K_SOLVE_DOWN_EVEN = 3, /* next level's right-hand side */
+    CRSOLVE_K_FACTOR_ODD = 0,      /* Cholesky + P, Q + Z^H Z of a level's odd blocks, and
+                                      the next level's blocks inside each CTA */
+    CRSOLVE_K_FACTOR_FIX = 1,      /* next level's blocks on CTA boundaries */
+    CRSOLVE_K_SOLVE_DOWN_ODD = 2,  /* r = L^{-1} y, Z^H r and the next level's right-hand
+                                      side inside each CTA */
+    CRSOLVE_K_SOLVE_DOWN_FIX = 3,  /* next level's right-hand side on CTA boundaries */
     CRSOLVE_K_SOLVE_UP = 4,        /* back-substitution of a level */
     CRSOLVE_K_ADJOINT = 5,         /* gA, gB outer products */
     CRSOLVE_K_NANFILL = 6          /* NaN fill of gA / gB after a breakdown */
@@ -172,7 +174,7 @@ enum crsolve_kernel_kind {
 typedef struct {
     int32_t kind;    /* crsolve_kernel_kind */
     int32_t level;   /* reduction level (0 for kernels outside the sweep) */
-    int64_t units;   /* blocks the launch processed (odd or even blocks of the level) */
+    int64_t units;   /* odd blocks the launch processed (CTA boundaries for the fix-ups) */
     float ms;        /* duration between CUDA events recorded around the launch */
 } crsolve_kernel_time;
 
@@ -187,6 +189,17 @@ int crsolve_timing_read(crsolve_plan p, crsolve_kernel_time *out, int32_t cap, i
 
 /* Kernels this plan has launched since it was created. */
 int crsolve_launch_count(crsolve_plan p, int64_t *count);
+
+/*
+ * Tile shape of block-size class mt (4, 8, 16, 32 or 64; a plan with block
+ * size m uses the smallest class >= m): odd blocks per CTA of the factor and
+ * of the solve kernels, right-hand-side columns per solve CTA, and threads
+ * per CTA (a multiple of 32, at most 256).  Process-wide, for later launches.
+ * crsolve_tile_set returns CRSOLVE_EINVAL for a shape that is out of range or
+ * does not fit in the current device's shared memory.
+ */
+int crsolve_tile_set(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc, int32_t threads);
+int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads);
 
 /* Number of levels of the plan (floor(log2 N) + 1) and the level sizes. */
 int crsolve_plan_levels(crsolve_plan p, int32_t *nlev, int64_t *sizes /* [nlev] or NULL */);

@@ -44,7 +44,7 @@ class CrsolveKernelTime(ctypes.Structure):
                 ("units", ctypes.c_int64), ("ms", ctypes.c_float)]
 
 
-KERNEL_KINDS = {0: "factor_odd", 1: "factor_even", 2: "solve_down_odd", 3: "solve_down_even",
+KERNEL_KINDS = {0: "factor_odd", 1: "factor_fix", 2: "solve_down_odd", 3: "solve_down_fix",
                 4: "solve_up", 5: "adjoint_outer", 6: "nan_fill"}
 
 SIGNATURES = {
@@ -63,6 +63,8 @@ SIGNATURES = {
     "crsolve_timing_enable": (ctypes.c_int, [_P, _I32]),
     "crsolve_timing_read": (ctypes.c_int, [_P, ctypes.POINTER(CrsolveKernelTime), _I32, ctypes.POINTER(_I32)]),
     "crsolve_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "crsolve_tile_set": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32]),
+    "crsolve_tile_get": (ctypes.c_int, [_I32] + [ctypes.POINTER(_I32)] * 4),
 }
 
 

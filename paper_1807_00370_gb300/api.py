@@ -16,7 +16,8 @@ from . import _native as nat
 __all__ = ["Plan", "crsolve_plan_create", "crsolve_factor", "crsolve_solve", "crsolve_backward",
            "crsolve_info_get", "crsolve_solve_host", "crsolve_plan_levels",
            "crsolve_debug_level_system", "crsolve_timing_enable", "crsolve_timing_read",
-           "crsolve_launch_count", "solve", "CRSolveFn", "NotPositiveDefinite"]
+           "crsolve_launch_count", "crsolve_tile_set", "crsolve_tile_get", "solve", "CRSolveFn",
+           "NotPositiveDefinite"]
 
 
 class NotPositiveDefinite(RuntimeError):
@@ -199,6 +200,16 @@ def crsolve_launch_count(plan: Plan) -> int:
     c = ctypes.c_int64()
     nat.check(nat.load().crsolve_launch_count(plan.handle, ctypes.byref(c)), "crsolve_launch_count")
     return int(c.value)
+
+
+def crsolve_tile_set(mt: int, nb_factor: int, nb_solve: int, kc: int, threads: int) -> None:
+    nat.check(nat.load().crsolve_tile_set(mt, nb_factor, nb_solve, kc, threads), "crsolve_tile_set")
+
+
+def crsolve_tile_get(mt: int):
+    v = [ctypes.c_int32() for _ in range(4)]
+    nat.check(nat.load().crsolve_tile_get(mt, *[ctypes.byref(x) for x in v]), "crsolve_tile_get")
+    return tuple(int(x.value) for x in v)
 
 
 def solve(A: torch.Tensor, B: torch.Tensor | None, y: torch.Tensor, check: bool = True) -> torch.Tensor:

@@ -78,14 +78,12 @@ struct LevelArgs {
     z2 *L;              // [no][m][m]  Cholesky factors (lower, upper zero)
     double *inv;        // [no][m]     1 / diag(L)
     z2 *Z;              // [no][m][2m] [P | Q] = L^{-1} [B_{i-1} | B_i^H]
-    z2 *Wl;             // [no][m][m]  P^H P (lower)   scratch
-    z2 *Wr;             // [no][m][m]  Q^H Q (lower)   scratch
+    z2 *Wbd;            // [ncta][m][m] P^H P of each CTA's first odd block (CTA-boundary scratch)
     z2 *An;             // [ne][m][m]  next level diagonal blocks
     z2 *Bn;             // [ne-1][m][m] next level sub-diagonal blocks
     const z2 *y;        // [Nl][m][k]  level right-hand side
     z2 *r;              // [no][m][k]  L^{-1} y_odd
-    z2 *cl;             // [no][m][k]  P^H r  (goes to the left even block)   scratch
-    z2 *cr;             // [no][m][k]  Q^H r  (goes to the right even block)  scratch
+    z2 *cbd;            // [ncta][m][k] P^H r of each CTA's first odd block (CTA-boundary scratch)
     z2 *yn;             // [ne][m][k]  next level right-hand side
     const z2 *xn;       // [ne][m][k]  next level solution
     z2 *x;              // [Nl][m][k]  level solution

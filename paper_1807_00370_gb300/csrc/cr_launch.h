@@ -15,21 +15,31 @@ struct TileShape {
 };
 
 TileShape tile_shape(int mt);
+bool set_tile_shape(int mt, const TileShape &ts, size_t smem_limit);
 int pick_mt(int m);                                  // 4, 8, 16, 32, 64 or 0
 size_t factor_smem_bytes(int mt, int nb);
-size_t solve_smem_bytes(int mt, int nb, int kc, bool up);
+size_t solve_smem_bytes(int mt, int nb, int kc, int panels);
 cudaError_t prepare_kernels(int mt);                 // raise shared-memory limits once per device
 
-// Factor sweep of one level: the odd-block kernel (Cholesky, P, Q, Z^H Z),
-// then the even-block kernel (the next level's diagonal blocks).
-cudaError_t launch_factor_odd(int mt, const LevelArgs &a, int nsm, cudaStream_t s);
-cudaError_t launch_factor_even(const LevelArgs &a, int nsm, cudaStream_t s);
-// Down sweep of one level: r and Z^H r on the odd blocks, then the next
-// level's right-hand side on the even blocks.
-cudaError_t launch_solve_down_odd(int mt, const LevelArgs &a, int nsm, cudaStream_t s);
-cudaError_t launch_solve_down_even(const LevelArgs &a, int nsm, cudaStream_t s);
+// Odd blocks per CTA of a level with `no` odd blocks (the tile's maximum,
+// shrunk on small levels so that about two CTAs land on every SM), and the
+// right-hand-side chunk width of the solve kernels.
+int factor_nb(int mt, int64_t no, int nsm);
+int solve_nb(int mt, int64_t no, int nsm);
+int solve_kc(int mt, int k);
+__host__ __device__ inline int64_t num_ctas(int64_t no, int nb) { return (no + nb - 1) / nb; }
+
+// Factor sweep of one level (a.nb set by factor_nb): the odd-block kernel
+// (Cholesky, P, Q, Z^H Z, and the even blocks that lie inside its CTA), then
+// the fix-up of the even blocks on CTA boundaries.
+cudaError_t launch_factor_odd(int mt, const LevelArgs &a, cudaStream_t s);
+cudaError_t launch_factor_fix(const LevelArgs &a, int nsm, cudaStream_t s);
+// Down sweep of one level (a.nb, a.kc set): r, Z^H r and the next level's
+// right-hand side inside each CTA, then the CTA-boundary fix-up.
+cudaError_t launch_solve_down_odd(int mt, const LevelArgs &a, cudaStream_t s);
+cudaError_t launch_solve_down_fix(const LevelArgs &a, int nsm, cudaStream_t s);
 // Up sweep of one level (x of this level from the next level's x).
-cudaError_t launch_solve_up_level(int mt, const LevelArgs &a, int nsm, cudaStream_t s);
+cudaError_t launch_solve_up(int mt, const LevelArgs &a, cudaStream_t s);
 // Adjoint outer products gA, gB from x and gy.
 cudaError_t launch_adjoint_outer(int64_t N, int m, int k, const z2 *x, const z2 *gy, z2 *gA,
                                  z2 *gB, int nsm, cudaStream_t s);

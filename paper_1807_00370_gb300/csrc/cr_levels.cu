@@ -1,31 +1,39 @@
 // cr_levels.cu -- the per-level kernels of classic cyclic reduction in FP64.
 //
 // One level (Sec. 2, eq. Formulas; 0-based: odd block t at position 2t, even
-// block j' at 2j'+1):
-//   k_factor_odd   per odd block: Cholesky A_2t = L L^H with the breakdown
-//                  test, Z = [P | Q] = L^{-1} [B_{2t-1} | B_{2t}^H], and the
-//                  Hermitian product Z^H Z (Sec. 4's rule), whose three parts
-//                  are P^H P (to the left even block), Q^H Q (to the right
-//                  even block) and Q^H P (= -F, the next level's B).
-//   k_factor_even  per even block: V = A_{2j'+1} - Q^H Q(left) - P^H P(right).
-//   k_solve_down_* r = L^{-1} y_odd, then v = y_even - Q^H r(left) - P^H r(right).
-//   k_solve_up     x_odd = L^{-H}(r - P x_left - Q x_right); x_even copied.
+// block j at 2j+1, so odd t has the even blocks j = t-1 on its left and
+// j = t on its right):
+//   k_factor_odd     per odd block: Cholesky A_2t = L L^H with the breakdown
+//                    test, Z = [P | Q] = L^{-1} [B_{2t-1} | B_{2t}^H], and the
+//                    Hermitian product Z^H Z (Sec. 4's rule), whose parts are
+//                    Q^H Q (subtracted from the right even block), P^H P (from
+//                    the left even block) and Q^H P (= -F, the next level's B).
+//                    The even blocks whose two odd neighbours sit in the same
+//                    CTA are finished there: V_j = (A_2j+1 - Q^H Q) - P^H P.
+//   k_factor_fix     the even block on each CTA boundary: subtract the P^H P
+//                    that the next CTA left in a scratch buffer.
+//   k_solve_down_odd r = L^{-1} y_odd, v_j = (y_2j+1 - Q^H r) - P^H r, same
+//                    CTA split, and k_solve_down_fix for the boundaries.
+//   k_solve_up       x_odd = L^{-H}(r - P x_left - Q x_right); x_even copied.
 //
 // GPU mapping.  A CTA owns nb consecutive odd blocks and stages them in
 // shared memory.  Each phase is a list of equal-cost work items (a matrix
-// entry, a column of a triangular solve) spread over all threads of the CTA,
-// so that warps issue FP64 instructions with every lane active: on GB300 the
-// FP64 pipe (2 DFMA/clk/SM) is the bound of this path, and one warp per SM
-// sub-partition with a dependent chain already keeps it ~90% busy, so
-// occupancy matters little and lane utilisation and instruction count matter
-// most.
+// entry, a column of a triangular solve) spread over all threads of the CTA;
+// items of different cost (pivots, real diagonal entries) get warps of their
+// own.  On GB300 the FP64 pipe (2 DFMA/clk/SM) bounds this path and one warp
+// per SM sub-partition with a dependent chain already keeps it ~90% busy, so
+// lane utilisation and FP64 instruction count matter most, occupancy little.
 #include "cr_launch.h"
 
 namespace crs {
 
+// Packed lower-triangular storage in shared memory: entry (r, c), r >= c.
+__device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }
+template <int MT> struct Tri { static constexpr int n = MT * (MT + 1) / 2; };
+
 // --------------------------------------------------------------- helpers
 
-// z := L^{-1} z for one column z (shared memory, stride ld).
+// z := L^{-1} z for one column z (shared memory, stride ld); L packed lower.
 template <int MT>
 __device__ __forceinline__ void trsv_lower_col(const z2 *Lb, const double *ivb, z2 *col, int ld, int m) {
     if constexpr (MT <= 32) {
@@ -38,7 +46,7 @@ __device__ __forceinline__ void trsv_lower_col(const z2 *Lb, const double *ivb, 
             if (r < m) {
                 z2 acc = z[r];
 #pragma unroll
-                for (int s = 0; s < r; ++s) zmsub(acc, Lb[r * MT + s], z[s]);
+                for (int s = 0; s < r; ++s) zmsub(acc, Lb[tri(r, s)], z[s]);
                 z[r] = zscale(acc, ivb[r]);
             }
         }
@@ -48,16 +56,16 @@ __device__ __forceinline__ void trsv_lower_col(const z2 *Lb, const double *ivb, 
     } else {
         for (int r = 0; r < m; ++r) {
             z2 acc = col[r * ld];
-            for (int s = 0; s < r; ++s) zmsub(acc, Lb[r * MT + s], col[s * ld]);
+            for (int s = 0; s < r; ++s) zmsub(acc, Lb[tri(r, s)], col[s * ld]);
             col[r * ld] = zscale(acc, ivb[r]);
         }
     }
 }
 
-// z := L^{-H} z for one column z (shared memory, stride ld).
+// z := L^{-H} z for one column z (shared memory, stride ld); L packed lower.
 template <int MT>
 __device__ __forceinline__ void trsv_lower_h_col(const z2 *Lb, const double *ivb, z2 *col, int ld, int m) {
-    if constexpr (MT <= 32) {
+    if constexpr (MT <= 16) {
         z2 z[MT];
 #pragma unroll
         for (int r = 0; r < MT; ++r)
@@ -68,7 +76,7 @@ __device__ __forceinline__ void trsv_lower_h_col(const z2 *Lb, const double *ivb
                 z2 acc = z[r];
 #pragma unroll
                 for (int s = r + 1; s < MT; ++s)
-                    if (s < m) zmsub_ca(acc, Lb[s * MT + r], z[s]);
+                    if (s < m) zmsub_ca(acc, Lb[tri(s, r)], z[s]);
                 z[r] = zscale(acc, ivb[r]);
             }
         }
@@ -78,7 +86,7 @@ __device__ __forceinline__ void trsv_lower_h_col(const z2 *Lb, const double *ivb
     } else {
         for (int r = m - 1; r >= 0; --r) {
             z2 acc = col[r * ld];
-            for (int s = r + 1; s < m; ++s) zmsub_ca(acc, Lb[s * MT + r], col[s * ld]);
+            for (int s = r + 1; s < m; ++s) zmsub_ca(acc, Lb[tri(s, r)], col[s * ld]);
             col[r * ld] = zscale(acc, ivb[r]);
         }
     }
@@ -89,20 +97,29 @@ __device__ __forceinline__ void trsv_lower_h_col(const z2 *Lb, const double *ivb
 template <int MT>
 __global__ void __launch_bounds__(256) k_factor_odd(LevelArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int LDZ = 2 * MT;
+    constexpr int LDZ = 2 * MT, TRI = Tri<MT>::n;
     const int m = a.m, nb = a.nb, NT = blockDim.x, tid = threadIdx.x;
     const int mm = m * m, m2 = 2 * m;
     const int64_t t0 = (int64_t)blockIdx.x * nb;
     const int nbh = (int)min((int64_t)nb, a.no - t0);
-    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                          // [nb][MT][MT]
-    z2 *sZ = sL + (size_t)nb * MT * MT;                                  // [nb][MT][2MT]
+    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                        // [nb][TRI] L, later P^H P
+    z2 *sV = sL + (size_t)nb * TRI;                                    // [nb][TRI] even block t0+b
+    z2 *sZ = sV + (size_t)nb * TRI;                                    // [nb][MT][2MT] [P | Q]
     double *sInv = reinterpret_cast<double *>(sZ + (size_t)nb * MT * LDZ);  // [nb][MT]
 
-    // stage the lower triangle of A_2t, B_{2t-1} (P part) and B_{2t}^H (Q part)
+    // stage the lower triangles of A_2t and A_2t+1, B_{2t-1} (P part) and
+    // B_{2t}^H (Q part)
     for (int e = tid; e < nbh * mm; e += NT) {
         const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        const int64_t pos = 2 * (t0 + b);
-        sL[(b * MT + r) * MT + c] = (r >= c) ? a.A[pos * mm + rem] : zmk(0.0, 0.0);
+        const int64_t t = t0 + b, pos = 2 * t;
+        if (r >= c) {
+            sL[b * TRI + tri(r, c)] = a.A[pos * mm + rem];
+            if (t < a.ne) {
+                z2 v = a.A[(pos + 1) * mm + rem];
+                if (r == c) v.y = 0.0;
+                sV[b * TRI + tri(r, c)] = v;
+            }
+        }
         sZ[(b * MT + r) * LDZ + c] = (pos >= 1) ? a.B[(pos - 1) * mm + rem] : zmk(0.0, 0.0);
         sZ[(b * MT + c) * LDZ + m + r] = (pos + 1 < a.Nl) ? zconj(a.B[pos * mm + rem]) : zmk(0.0, 0.0);
     }
@@ -118,29 +135,29 @@ __global__ void __launch_bounds__(256) k_factor_odd(LevelArgs a) {
         for (int e = tid; e < dpad + nbh * below; e += NT) {
             if (e < nbh) {
                 const int b = e;
-                z2 *Lb = sL + b * MT * MT;
-                double d = Lb[c * MT + c].x;
+                z2 *Lb = sL + b * TRI;
+                double d = Lb[tri(c, c)].x;
                 for (int s = 0; s < c; ++s) {
-                    const z2 l = Lb[c * MT + s];
+                    const z2 l = Lb[tri(c, s)];
                     d = fma(-l.x, l.x, d);
                     d = fma(-l.y, l.y, d);
                 }
                 if (!(d > 0.0)) report_fail(a.status, a.level, 2 * (t0 + b) + 1);
                 const double iv = rsqrt(d);
                 sInv[b * MT + c] = iv;
-                Lb[c * MT + c] = zmk(d * iv, 0.0);
+                Lb[tri(c, c)] = zmk(d * iv, 0.0);
             } else if (e >= dpad) {
                 const int e2 = e - dpad, b = e2 / below, r = c + 1 + (e2 - b * below);
-                z2 *Lb = sL + b * MT * MT;
-                z2 u = Lb[r * MT + c];
-                for (int s = 0; s < c; ++s) zmsub_cb(u, Lb[r * MT + s], Lb[c * MT + s]);
-                Lb[r * MT + c] = u;
+                z2 *Lb = sL + b * TRI;
+                z2 u = Lb[tri(r, c)];
+                for (int s = 0; s < c; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(c, s)]);
+                Lb[tri(r, c)] = u;
             }
         }
         __syncthreads();
         for (int e = tid; e < nbh * below; e += NT) {
             const int b = e / below, r = c + 1 + (e - b * below);
-            z2 *p = sL + (b * MT + r) * MT + c;
+            z2 *p = sL + b * TRI + tri(r, c);
             *p = zscale(*p, sInv[b * MT + c]);
         }
         __syncthreads();
@@ -151,14 +168,14 @@ __global__ void __launch_bounds__(256) k_factor_odd(LevelArgs a) {
         const int b = e / m2, col = e - b * m2;
         const int64_t pos = 2 * (t0 + b);
         if (col < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
-        trsv_lower_col<MT>(sL + b * MT * MT, sInv + b * MT, sZ + b * MT * LDZ + col, LDZ, m);
+        trsv_lower_col<MT>(sL + b * TRI, sInv + b * MT, sZ + b * MT * LDZ + col, LDZ, m);
     }
     __syncthreads();
 
     // keep L, 1/diag(L) and Z for the solves
     for (int e = tid; e < nbh * mm; e += NT) {
         const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        a.L[(t0 + b) * mm + rem] = (r >= c) ? sL[(b * MT + r) * MT + c] : zmk(0.0, 0.0);
+        a.L[(t0 + b) * mm + rem] = (r >= c) ? sL[b * TRI + tri(r, c)] : zmk(0.0, 0.0);
     }
     for (int e = tid; e < nbh * m; e += NT) {
         const int b = e / m, r = e - b * m;
@@ -168,34 +185,36 @@ __global__ void __launch_bounds__(256) k_factor_odd(LevelArgs a) {
         const int b = e / (m * m2), rem = e - b * (m * m2), r = rem / m2, c = rem - r * m2;
         a.Z[(t0 + b) * (int64_t)(m * m2) + rem] = sZ[(b * MT + r) * LDZ + c];
     }
+    __syncthreads();
 
-    // Lower triangle of Z^H Z.  The 2m real diagonal entries of each block
-    // come first, in warps of their own (2 FMA per term instead of 4), then
-    // the strictly lower entries (one complex dot product of length m each).
-    // Parts: rows/cols < m give P^H P, both >= m give Q^H Q, row >= m > col
-    // gives Q^H P = -F.
+    // Lower triangle of Z^H Z, one item per entry.  The 2m real diagonal
+    // entries of each block come first, in warps of their own (2 FMA per
+    // term instead of 4).  Parts: Q^H Q is subtracted from the right even
+    // block V_t in place, P^H P is kept in sW (the L buffer, free now) for the
+    // left even block, and Q^H P = -F goes to the next level's B.
+    z2 *sW = sL;
     const int ndiag = nbh * m2, dpadh = (ndiag + 31) & ~31, noff = m2 * (m2 - 1) / 2;
     for (int e = tid; e < dpadh + nbh * noff; e += NT) {
         if (e < ndiag) {
             const int b = e / m2, p = e - b * m2;
-            const int64_t t = t0 + b, pos = 2 * t;
-            if (p < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
-            const z2 *Zb = sZ + b * MT * LDZ;
+            const int64_t t = t0 + b;
+            if (p < m ? (t == 0) : (2 * t + 1 >= a.Nl)) continue;
+            const z2 *Zb = sZ + b * MT * LDZ + p;
             double d = 0.0;
 #pragma unroll
             for (int s = 0; s < MT; ++s)
                 if (s < m) {
-                    const z2 v = Zb[s * LDZ + p];
+                    const z2 v = Zb[s * LDZ];
                     d = fma(v.x, v.x, d);
                     d = fma(v.y, v.y, d);
                 }
-            if (p < m) a.Wl[t * mm + p * m + p] = zmk(d, 0.0);
-            else a.Wr[t * mm + (p - m) * m + (p - m)] = zmk(d, 0.0);
+            if (p < m) sW[b * TRI + tri(p, p)] = zmk(d, 0.0);
+            else sV[b * TRI + tri(p - m, p - m)].x -= d;
         } else if (e >= dpadh) {
             const int e2 = e - dpadh, b = e2 / noff, g = e2 - b * noff;
             const int p = tri_row(g) + 1, q = g - p * (p - 1) / 2;   // p > q
-            const int64_t t = t0 + b, pos = 2 * t;
-            const bool hasL = pos >= 1, hasR = pos + 1 < a.Nl;
+            const int64_t t = t0 + b;
+            const bool hasL = t >= 1, hasR = 2 * t + 1 < a.Nl;
             const int kind = (p < m) ? 0 : (q >= m ? 1 : 2);  // P^H P, Q^H Q, Q^H P
             if (kind == 0 ? !hasL : (kind == 1 ? !hasR : !(hasL && hasR))) continue;
             const z2 *Zb = sZ + b * MT * LDZ;
@@ -203,26 +222,47 @@ __global__ void __launch_bounds__(256) k_factor_odd(LevelArgs a) {
 #pragma unroll
             for (int s = 0; s < MT; ++s)
                 if (s < m) zmac_ca(acc, Zb[s * LDZ + p], Zb[s * LDZ + q]);
-            if (kind == 0) a.Wl[t * mm + p * m + q] = acc;
-            else if (kind == 1) a.Wr[t * mm + (p - m) * m + (q - m)] = acc;
-            else a.Bn[(t - 1) * mm + (p - m) * m + q] = zneg(acc);
+            if (kind == 0) {
+                sW[b * TRI + tri(p, q)] = acc;
+            } else if (kind == 1) {
+                z2 &v = sV[b * TRI + tri(p - m, q - m)];
+                v = zsub(v, acc);
+            } else {
+                a.Bn[(t - 1) * mm + (p - m) * m + q] = zneg(acc);
+            }
         }
+    }
+    __syncthreads();
+
+    // V_j = (A_2j+1 - Q^H Q) - P^H P for the even blocks j = t0 + b.  The
+    // CTA's last one misses its right neighbour's P^H P when that neighbour
+    // starts the next CTA (k_factor_fix completes it); the CTA's first P^H P
+    // goes to the boundary buffer for the previous CTA.
+    const int nl = m * (m + 1) / 2;
+    for (int e = tid; e < nbh * nl; e += NT) {
+        const int b = e / nl, f = e - b * nl, r = tri_row(f), c = f - r * (r + 1) / 2;
+        const int64_t j = t0 + b;
+        if (b == 0 && j >= 1) a.Wbd[(int64_t)blockIdx.x * mm + r * m + c] = sW[f];
+        if (j >= a.ne) continue;
+        z2 v = sV[b * TRI + f];
+        if (b + 1 < nbh) v = zsub(v, sW[(b + 1) * TRI + f]);
+        a.An[j * mm + r * m + c] = v;
+        if (r != c) a.An[j * mm + c * m + r] = zconj(v);
     }
 }
 
-// ----------------------------------------------------------- factor: even
-
-__global__ void __launch_bounds__(256) k_factor_even(LevelArgs a) {
+// Even block j = c * nb - 1 on the boundary between CTA c-1 and CTA c of the
+// odd kernel: subtract P^H P of odd block c * nb, left by CTA c in Wbd[c].
+__global__ void __launch_bounds__(256) k_factor_fix(LevelArgs a) {
     const int m = a.m, mm = m * m, nl = m * (m + 1) / 2;
-    const int64_t total = a.ne * nl;
+    const int64_t ncta = num_ctas(a.no, a.nb), total = (ncta - 1) * nl;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = e / nl;
-        const int f = (int)(e - j * nl);
+        const int64_t c = 1 + e / nl;
+        const int f = (int)(e - (c - 1) * nl);
         const int p = tri_row(f), q = f - p * (p + 1) / 2;
-        z2 v = a.A[(2 * j + 1) * mm + p * m + q];
-        v = zsub(v, a.Wr[j * mm + p * m + q]);                       // Q^H Q of odd block j (left)
-        if (j + 1 < a.no) v = zsub(v, a.Wl[(j + 1) * mm + p * m + q]);  // P^H P of odd block j+1 (right)
+        const int64_t j = c * a.nb - 1;
+        z2 v = zsub(a.An[j * mm + p * m + q], a.Wbd[c * mm + p * m + q]);
         if (p == q) v.y = 0.0;
         a.An[j * mm + p * m + q] = v;
         if (p != q) a.An[j * mm + q * m + p] = zconj(v);
@@ -234,18 +274,21 @@ __global__ void __launch_bounds__(256) k_factor_even(LevelArgs a) {
 template <int MT>
 __global__ void __launch_bounds__(256) k_solve_down_odd(LevelArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TRI = Tri<MT>::n;
     const int m = a.m, k = a.k, nb = a.nb, kc = a.kc, NT = blockDim.x, tid = threadIdx.x;
     const int mm = m * m, m2 = 2 * m, mk = m * k;
     const int c0 = blockIdx.y * kc, kw = min(kc, k - c0);
     const int64_t t0 = (int64_t)blockIdx.x * nb;
     const int nbh = (int)min((int64_t)nb, a.no - t0);
-    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                           // [nb][MT][MT]
-    z2 *sR = sL + (size_t)nb * MT * MT;                                   // [nb][MT][kc]
-    double *sInv = reinterpret_cast<double *>(sR + (size_t)nb * MT * kc);  // [nb][MT]
+    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                           // [nb][TRI]
+    z2 *sR = sL + (size_t)nb * TRI;                                       // [nb][MT][kc] r of odd t0+b
+    z2 *sV = sR + (size_t)nb * MT * kc;                                   // [nb][MT][kc] v of even t0+b
+    z2 *sW = sV + (size_t)nb * MT * kc;                                   // [nb][MT][kc] P^H r of odd t0+b
+    double *sInv = reinterpret_cast<double *>(sW + (size_t)nb * MT * kc);  // [nb][MT]
 
     for (int e = tid; e < nbh * mm; e += NT) {
         const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        sL[(b * MT + r) * MT + c] = a.L[(t0 + b) * mm + rem];
+        if (r >= c) sL[b * TRI + tri(r, c)] = a.L[(t0 + b) * mm + rem];
     }
     for (int e = tid; e < nbh * m; e += NT) {
         const int b = e / m, r = e - b * m;
@@ -253,13 +296,15 @@ __global__ void __launch_bounds__(256) k_solve_down_odd(LevelArgs a) {
     }
     for (int e = tid; e < nbh * m * kw; e += NT) {
         const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
-        sR[(b * MT + r) * kc + c] = a.y[(2 * (t0 + b)) * mk + r * k + c0 + c];
+        const int64_t t = t0 + b;
+        sR[(b * MT + r) * kc + c] = a.y[(2 * t) * mk + r * k + c0 + c];
+        if (t < a.ne) sV[(b * MT + r) * kc + c] = a.y[(2 * t + 1) * mk + r * k + c0 + c];
     }
     __syncthreads();
 
     for (int e = tid; e < nbh * kw; e += NT) {
         const int b = e / kw, c = e - b * kw;
-        trsv_lower_col<MT>(sL + b * MT * MT, sInv + b * MT, sR + b * MT * kc + c, kc, m);
+        trsv_lower_col<MT>(sL + b * TRI, sInv + b * MT, sR + b * MT * kc + c, kc, m);
     }
     __syncthreads();
 
@@ -267,31 +312,45 @@ __global__ void __launch_bounds__(256) k_solve_down_odd(LevelArgs a) {
         const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
         a.r[(t0 + b) * mk + r * k + c0 + c] = sR[(b * MT + r) * kc + c];
     }
-    // Z^H r: rows p < m give P^H r (left even block), rows p >= m give Q^H r (right)
+    // Z^H r: rows p < m give P^H r (kept in sW for the left even block), rows
+    // p >= m give Q^H r (subtracted from the right even block in place)
     for (int e = tid; e < nbh * kw * m2; e += NT) {
         const int b = e / (kw * m2), rem = e - b * (kw * m2), c = rem / m2, p = rem - c * m2;
-        const int64_t t = t0 + b, pos = 2 * t;
-        if (p < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
-        const z2 *Zt = a.Z + t * (int64_t)(m * m2);
+        const int64_t t = t0 + b;
+        if (p < m ? (t == 0) : (2 * t + 1 >= a.Nl)) continue;
+        const z2 *Zt = a.Z + t * (int64_t)(m * m2) + p;
         const z2 *Rb = sR + b * MT * kc + c;
         z2 acc = zmk(0.0, 0.0);
 #pragma unroll
         for (int s = 0; s < MT; ++s)
-            if (s < m) zmac_ca(acc, __ldg(Zt + s * m2 + p), Rb[s * kc]);
-        if (p < m) a.cl[t * mk + p * k + c0 + c] = acc;
-        else a.cr[t * mk + (p - m) * k + c0 + c] = acc;
+            if (s < m) zmac_ca(acc, __ldg(Zt + s * m2), Rb[s * kc]);
+        if (p < m) {
+            sW[(b * MT + p) * kc + c] = acc;
+        } else {
+            z2 &v = sV[(b * MT + p - m) * kc + c];
+            v = zsub(v, acc);
+        }
+    }
+    __syncthreads();
+    // v_j = (y_2j+1 - Q^H r) - P^H r; the CTA's first P^H r goes to the boundary buffer
+    for (int e = tid; e < nbh * m * kw; e += NT) {
+        const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
+        const int64_t j = t0 + b;
+        if (b == 0 && j >= 1) a.cbd[(int64_t)blockIdx.x * mk + r * k + c0 + c] = sW[r * kc + c];
+        if (j >= a.ne) continue;
+        z2 v = sV[(b * MT + r) * kc + c];
+        if (b + 1 < nbh) v = zsub(v, sW[((b + 1) * MT + r) * kc + c]);
+        a.yn[j * mk + r * k + c0 + c] = v;
     }
 }
 
-__global__ void __launch_bounds__(256) k_solve_down_even(LevelArgs a) {
-    const int64_t mk = (int64_t)a.m * a.k, total = a.ne * mk;
+// Even block j = c * nb - 1 on a CTA boundary: subtract P^H r of odd block c * nb.
+__global__ void __launch_bounds__(256) k_solve_down_fix(LevelArgs a) {
+    const int64_t mk = (int64_t)a.m * a.k, ncta = num_ctas(a.no, a.nb), total = (ncta - 1) * mk;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
          e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t j = e / mk, rem = e - j * mk;
-        z2 v = a.y[(2 * j + 1) * mk + rem];
-        v = zsub(v, a.cr[j * mk + rem]);                          // Q^H r of odd block j (left)
-        if (j + 1 < a.no) v = zsub(v, a.cl[(j + 1) * mk + rem]);  // P^H r of odd block j+1 (right)
-        a.yn[j * mk + rem] = v;
+        const int64_t c = 1 + e / mk, rem = e - (c - 1) * mk, j = c * a.nb - 1;
+        a.yn[j * mk + rem] = zsub(a.yn[j * mk + rem], a.cbd[c * mk + rem]);
     }
 }
 
@@ -300,13 +359,14 @@ __global__ void __launch_bounds__(256) k_solve_down_even(LevelArgs a) {
 template <int MT>
 __global__ void __launch_bounds__(256) k_solve_up(LevelArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr int TRI = Tri<MT>::n;
     const int m = a.m, k = a.k, nb = a.nb, kc = a.kc, NT = blockDim.x, tid = threadIdx.x;
     const int mm = m * m, m2 = 2 * m, mk = m * k;
     const int c0 = blockIdx.y * kc, kw = min(kc, k - c0);
     const int64_t t0 = (int64_t)blockIdx.x * nb;
     const int nbh = (int)min((int64_t)nb, a.no - t0);
-    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                                // [nb][MT][MT]
-    z2 *sW = sL + (size_t)nb * MT * MT;                                        // [nb][MT][kc]
+    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                                // [nb][TRI]
+    z2 *sW = sL + (size_t)nb * TRI;                                            // [nb][MT][kc]
     z2 *sX = sW + (size_t)nb * MT * kc;                                        // [nb][2MT][kc]
     double *sInv = reinterpret_cast<double *>(sX + (size_t)nb * 2 * MT * kc);  // [nb][MT]
 
@@ -324,7 +384,7 @@ __global__ void __launch_bounds__(256) k_solve_up(LevelArgs a) {
 
     for (int e = tid; e < nbh * mm; e += NT) {
         const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        sL[(b * MT + r) * MT + c] = a.L[(t0 + b) * mm + rem];
+        if (r >= c) sL[b * TRI + tri(r, c)] = a.L[(t0 + b) * mm + rem];
     }
     for (int e = tid; e < nbh * m; e += NT) {
         const int b = e / m, r = e - b * m;
@@ -359,7 +419,7 @@ __global__ void __launch_bounds__(256) k_solve_up(LevelArgs a) {
     // x_odd = L^{-H} w
     for (int e = tid; e < nbh * kw; e += NT) {
         const int b = e / kw, c = e - b * kw;
-        trsv_lower_h_col<MT>(sL + b * MT * MT, sInv + b * MT, sW + b * MT * kc + c, kc, m);
+        trsv_lower_h_col<MT>(sL + b * TRI, sInv + b * MT, sW + b * MT * kc + c, kc, m);
     }
     __syncthreads();
     for (int e = tid; e < nbh * m * kw; e += NT) {
@@ -416,15 +476,41 @@ __global__ void k_nan_if_failed(z2 *x, int64_t n, const unsigned long long *stat
 
 // ------------------------------------------------------------- host side
 
-TileShape tile_shape(int mt) {
+// Default tile shapes per block-size class; crsolve_tile_set overrides them.
+static TileShape g_tiles[5] = {
+    {32, 32, 32, 256},  // MT = 4
+    {16, 16, 16, 256},  // MT = 8
+    {4, 8, 16, 256},    // MT = 16
+    {2, 2, 32, 256},    // MT = 32
+    {1, 1, 32, 256},    // MT = 64
+};
+
+static int mt_slot(int mt) {
     switch (mt) {
-        case 4: return {32, 32, 32, 256};
-        case 8: return {16, 16, 16, 256};
-        case 16: return {4, 8, 16, 256};
-        case 32: return {2, 2, 32, 256};
-        case 64: return {1, 1, 32, 256};
-        default: return {0, 0, 0, 0};
+        case 4: return 0;
+        case 8: return 1;
+        case 16: return 2;
+        case 32: return 3;
+        case 64: return 4;
+        default: return -1;
     }
+}
+
+TileShape tile_shape(int mt) {
+    const int i = mt_slot(mt);
+    return i < 0 ? TileShape{0, 0, 0, 0} : g_tiles[i];
+}
+
+bool set_tile_shape(int mt, const TileShape &ts, size_t smem_limit) {
+    const int i = mt_slot(mt);
+    if (i < 0 || ts.nb_factor < 1 || ts.nb_solve < 1 || ts.kc_max < 1 || ts.threads < 32 ||
+        ts.threads > 256 || ts.threads % 32)
+        return false;
+    if (factor_smem_bytes(mt, ts.nb_factor) > smem_limit ||
+        solve_smem_bytes(mt, ts.nb_solve, ts.kc_max, 3) > smem_limit)
+        return false;
+    g_tiles[i] = ts;
+    return true;
 }
 
 int pick_mt(int m) {
@@ -436,46 +522,57 @@ int pick_mt(int m) {
     return 0;
 }
 
+// Per block: packed L (later P^H P) and packed V, Z = [P | Q], 1/diag(L).
 size_t factor_smem_bytes(int mt, int nb) {
-    return (size_t)nb * (3 * (size_t)mt * mt * sizeof(z2) + (size_t)mt * sizeof(double));
+    const size_t tri = (size_t)mt * (mt + 1) / 2;
+    return (size_t)nb * ((2 * tri + 2 * (size_t)mt * mt) * sizeof(z2) + (size_t)mt * sizeof(double));
 }
 
-size_t solve_smem_bytes(int mt, int nb, int kc, bool up) {
-    return (size_t)nb * ((size_t)mt * mt * sizeof(z2) + (size_t)mt * kc * sizeof(z2) * (up ? 3 : 1) +
-                         (size_t)mt * sizeof(double));
+// Per block: packed L, `panels` right-hand-side panels of MT x kc (3 down, 3 up), 1/diag(L).
+size_t solve_smem_bytes(int mt, int nb, int kc, int panels) {
+    const size_t tri = (size_t)mt * (mt + 1) / 2;
+    return (size_t)nb * (tri * sizeof(z2) + (size_t)mt * kc * sizeof(z2) * panels + (size_t)mt * sizeof(double));
 }
 
+// Allow every kernel the device's full opt-in shared memory, so that any
+// tile shape that set_tile_shape accepted can launch.
 template <int MT>
-static cudaError_t prepare_mt() {
-    const TileShape ts = tile_shape(MT);
+static cudaError_t prepare_mt(int smem_optin) {
     cudaError_t e;
-    e = cudaFuncSetAttribute(k_factor_odd<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)factor_smem_bytes(MT, ts.nb_factor));
+    e = cudaFuncSetAttribute(k_factor_odd<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_solve_down_odd<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)solve_smem_bytes(MT, ts.nb_solve, ts.kc_max, false));
+    e = cudaFuncSetAttribute(k_solve_down_odd<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_solve_up<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)solve_smem_bytes(MT, ts.nb_solve, ts.kc_max, true));
+    return cudaFuncSetAttribute(k_solve_up<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
 }
 
 cudaError_t prepare_kernels(int mt) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return e;
     switch (mt) {
-        case 4: return prepare_mt<4>();
-        case 8: return prepare_mt<8>();
-        case 16: return prepare_mt<16>();
-        case 32: return prepare_mt<32>();
-        case 64: return prepare_mt<64>();
+        case 4: return prepare_mt<4>(optin);
+        case 8: return prepare_mt<8>(optin);
+        case 16: return prepare_mt<16>(optin);
+        case 32: return prepare_mt<32>(optin);
+        case 64: return prepare_mt<64>(optin);
         default: return cudaErrorInvalidValue;
     }
 }
 
-// Odd blocks per CTA for a level with `no` odd blocks: the tile's maximum,
-// shrunk on small levels so that about two CTAs land on every SM.
 static int level_nb(int nb_max, int64_t no, int nsm) {
     int64_t want = (no + 2 * (int64_t)nsm - 1) / (2 * (int64_t)nsm);
     if (want < 1) want = 1;
     return (int)(want < nb_max ? want : nb_max);
+}
+
+int factor_nb(int mt, int64_t no, int nsm) { return level_nb(tile_shape(mt).nb_factor, no, nsm); }
+int solve_nb(int mt, int64_t no, int nsm) { return level_nb(tile_shape(mt).nb_solve, no, nsm); }
+int solve_kc(int mt, int k) {
+    const int kmax = tile_shape(mt).kc_max;
+    return k < kmax ? k : kmax;
 }
 
 static unsigned grid_1d(int64_t items, int nsm) {
@@ -487,31 +584,23 @@ static unsigned grid_1d(int64_t items, int nsm) {
 }
 
 template <int MT>
-static cudaError_t factor_odd_mt(LevelArgs a, int nsm, cudaStream_t s) {
-    const TileShape ts = tile_shape(MT);
-    a.nb = level_nb(ts.nb_factor, a.no, nsm);
-    const unsigned grid = (unsigned)((a.no + a.nb - 1) / a.nb);
-    k_factor_odd<MT><<<grid, ts.threads, factor_smem_bytes(MT, a.nb), s>>>(a);
+static cudaError_t factor_odd_mt(const LevelArgs &a, cudaStream_t s) {
+    const unsigned grid = (unsigned)num_ctas(a.no, a.nb);
+    k_factor_odd<MT><<<grid, tile_shape(MT).threads, factor_smem_bytes(MT, a.nb), s>>>(a);
     return cudaGetLastError();
 }
 
 template <int MT>
-static cudaError_t solve_down_odd_mt(LevelArgs a, int nsm, cudaStream_t s) {
-    const TileShape ts = tile_shape(MT);
-    a.nb = level_nb(ts.nb_solve, a.no, nsm);
-    a.kc = a.k < ts.kc_max ? a.k : ts.kc_max;
-    const dim3 grid((unsigned)((a.no + a.nb - 1) / a.nb), (unsigned)((a.k + a.kc - 1) / a.kc));
-    k_solve_down_odd<MT><<<grid, ts.threads, solve_smem_bytes(MT, a.nb, a.kc, false), s>>>(a);
+static cudaError_t solve_down_odd_mt(const LevelArgs &a, cudaStream_t s) {
+    const dim3 grid((unsigned)num_ctas(a.no, a.nb), (unsigned)((a.k + a.kc - 1) / a.kc));
+    k_solve_down_odd<MT><<<grid, tile_shape(MT).threads, solve_smem_bytes(MT, a.nb, a.kc, 3), s>>>(a);
     return cudaGetLastError();
 }
 
 template <int MT>
-static cudaError_t solve_up_mt(LevelArgs a, int nsm, cudaStream_t s) {
-    const TileShape ts = tile_shape(MT);
-    a.nb = level_nb(ts.nb_solve, a.no, nsm);
-    a.kc = a.k < ts.kc_max ? a.k : ts.kc_max;
-    const dim3 grid((unsigned)((a.no + a.nb - 1) / a.nb), (unsigned)((a.k + a.kc - 1) / a.kc));
-    k_solve_up<MT><<<grid, ts.threads, solve_smem_bytes(MT, a.nb, a.kc, true), s>>>(a);
+static cudaError_t solve_up_mt(const LevelArgs &a, cudaStream_t s) {
+    const dim3 grid((unsigned)num_ctas(a.no, a.nb), (unsigned)((a.k + a.kc - 1) / a.kc));
+    k_solve_up<MT><<<grid, tile_shape(MT).threads, solve_smem_bytes(MT, a.nb, a.kc, 3), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -525,24 +614,26 @@ static cudaError_t solve_up_mt(LevelArgs a, int nsm, cudaStream_t s) {
         default: return cudaErrorInvalidValue;      \
     }
 
-cudaError_t launch_factor_odd(int mt, const LevelArgs &a, int nsm, cudaStream_t s) {
-    CRS_DISPATCH(factor_odd_mt, mt, a, nsm, s)
+cudaError_t launch_factor_odd(int mt, const LevelArgs &a, cudaStream_t s) {
+    CRS_DISPATCH(factor_odd_mt, mt, a, s)
 }
-cudaError_t launch_factor_even(const LevelArgs &a, int nsm, cudaStream_t s) {
-    if (a.ne == 0) return cudaSuccess;
-    k_factor_even<<<grid_1d(a.ne * (a.m * (a.m + 1) / 2), nsm), 256, 0, s>>>(a);
+cudaError_t launch_factor_fix(const LevelArgs &a, int nsm, cudaStream_t s) {
+    const int64_t ncta = num_ctas(a.no, a.nb);
+    if (ncta < 2) return cudaSuccess;
+    k_factor_fix<<<grid_1d((ncta - 1) * (a.m * (a.m + 1) / 2), nsm), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_solve_down_odd(int mt, const LevelArgs &a, int nsm, cudaStream_t s) {
-    CRS_DISPATCH(solve_down_odd_mt, mt, a, nsm, s)
+cudaError_t launch_solve_down_odd(int mt, const LevelArgs &a, cudaStream_t s) {
+    CRS_DISPATCH(solve_down_odd_mt, mt, a, s)
 }
-cudaError_t launch_solve_down_even(const LevelArgs &a, int nsm, cudaStream_t s) {
-    if (a.ne == 0) return cudaSuccess;
-    k_solve_down_even<<<grid_1d(a.ne * a.m * a.k, nsm), 256, 0, s>>>(a);
+cudaError_t launch_solve_down_fix(const LevelArgs &a, int nsm, cudaStream_t s) {
+    const int64_t ncta = num_ctas(a.no, a.nb);
+    if (ncta < 2) return cudaSuccess;
+    k_solve_down_fix<<<grid_1d((ncta - 1) * a.m * a.k, nsm), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_solve_up_level(int mt, const LevelArgs &a, int nsm, cudaStream_t s) {
-    CRS_DISPATCH(solve_up_mt, mt, a, nsm, s)
+cudaError_t launch_solve_up(int mt, const LevelArgs &a, cudaStream_t s) {
+    CRS_DISPATCH(solve_up_mt, mt, a, s)
 }
 
 cudaError_t launch_adjoint_outer(int64_t N, int m, int k, const z2 *x, const z2 *gy, z2 *gA, z2 *gB,

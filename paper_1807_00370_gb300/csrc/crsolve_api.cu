@@ -32,7 +32,7 @@ struct crsolve_plan_s {
     int m = 0, kmax = 0, precision = 0, mt = 0, device = 0, nsm = 0;
     uint32_t flags = 0;
     std::vector<LevelPlan> lev;
-    size_t offStatus = 0, offWl = 0, offWr = 0, offCl = 0, offCr = 0;
+    size_t offStatus = 0, offWbd = 0, offCbd = 0;
     size_t offSA = 0, offSB = 0, offSY = 0, offSX = 0;
     size_t total = 0;
     char *ws = nullptr;
@@ -69,13 +69,11 @@ crs::LevelArgs level_args(const crsolve_plan_s *p, int l, const z2 *A0, const z2
     a.L = reinterpret_cast<z2 *>(ws + L.offL);
     a.inv = reinterpret_cast<double *>(ws + L.offInv);
     a.Z = reinterpret_cast<z2 *>(ws + L.offZ);
-    a.Wl = reinterpret_cast<z2 *>(ws + p->offWl);
-    a.Wr = reinterpret_cast<z2 *>(ws + p->offWr);
+    a.Wbd = reinterpret_cast<z2 *>(ws + p->offWbd);
     a.An = reinterpret_cast<z2 *>(ws + L.offAn);
     a.Bn = reinterpret_cast<z2 *>(ws + L.offBn);
     a.r = reinterpret_cast<z2 *>(ws + L.offR);
-    a.cl = reinterpret_cast<z2 *>(ws + p->offCl);
-    a.cr = reinterpret_cast<z2 *>(ws + p->offCr);
+    a.cbd = reinterpret_cast<z2 *>(ws + p->offCbd);
     a.yn = reinterpret_cast<z2 *>(ws + L.offYn);
     a.xn = reinterpret_cast<const z2 *>(ws + L.offXn);
     a.status = reinterpret_cast<unsigned long long *>(ws + p->offStatus);
@@ -128,12 +126,14 @@ int do_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
         return CRSOLVE_ECUDA;
     int rc;
     for (int l = 0; l < (int)p->lev.size(); ++l) {
-        const crs::LevelArgs a = level_args(p, l, A, B);
+        crs::LevelArgs a = level_args(p, l, A, B);
+        a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
         if ((rc = launch(p, CRSOLVE_K_FACTOR_ODD, l, a.no, s,
-                         [&] { return crs::launch_factor_odd(p->mt, a, p->nsm, s); })))
+                         [&] { return crs::launch_factor_odd(p->mt, a, s); })))
             return rc;
-        if (a.ne > 0 && (rc = launch(p, CRSOLVE_K_FACTOR_EVEN, l, a.ne, s,
-                                     [&] { return crs::launch_factor_even(a, p->nsm, s); })))
+        if (crs::num_ctas(a.no, a.nb) > 1 &&
+            (rc = launch(p, CRSOLVE_K_FACTOR_FIX, l, crs::num_ctas(a.no, a.nb) - 1, s,
+                         [&] { return crs::launch_factor_fix(a, p->nsm, s); })))
             return rc;
     }
     p->factored = true;
@@ -146,20 +146,25 @@ int do_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     for (int l = 0; l < nlev; ++l) {
         crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
         a.k = k;
+        a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
+        a.kc = crs::solve_kc(p->mt, k);
         a.y = (l == 0) ? y : reinterpret_cast<const z2 *>(p->ws + p->lev[l - 1].offYn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s,
-                         [&] { return crs::launch_solve_down_odd(p->mt, a, p->nsm, s); })))
+                         [&] { return crs::launch_solve_down_odd(p->mt, a, s); })))
             return rc;
-        if (a.ne > 0 && (rc = launch(p, CRSOLVE_K_SOLVE_DOWN_EVEN, l, a.ne, s,
-                                     [&] { return crs::launch_solve_down_even(a, p->nsm, s); })))
+        if (crs::num_ctas(a.no, a.nb) > 1 &&
+            (rc = launch(p, CRSOLVE_K_SOLVE_DOWN_FIX, l, crs::num_ctas(a.no, a.nb) - 1, s,
+                         [&] { return crs::launch_solve_down_fix(a, p->nsm, s); })))
             return rc;
     }
     for (int l = nlev - 1; l >= 0; --l) {
         crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
         a.k = k;
+        a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
+        a.kc = crs::solve_kc(p->mt, k);
         a.x = (l == 0) ? x : reinterpret_cast<z2 *>(p->ws + p->lev[l - 1].offXn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, l, a.no, s,
-                         [&] { return crs::launch_solve_up_level(p->mt, a, p->nsm, s); })))
+                         [&] { return crs::launch_solve_up(p->mt, a, s); })))
             return rc;
     }
     return CRSOLVE_OK;
@@ -206,10 +211,10 @@ int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, u
         Nl /= 2;
     }
     const int64_t no0 = (N + 1) / 2;
-    p->offWl = take(cur, no0 * mm * zsz);
-    p->offWr = take(cur, no0 * mm * zsz);
-    p->offCl = take(cur, no0 * mk * zsz);
-    p->offCr = take(cur, no0 * mk * zsz);
+    // CTA-boundary scratch: at most one m x m (factor) and one m x kmax (solve)
+    // per CTA of the largest level
+    p->offWbd = take(cur, no0 * mm * zsz);
+    p->offCbd = take(cur, no0 * mk * zsz);
     if (flags & CRSOLVE_PLAN_HOST_STAGING) {
         p->offSA = take(cur, N * mm * zsz);
         p->offSB = take(cur, (N - 1) * mm * zsz);
@@ -392,6 +397,24 @@ const char *crsolve_strerror(int code) {
         case CRSOLVE_EUNSUPPORTED: return "unsupported size or precision";
         default: return "unknown status";
     }
+}
+
+int crsolve_tile_set(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc, int32_t threads) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    return crs::set_tile_shape(mt, crs::TileShape{nb_factor, nb_solve, kc, threads}, (size_t)optin)
+               ? CRSOLVE_OK
+               : CRSOLVE_EINVAL;
+}
+
+int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads) {
+    if (!nb_factor || !nb_solve || !kc || !threads) return CRSOLVE_EINVAL;
+    const crs::TileShape ts = crs::tile_shape(mt);
+    if (ts.threads == 0) return CRSOLVE_EINVAL;
+    *nb_factor = ts.nb_factor; *nb_solve = ts.nb_solve; *kc = ts.kc_max; *threads = ts.threads;
+    return CRSOLVE_OK;
 }
 
 int crsolve_plan_levels(crsolve_plan p, int32_t *nlev, int64_t *sizes) {
