@@ -157,6 +157,30 @@ int crsolve_destroy(crsolve_plan p);
 /* Static description of a status code. */
 const char *crsolve_strerror(int code);
 
+/*
+ * crsolve_solve_noalloc -- factor and solve one system with no device
+ * allocation, for callers that cannot call cudaMalloc (code running where the
+ * allocator is unavailable or forbidden, e.g. a host callback, a
+ * pre-allocated real-time loop, or a plugin that must not grow the device
+ * footprint after start-up).  The paper has no counterpart; this is the same
+ * classic cyclic reduction as crsolve_factor + crsolve_solve.
+ *   The caller passes A [N][m][m], B [N-1][m][m] (NULL iff N == 1), y and x
+ *   [N][m][k] in device memory, as for crsolve_factor / crsolve_solve.  All
+ *   intermediates live in one fixed 32 MiB device array inside this library
+ *   (held by every GPU that loads the library until the process exits); a
+ *   system whose intermediates exceed it returns CRSOLVE_ENOMEM and enqueues
+ *   nothing (about N * (5.5 m^2 + 3.5 m k) * 16 bytes must fit, e.g. N up to
+ *   ~4500 for m = 8, k = 4).
+ *   The first call on a device looks up the array's address and prepares the
+ *   kernels; make it before any stream capture.  All calls share the array
+ *   and it keeps the last call's contents, so calls that overlap on the GPU
+ *   race: serialise them.  After a breakdown x holds NaN.  With info != NULL
+ *   the call synchronises the stream and reports the breakdown status there;
+ *   with info == NULL it is asynchronous.
+ */
+int crsolve_solve_noalloc(int64_t N, int32_t m, int32_t k, const crsolve_z *A, const crsolve_z *B,
+                          const crsolve_z *y, crsolve_z *x, crsolve_info *info, void *stream);
+
 /* ---- instrumentation (the paper has no counterpart; used by the benchmark) ---- */
 
 enum crsolve_kernel_kind {

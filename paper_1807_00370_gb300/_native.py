@@ -64,6 +64,7 @@ SIGNATURES = {
     "crsolve_timing_read": (ctypes.c_int, [_P, ctypes.POINTER(CrsolveKernelTime), _I32, ctypes.POINTER(_I32)]),
     "crsolve_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "crsolve_tile_set": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32]),
+    "crsolve_solve_noalloc": (ctypes.c_int, [_I64, _I32, _I32, _P, _P, _P, _P, ctypes.POINTER(CrsolveInfo), _P]),
     "crsolve_tile_get": (ctypes.c_int, [_I32] + [ctypes.POINTER(_I32)] * 4),
 }
 

@@ -16,7 +16,7 @@ from . import _native as nat
 __all__ = ["Plan", "crsolve_plan_create", "crsolve_factor", "crsolve_solve", "crsolve_backward",
            "crsolve_info_get", "crsolve_solve_host", "crsolve_plan_levels",
            "crsolve_debug_level_system", "crsolve_timing_enable", "crsolve_timing_read",
-           "crsolve_launch_count", "crsolve_tile_set", "crsolve_tile_get", "solve", "CRSolveFn",
+           "crsolve_launch_count", "crsolve_tile_set", "crsolve_tile_get", "crsolve_solve_noalloc", "solve", "CRSolveFn",
            "NotPositiveDefinite"]
 
 
@@ -210,6 +210,30 @@ def crsolve_tile_get(mt: int):
     v = [ctypes.c_int32() for _ in range(4)]
     nat.check(nat.load().crsolve_tile_get(mt, *[ctypes.byref(x) for x in v]), "crsolve_tile_get")
     return tuple(int(x.value) for x in v)
+
+
+def crsolve_solve_noalloc(A: torch.Tensor, B: torch.Tensor | None, y: torch.Tensor,
+                          x: torch.Tensor | None = None, want_info: bool = True, stream=None):
+    """Factor + solve without any device allocation by the library (its
+    intermediates live in a fixed 32 MiB device array; see include/crsolve.h).
+    Returns (x, info dict or None)."""
+    N, m, _ = A.shape
+    k = y.shape[-1]
+    _need(A, (N, m, m), "A")
+    if N > 1:
+        _need(B, (N - 1, m, m), "B", A.device)
+    _need(y, (N, m, k), "y", A.device)
+    if x is None:
+        x = torch.empty_like(y)
+    _need(x, (N, m, k), "x", A.device)
+    info = nat.CrsolveInfo() if want_info else None
+    with torch.cuda.device(A.device):
+        nat.check(nat.load().crsolve_solve_noalloc(N, m, k, _vp(A), _vp(B) if N > 1 else None, _vp(y), _vp(x),
+                                                   ctypes.byref(info) if want_info else None, _stream(stream)),
+                  "crsolve_solve_noalloc")
+    if not want_info:
+        return x, None
+    return x, {"status": info.status, "level": info.level, "block": info.block, "orig_block": info.orig_block}
 
 
 def solve(A: torch.Tensor, B: torch.Tensor | None, y: torch.Tensor, check: bool = True) -> torch.Tensor:
