@@ -174,6 +174,73 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+BATCH_SEED = 3003
+BATCH_WORKLOAD = ("batched CR: 4096 independent HPD block-tridiagonal systems in one persistent launch, "
+                  "N ~ U[16, 4096], m in {4, 8, 16, 32}, k ~ U[1, 16], complex128")
+
+
+def run_batched(args):
+    """4096 uneven systems (seed 3003): one persistent launch replayed as a CUDA
+    graph, against the plain single-system path called per system."""
+    import torch
+    import paper_1807_00370_gb300 as crs
+    torch.cuda.set_device(0)
+    nsys = args.nsys
+    Ns, ms, ks = synthetic.gen_batch_shapes(4096, seed=BATCH_SEED)
+    Ns, ms, ks = Ns[:nsys], ms[:nsys], ks[:nsys]
+    A, B, y = synthetic.gen_batch_device(Ns, ms, ks, seed=BATCH_SEED)
+    x = torch.empty_like(y)
+    b = crs.Batch(Ns, ms, ks)
+    rows = int(Ns.sum())
+    flops = float((Ns * (25.33 * ms.astype(float) ** 3 + 40.0 * ms.astype(float) ** 2 * ks)).sum())
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 1)):
+        crs.crsolve_batch_graph_launch(b, A, B, y, x)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(1.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark(True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        crs.crsolve_batch_graph_launch(b, A, B, y, x)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark(False)
+    clocks = sampler.stop()
+    ms_step = e0.elapsed_time(e1) / args.steps
+    infos = crs.crsolve_batch_info(b)
+    # the plain path: one plan per system, all on the same stream
+    xp = torch.empty_like(y)
+    e0.record(stream)
+    for i in range(len(Ns)):
+        p = crs.Plan(int(Ns[i]), int(ms[i]), int(ks[i]))
+        a, bb, yy = b.system_view(i, A, B, y)
+        crs.crsolve_factor(p, a, bb if Ns[i] > 1 else None)
+        crs.crsolve_solve(p, yy, b.system_view(i, A, B, xp)[2])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_plain = e0.elapsed_time(e1)
+    same = bool(torch.equal(x, xp))
+    peak_tf = FP64_PEAK_GFLOPS / 1e3
+    line = {
+        "metric": "block-rows/s", "value": rows / (ms_step * 1e-3), "unit": "block-rows/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD, "systems": len(Ns), "block_rows": rows, "seed": BATCH_SEED,
+                   "slots": b.nslots, "l2": "inputs larger than L2, no flush"},
+        "roofline": {"bound": "alu", "kernel": "k_batch (whole step)", "achieved": flops / (ms_step * 1e-3) / 1e12,
+                     "peak": peak_tf, "unit": "TFLOP/s", "frac": flops / (ms_step * 1e-3) / 1e12 / peak_tf,
+                     "traffic": None},
+        "speedup_vs_plain": {"plain_ms": ms_plain, "batched_ms": ms_step, "speedup": ms_plain / ms_step,
+                             "bitwise_equal": same},
+        "breakdown_count": sum(1 for r in infos if r["status"]),
+        "gpu_launches": args.steps, "clocks": clocks, "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -183,11 +250,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--nsys", type=int, default=4096, help="systems of the batched workload")
     ap.add_argument("--log2n", type=int, default=20,
                     help="log2 of the block count (smaller cases are for profiling only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import torch
     import paper_1807_00370_gb300 as crs

@@ -157,6 +157,59 @@ int crsolve_destroy(crsolve_plan p);
 /* Static description of a status code. */
 const char *crsolve_strerror(int code);
 
+/* ---- batched: many independent systems in one persistent launch ---- */
+
+typedef struct crsolve_batch_s *crsolve_batch;
+
+/*
+ * crsolve_batch_create -- describe nsys independent systems (host only apart
+ * from reading the device properties).  System i has N[i] >= 1 blocks of
+ * size 1 <= m[i] <= CRSOLVE_MAX_M and k[i] >= 1 right-hand sides.  Inputs
+ * are packed back to back in system order: system i's A starts at element
+ * offA[i] = sum_{j<i} N_j m_j^2 of one A array, its B at offB[i] =
+ * sum_{j<i} (N_j - 1) m_j^2, its y and x at offY[i] = sum_{j<i} N_j m_j k_j
+ * (crsolve_batch_offsets reports them).  The systems are independent (the
+ * block formulas of Sec. 2 never couple two systems); each is solved by the
+ * same classic cyclic reduction as crsolve_factor + crsolve_solve, with
+ * bit-identical arithmetic.
+ */
+int crsolve_batch_create(int32_t nsys, const int64_t *N, const int32_t *m, const int32_t *k,
+                         crsolve_batch *out);
+
+/* Tile shape of block-size class mt for this batch (odd blocks per chunk of
+ * the factor and solve steps, right-hand-side columns per chunk); before
+ * crsolve_batch_set_workspace.  CRSOLVE_EINVAL if out of range or if the
+ * kernel would not fit in shared memory. */
+int crsolve_batch_tile_set(crsolve_batch b, int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc);
+
+/* Workspace size: one slot per persistent CTA (as many as fit on the device,
+ * at most nsys, and at most what fits in max_bytes when max_bytes > 0) plus
+ * per-system descriptors and status.  Reports the slot count in *nslots. */
+int crsolve_batch_workspace_bytes(crsolve_batch b, size_t max_bytes, size_t *bytes, int32_t *nslots);
+
+/* Bind caller-owned device memory (256-byte aligned, >= the size above). */
+int crsolve_batch_set_workspace(crsolve_batch b, void *dev_ptr, size_t bytes);
+
+/* Element offsets of every system in the packed arrays (host arrays of nsys
+ * entries, any may be NULL) and totals[3] = elements of A, B and y/x. */
+int crsolve_batch_offsets(crsolve_batch b, int64_t *offA, int64_t *offB, int64_t *offY, int64_t *totals);
+
+/* Factor and solve every system: one persistent kernel launch on the stream
+ * (plus two memsets).  A, B, y, x are the packed device arrays; x must not
+ * alias y.  Per-system breakdown is read with crsolve_batch_info. */
+int crsolve_batch_solve(crsolve_batch b, const crsolve_z *A, const crsolve_z *B, const crsolve_z *y,
+                        crsolve_z *x, void *stream);
+
+/* Same as crsolve_batch_solve, through a CUDA graph captured on the first
+ * call (and again whenever the pointers change) and replayed on the stream. */
+int crsolve_batch_graph_launch(crsolve_batch b, const crsolve_z *A, const crsolve_z *B, const crsolve_z *y,
+                               crsolve_z *x, void *stream);
+
+/* Synchronises the stream and writes nsys breakdown records into out. */
+int crsolve_batch_info(crsolve_batch b, crsolve_info *out, void *stream);
+
+int crsolve_batch_destroy(crsolve_batch b);
+
 /*
  * crsolve_solve_noalloc -- factor and solve one system with no device
  * allocation, for callers that cannot call cudaMalloc (code running where the

@@ -64,6 +64,15 @@ SIGNATURES = {
     "crsolve_timing_read": (ctypes.c_int, [_P, ctypes.POINTER(CrsolveKernelTime), _I32, ctypes.POINTER(_I32)]),
     "crsolve_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "crsolve_tile_set": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32]),
+    "crsolve_batch_create": (ctypes.c_int, [_I32, _P, _P, _P, ctypes.POINTER(_P)]),
+    "crsolve_batch_tile_set": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32]),
+    "crsolve_batch_workspace_bytes": (ctypes.c_int, [_P, _SZ, ctypes.POINTER(_SZ), ctypes.POINTER(_I32)]),
+    "crsolve_batch_set_workspace": (ctypes.c_int, [_P, _P, _SZ]),
+    "crsolve_batch_offsets": (ctypes.c_int, [_P, _P, _P, _P, _P]),
+    "crsolve_batch_solve": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "crsolve_batch_graph_launch": (ctypes.c_int, [_P, _P, _P, _P, _P, _P]),
+    "crsolve_batch_info": (ctypes.c_int, [_P, _P, _P]),
+    "crsolve_batch_destroy": (ctypes.c_int, [_P]),
     "crsolve_solve_noalloc": (ctypes.c_int, [_I64, _I32, _I32, _P, _P, _P, _P, ctypes.POINTER(CrsolveInfo), _P]),
     "crsolve_tile_get": (ctypes.c_int, [_I32] + [ctypes.POINTER(_I32)] * 4),
 }

@@ -73,6 +73,8 @@ __device__ __forceinline__ int tri_row(int f) {
 struct LevelArgs {
     int64_t Nl, no, ne;
     int m, k, nb, kc, level;
+    int inline_fix;     // 1: one CTA runs the chunks of the level in order and completes each
+                        // chunk-boundary even block itself (no Wbd / cbd, no fix-up pass)
     const z2 *A;        // [Nl][m][m] level system (lower triangle read)
     const z2 *B;        // [Nl-1][m][m]
     z2 *L;              // [no][m][m]  Cholesky factors (lower, upper zero)

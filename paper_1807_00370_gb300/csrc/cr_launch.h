@@ -1,7 +1,7 @@
 // cr_launch.h -- host-side launchers of the per-level kernels (internal).
 #pragma once
 #include <cuda_runtime.h>
-#include "cr_device.cuh"
+#include "cr_core.cuh"
 
 namespace crs {
 
@@ -27,7 +27,7 @@ cudaError_t prepare_kernels(int mt);                 // raise shared-memory limi
 int factor_nb(int mt, int64_t no, int nsm);
 int solve_nb(int mt, int64_t no, int nsm);
 int solve_kc(int mt, int k);
-__host__ __device__ inline int64_t num_ctas(int64_t no, int nb) { return (no + nb - 1) / nb; }
+inline int64_t num_ctas(int64_t no, int nb) { return crs_num_ctas(no, nb); }
 
 // Factor sweep of one level (a.nb set by factor_nb): the odd-block kernel
 // (Cholesky, P, Q, Z^H Z, and the even blocks that lie inside its CTA), then

@@ -1,431 +1,35 @@
-// cr_levels.cu -- the per-level kernels of classic cyclic reduction in FP64.
-//
-// One level (Sec. 2, eq. Formulas; 0-based: odd block t at position 2t, even
-// block j at 2j+1, so odd t has the even blocks j = t-1 on its left and
-// j = t on its right):
-//   k_factor_odd     per odd block: Cholesky A_2t = L L^H with the breakdown
-//                    test, Z = [P | Q] = L^{-1} [B_{2t-1} | B_{2t}^H], and the
-//                    Hermitian product Z^H Z (Sec. 4's rule), whose parts are
-//                    Q^H Q (subtracted from the right even block), P^H P (from
-//                    the left even block) and Q^H P (= -F, the next level's B).
-//                    The even blocks whose two odd neighbours sit in the same
-//                    CTA are finished there: V_j = (A_2j+1 - Q^H Q) - P^H P.
-//   k_factor_fix     the even block on each CTA boundary: subtract the P^H P
-//                    that the next CTA left in a scratch buffer.
-//   k_solve_down_odd r = L^{-1} y_odd, v_j = (y_2j+1 - Q^H r) - P^H r, same
-//                    CTA split, and k_solve_down_fix for the boundaries.
-//   k_solve_up       x_odd = L^{-H}(r - P x_left - Q x_right); x_even copied.
-//
-// GPU mapping.  A CTA owns nb consecutive odd blocks and stages them in
-// shared memory.  Each phase is a list of equal-cost work items (a matrix
-// entry, a column of a triangular solve) spread over all threads of the CTA;
-// items of different cost (pivots, real diagonal entries) get warps of their
-// own.  On GB300 the FP64 pipe (2 DFMA/clk/SM) bounds this path and one warp
-// per SM sub-partition with a dependent chain already keeps it ~90% busy, so
-// lane utilisation and FP64 instruction count matter most, occupancy little.
+// cr_levels.cu -- the per-level kernels of classic cyclic reduction in FP64
+// (one chunk of odd blocks per CTA; the steps themselves are in cr_core.cuh)
+// and their host-side launchers.
 #include "cr_launch.h"
+#include "cr_core.cuh"
 
 namespace crs {
-
-// Packed lower-triangular storage in shared memory: entry (r, c), r >= c.
-__device__ __forceinline__ int tri(int r, int c) { return r * (r + 1) / 2 + c; }
-template <int MT> struct Tri { static constexpr int n = MT * (MT + 1) / 2; };
-
-// --------------------------------------------------------------- helpers
-
-// z := L^{-1} z for one column z (shared memory, stride ld); L packed lower.
-template <int MT>
-__device__ __forceinline__ void trsv_lower_col(const z2 *Lb, const double *ivb, z2 *col, int ld, int m) {
-    if constexpr (MT <= 32) {
-        z2 z[MT];
-#pragma unroll
-        for (int r = 0; r < MT; ++r)
-            if (r < m) z[r] = col[r * ld];
-#pragma unroll
-        for (int r = 0; r < MT; ++r) {
-            if (r < m) {
-                z2 acc = z[r];
-#pragma unroll
-                for (int s = 0; s < r; ++s) zmsub(acc, Lb[tri(r, s)], z[s]);
-                z[r] = zscale(acc, ivb[r]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < MT; ++r)
-            if (r < m) col[r * ld] = z[r];
-    } else {
-        for (int r = 0; r < m; ++r) {
-            z2 acc = col[r * ld];
-            for (int s = 0; s < r; ++s) zmsub(acc, Lb[tri(r, s)], col[s * ld]);
-            col[r * ld] = zscale(acc, ivb[r]);
-        }
-    }
-}
-
-// z := L^{-H} z for one column z (shared memory, stride ld); L packed lower.
-template <int MT>
-__device__ __forceinline__ void trsv_lower_h_col(const z2 *Lb, const double *ivb, z2 *col, int ld, int m) {
-    if constexpr (MT <= 16) {
-        z2 z[MT];
-#pragma unroll
-        for (int r = 0; r < MT; ++r)
-            if (r < m) z[r] = col[r * ld];
-#pragma unroll
-        for (int r = MT - 1; r >= 0; --r) {
-            if (r < m) {
-                z2 acc = z[r];
-#pragma unroll
-                for (int s = r + 1; s < MT; ++s)
-                    if (s < m) zmsub_ca(acc, Lb[tri(s, r)], z[s]);
-                z[r] = zscale(acc, ivb[r]);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < MT; ++r)
-            if (r < m) col[r * ld] = z[r];
-    } else {
-        for (int r = m - 1; r >= 0; --r) {
-            z2 acc = col[r * ld];
-            for (int s = r + 1; s < m; ++s) zmsub_ca(acc, Lb[tri(s, r)], col[s * ld]);
-            col[r * ld] = zscale(acc, ivb[r]);
-        }
-    }
-}
-
-// ------------------------------------------------------------ factor: odd
 
 template <int MT>
 __global__ void __launch_bounds__(256) k_factor_odd(LevelArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int LDZ = 2 * MT, TRI = Tri<MT>::n;
-    const int m = a.m, nb = a.nb, NT = blockDim.x, tid = threadIdx.x;
-    const int mm = m * m, m2 = 2 * m;
-    const int64_t t0 = (int64_t)blockIdx.x * nb;
-    const int nbh = (int)min((int64_t)nb, a.no - t0);
-    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                        // [nb][TRI] L, later P^H P
-    z2 *sV = sL + (size_t)nb * TRI;                                    // [nb][TRI] even block t0+b
-    z2 *sZ = sV + (size_t)nb * TRI;                                    // [nb][MT][2MT] [P | Q]
-    double *sInv = reinterpret_cast<double *>(sZ + (size_t)nb * MT * LDZ);  // [nb][MT]
-
-    // stage the lower triangles of A_2t and A_2t+1, B_{2t-1} (P part) and
-    // B_{2t}^H (Q part)
-    for (int e = tid; e < nbh * mm; e += NT) {
-        const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        const int64_t t = t0 + b, pos = 2 * t;
-        if (r >= c) {
-            sL[b * TRI + tri(r, c)] = a.A[pos * mm + rem];
-            if (t < a.ne) {
-                z2 v = a.A[(pos + 1) * mm + rem];
-                if (r == c) v.y = 0.0;
-                sV[b * TRI + tri(r, c)] = v;
-            }
-        }
-        sZ[(b * MT + r) * LDZ + c] = (pos >= 1) ? a.B[(pos - 1) * mm + rem] : zmk(0.0, 0.0);
-        sZ[(b * MT + c) * LDZ + m + r] = (pos + 1 < a.Nl) ? zconj(a.B[pos * mm + rem]) : zmk(0.0, 0.0);
-    }
-    __syncthreads();
-
-    // Cholesky, left-looking by columns.  Pass 1 of column c: the pivots
-    // (one item per block, in warps of their own so that the sqrt path does
-    // not diverge from the off-diagonal path), then the unscaled entries
-    // below the pivot.  Pass 2 scales them by 1 / pivot.
-    const int dpad = (nbh + 31) & ~31;
-    for (int c = 0; c < m; ++c) {
-        const int below = m - c - 1;
-        for (int e = tid; e < dpad + nbh * below; e += NT) {
-            if (e < nbh) {
-                const int b = e;
-                z2 *Lb = sL + b * TRI;
-                double d = Lb[tri(c, c)].x;
-                for (int s = 0; s < c; ++s) {
-                    const z2 l = Lb[tri(c, s)];
-                    d = fma(-l.x, l.x, d);
-                    d = fma(-l.y, l.y, d);
-                }
-                if (!(d > 0.0)) report_fail(a.status, a.level, 2 * (t0 + b) + 1);
-                const double iv = rsqrt(d);
-                sInv[b * MT + c] = iv;
-                Lb[tri(c, c)] = zmk(d * iv, 0.0);
-            } else if (e >= dpad) {
-                const int e2 = e - dpad, b = e2 / below, r = c + 1 + (e2 - b * below);
-                z2 *Lb = sL + b * TRI;
-                z2 u = Lb[tri(r, c)];
-                for (int s = 0; s < c; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(c, s)]);
-                Lb[tri(r, c)] = u;
-            }
-        }
-        __syncthreads();
-        for (int e = tid; e < nbh * below; e += NT) {
-            const int b = e / below, r = c + 1 + (e - b * below);
-            z2 *p = sL + b * TRI + tri(r, c);
-            *p = zscale(*p, sInv[b * MT + c]);
-        }
-        __syncthreads();
-    }
-
-    // Z := L^{-1} Z, one item per (block, column); zero columns stay zero
-    for (int e = tid; e < nbh * m2; e += NT) {
-        const int b = e / m2, col = e - b * m2;
-        const int64_t pos = 2 * (t0 + b);
-        if (col < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
-        trsv_lower_col<MT>(sL + b * TRI, sInv + b * MT, sZ + b * MT * LDZ + col, LDZ, m);
-    }
-    __syncthreads();
-
-    // keep L, 1/diag(L) and Z for the solves
-    for (int e = tid; e < nbh * mm; e += NT) {
-        const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        a.L[(t0 + b) * mm + rem] = (r >= c) ? sL[b * TRI + tri(r, c)] : zmk(0.0, 0.0);
-    }
-    for (int e = tid; e < nbh * m; e += NT) {
-        const int b = e / m, r = e - b * m;
-        a.inv[(t0 + b) * m + r] = sInv[b * MT + r];
-    }
-    for (int e = tid; e < nbh * m * m2; e += NT) {
-        const int b = e / (m * m2), rem = e - b * (m * m2), r = rem / m2, c = rem - r * m2;
-        a.Z[(t0 + b) * (int64_t)(m * m2) + rem] = sZ[(b * MT + r) * LDZ + c];
-    }
-    __syncthreads();
-
-    // Lower triangle of Z^H Z, one item per entry.  The 2m real diagonal
-    // entries of each block come first, in warps of their own (2 FMA per
-    // term instead of 4).  Parts: Q^H Q is subtracted from the right even
-    // block V_t in place, P^H P is kept in sW (the L buffer, free now) for the
-    // left even block, and Q^H P = -F goes to the next level's B.
-    z2 *sW = sL;
-    const int ndiag = nbh * m2, dpadh = (ndiag + 31) & ~31, noff = m2 * (m2 - 1) / 2;
-    for (int e = tid; e < dpadh + nbh * noff; e += NT) {
-        if (e < ndiag) {
-            const int b = e / m2, p = e - b * m2;
-            const int64_t t = t0 + b;
-            if (p < m ? (t == 0) : (2 * t + 1 >= a.Nl)) continue;
-            const z2 *Zb = sZ + b * MT * LDZ + p;
-            double d = 0.0;
-#pragma unroll
-            for (int s = 0; s < MT; ++s)
-                if (s < m) {
-                    const z2 v = Zb[s * LDZ];
-                    d = fma(v.x, v.x, d);
-                    d = fma(v.y, v.y, d);
-                }
-            if (p < m) sW[b * TRI + tri(p, p)] = zmk(d, 0.0);
-            else sV[b * TRI + tri(p - m, p - m)].x -= d;
-        } else if (e >= dpadh) {
-            const int e2 = e - dpadh, b = e2 / noff, g = e2 - b * noff;
-            const int p = tri_row(g) + 1, q = g - p * (p - 1) / 2;   // p > q
-            const int64_t t = t0 + b;
-            const bool hasL = t >= 1, hasR = 2 * t + 1 < a.Nl;
-            const int kind = (p < m) ? 0 : (q >= m ? 1 : 2);  // P^H P, Q^H Q, Q^H P
-            if (kind == 0 ? !hasL : (kind == 1 ? !hasR : !(hasL && hasR))) continue;
-            const z2 *Zb = sZ + b * MT * LDZ;
-            z2 acc = zmk(0.0, 0.0);
-#pragma unroll
-            for (int s = 0; s < MT; ++s)
-                if (s < m) zmac_ca(acc, Zb[s * LDZ + p], Zb[s * LDZ + q]);
-            if (kind == 0) {
-                sW[b * TRI + tri(p, q)] = acc;
-            } else if (kind == 1) {
-                z2 &v = sV[b * TRI + tri(p - m, q - m)];
-                v = zsub(v, acc);
-            } else {
-                a.Bn[(t - 1) * mm + (p - m) * m + q] = zneg(acc);
-            }
-        }
-    }
-    __syncthreads();
-
-    // V_j = (A_2j+1 - Q^H Q) - P^H P for the even blocks j = t0 + b.  The
-    // CTA's last one misses its right neighbour's P^H P when that neighbour
-    // starts the next CTA (k_factor_fix completes it); the CTA's first P^H P
-    // goes to the boundary buffer for the previous CTA.
-    const int nl = m * (m + 1) / 2;
-    for (int e = tid; e < nbh * nl; e += NT) {
-        const int b = e / nl, f = e - b * nl, r = tri_row(f), c = f - r * (r + 1) / 2;
-        const int64_t j = t0 + b;
-        if (b == 0 && j >= 1) a.Wbd[(int64_t)blockIdx.x * mm + r * m + c] = sW[f];
-        if (j >= a.ne) continue;
-        z2 v = sV[b * TRI + f];
-        if (b + 1 < nbh) v = zsub(v, sW[(b + 1) * TRI + f]);
-        a.An[j * mm + r * m + c] = v;
-        if (r != c) a.An[j * mm + c * m + r] = zconj(v);
-    }
+    factor_chunk<MT>(a, blockIdx.x, smem_raw);
 }
 
-// Even block j = c * nb - 1 on the boundary between CTA c-1 and CTA c of the
-// odd kernel: subtract P^H P of odd block c * nb, left by CTA c in Wbd[c].
 __global__ void __launch_bounds__(256) k_factor_fix(LevelArgs a) {
-    const int m = a.m, mm = m * m, nl = m * (m + 1) / 2;
-    const int64_t ncta = num_ctas(a.no, a.nb), total = (ncta - 1) * nl;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = 1 + e / nl;
-        const int f = (int)(e - (c - 1) * nl);
-        const int p = tri_row(f), q = f - p * (p + 1) / 2;
-        const int64_t j = c * a.nb - 1;
-        z2 v = zsub(a.An[j * mm + p * m + q], a.Wbd[c * mm + p * m + q]);
-        if (p == q) v.y = 0.0;
-        a.An[j * mm + p * m + q] = v;
-        if (p != q) a.An[j * mm + q * m + p] = zconj(v);
-    }
+    factor_fix_items(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
-
-// ------------------------------------------------------------- solve: down
 
 template <int MT>
 __global__ void __launch_bounds__(256) k_solve_down_odd(LevelArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int TRI = Tri<MT>::n;
-    const int m = a.m, k = a.k, nb = a.nb, kc = a.kc, NT = blockDim.x, tid = threadIdx.x;
-    const int mm = m * m, m2 = 2 * m, mk = m * k;
-    const int c0 = blockIdx.y * kc, kw = min(kc, k - c0);
-    const int64_t t0 = (int64_t)blockIdx.x * nb;
-    const int nbh = (int)min((int64_t)nb, a.no - t0);
-    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                           // [nb][TRI]
-    z2 *sR = sL + (size_t)nb * TRI;                                       // [nb][MT][kc] r of odd t0+b
-    z2 *sV = sR + (size_t)nb * MT * kc;                                   // [nb][MT][kc] v of even t0+b
-    z2 *sW = sV + (size_t)nb * MT * kc;                                   // [nb][MT][kc] P^H r of odd t0+b
-    double *sInv = reinterpret_cast<double *>(sW + (size_t)nb * MT * kc);  // [nb][MT]
-
-    for (int e = tid; e < nbh * mm; e += NT) {
-        const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        if (r >= c) sL[b * TRI + tri(r, c)] = a.L[(t0 + b) * mm + rem];
-    }
-    for (int e = tid; e < nbh * m; e += NT) {
-        const int b = e / m, r = e - b * m;
-        sInv[b * MT + r] = a.inv[(t0 + b) * m + r];
-    }
-    for (int e = tid; e < nbh * m * kw; e += NT) {
-        const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
-        const int64_t t = t0 + b;
-        sR[(b * MT + r) * kc + c] = a.y[(2 * t) * mk + r * k + c0 + c];
-        if (t < a.ne) sV[(b * MT + r) * kc + c] = a.y[(2 * t + 1) * mk + r * k + c0 + c];
-    }
-    __syncthreads();
-
-    for (int e = tid; e < nbh * kw; e += NT) {
-        const int b = e / kw, c = e - b * kw;
-        trsv_lower_col<MT>(sL + b * TRI, sInv + b * MT, sR + b * MT * kc + c, kc, m);
-    }
-    __syncthreads();
-
-    for (int e = tid; e < nbh * m * kw; e += NT) {
-        const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
-        a.r[(t0 + b) * mk + r * k + c0 + c] = sR[(b * MT + r) * kc + c];
-    }
-    // Z^H r: rows p < m give P^H r (kept in sW for the left even block), rows
-    // p >= m give Q^H r (subtracted from the right even block in place)
-    for (int e = tid; e < nbh * kw * m2; e += NT) {
-        const int b = e / (kw * m2), rem = e - b * (kw * m2), c = rem / m2, p = rem - c * m2;
-        const int64_t t = t0 + b;
-        if (p < m ? (t == 0) : (2 * t + 1 >= a.Nl)) continue;
-        const z2 *Zt = a.Z + t * (int64_t)(m * m2) + p;
-        const z2 *Rb = sR + b * MT * kc + c;
-        z2 acc = zmk(0.0, 0.0);
-#pragma unroll
-        for (int s = 0; s < MT; ++s)
-            if (s < m) zmac_ca(acc, __ldg(Zt + s * m2), Rb[s * kc]);
-        if (p < m) {
-            sW[(b * MT + p) * kc + c] = acc;
-        } else {
-            z2 &v = sV[(b * MT + p - m) * kc + c];
-            v = zsub(v, acc);
-        }
-    }
-    __syncthreads();
-    // v_j = (y_2j+1 - Q^H r) - P^H r; the CTA's first P^H r goes to the boundary buffer
-    for (int e = tid; e < nbh * m * kw; e += NT) {
-        const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
-        const int64_t j = t0 + b;
-        if (b == 0 && j >= 1) a.cbd[(int64_t)blockIdx.x * mk + r * k + c0 + c] = sW[r * kc + c];
-        if (j >= a.ne) continue;
-        z2 v = sV[(b * MT + r) * kc + c];
-        if (b + 1 < nbh) v = zsub(v, sW[((b + 1) * MT + r) * kc + c]);
-        a.yn[j * mk + r * k + c0 + c] = v;
-    }
+    solve_down_chunk<MT>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
-// Even block j = c * nb - 1 on a CTA boundary: subtract P^H r of odd block c * nb.
 __global__ void __launch_bounds__(256) k_solve_down_fix(LevelArgs a) {
-    const int64_t mk = (int64_t)a.m * a.k, ncta = num_ctas(a.no, a.nb), total = (ncta - 1) * mk;
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t c = 1 + e / mk, rem = e - (c - 1) * mk, j = c * a.nb - 1;
-        a.yn[j * mk + rem] = zsub(a.yn[j * mk + rem], a.cbd[c * mk + rem]);
-    }
+    solve_down_fix_items(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
-
-// --------------------------------------------------------------- solve: up
 
 template <int MT>
 __global__ void __launch_bounds__(256) k_solve_up(LevelArgs a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr int TRI = Tri<MT>::n;
-    const int m = a.m, k = a.k, nb = a.nb, kc = a.kc, NT = blockDim.x, tid = threadIdx.x;
-    const int mm = m * m, m2 = 2 * m, mk = m * k;
-    const int c0 = blockIdx.y * kc, kw = min(kc, k - c0);
-    const int64_t t0 = (int64_t)blockIdx.x * nb;
-    const int nbh = (int)min((int64_t)nb, a.no - t0);
-    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                                // [nb][TRI]
-    z2 *sW = sL + (size_t)nb * TRI;                                            // [nb][MT][kc]
-    z2 *sX = sW + (size_t)nb * MT * kc;                                        // [nb][2MT][kc]
-    double *sInv = reinterpret_cast<double *>(sX + (size_t)nb * 2 * MT * kc);  // [nb][MT]
-
-    if (a.level == 0 && *a.status != CRS_NO_FAIL) {
-        // the factorisation broke down: the result is NaN
-        const z2 nan2 = zmk(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
-        for (int e = tid; e < nbh * m * kw; e += NT) {
-            const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
-            const int64_t t = t0 + b;
-            a.x[(2 * t) * mk + r * k + c0 + c] = nan2;
-            if (t < a.ne) a.x[(2 * t + 1) * mk + r * k + c0 + c] = nan2;
-        }
-        return;
-    }
-
-    for (int e = tid; e < nbh * mm; e += NT) {
-        const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        if (r >= c) sL[b * TRI + tri(r, c)] = a.L[(t0 + b) * mm + rem];
-    }
-    for (int e = tid; e < nbh * m; e += NT) {
-        const int b = e / m, r = e - b * m;
-        sInv[b * MT + r] = a.inv[(t0 + b) * m + r];
-    }
-    for (int e = tid; e < nbh * m * kw; e += NT) {
-        const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
-        const int64_t t = t0 + b;
-        sW[(b * MT + r) * kc + c] = a.r[t * mk + r * k + c0 + c];
-        // [x_left; x_right] = [xn_{t-1}; xn_t], zero past the boundary
-        sX[(b * 2 * MT + r) * kc + c] = (t >= 1) ? a.xn[(t - 1) * mk + r * k + c0 + c] : zmk(0.0, 0.0);
-        const z2 xr = (t < a.ne) ? a.xn[t * mk + r * k + c0 + c] : zmk(0.0, 0.0);
-        sX[(b * 2 * MT + m + r) * kc + c] = xr;
-        if (t < a.ne) a.x[(2 * t + 1) * mk + r * k + c0 + c] = xr;  // even unknowns
-    }
-    __syncthreads();
-
-    // w = r - P x_left - Q x_right
-    for (int e = tid; e < nbh * m * kw; e += NT) {
-        const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
-        const int64_t t = t0 + b;
-        const z2 *Zr = a.Z + t * (int64_t)(m * m2) + r * m2;
-        const z2 *Xb = sX + b * 2 * MT * kc + c;
-        z2 acc = sW[(b * MT + r) * kc + c];
-#pragma unroll
-        for (int s = 0; s < 2 * MT; ++s)
-            if (s < m2) zmsub(acc, __ldg(Zr + s), Xb[s * kc]);
-        sW[(b * MT + r) * kc + c] = acc;
-    }
-    __syncthreads();
-
-    // x_odd = L^{-H} w
-    for (int e = tid; e < nbh * kw; e += NT) {
-        const int b = e / kw, c = e - b * kw;
-        trsv_lower_h_col<MT>(sL + b * TRI, sInv + b * MT, sW + b * MT * kc + c, kc, m);
-    }
-    __syncthreads();
-    for (int e = tid; e < nbh * m * kw; e += NT) {
-        const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
-        a.x[(2 * (t0 + b)) * mk + r * k + c0 + c] = sW[(b * MT + r) * kc + c];
-    }
+    solve_up_chunk<MT>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // ------------------------------------------------------------------ adjoint

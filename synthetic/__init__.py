@@ -109,3 +109,83 @@ def gen_batch(Ns, ms, ks, seed: int):
     """List of (A, B, y) for each system; system i uses seed*100003 + i."""
     return [gen_system(int(n), int(m), int(k), seed * 100003 + i)
             for i, (n, m, k) in enumerate(zip(Ns, ms, ks))]
+
+
+def batch_offsets(Ns, ms, ks):
+    """Packed layout of a batch (systems back to back in order): element
+    offsets of each system in A, B, y/x and the totals."""
+    Ns = np.asarray(Ns, np.int64)
+    ms = np.asarray(ms, np.int64)
+    ks = np.asarray(ks, np.int64)
+    sa, sb, sy = Ns * ms * ms, (Ns - 1) * ms * ms, Ns * ms * ks
+    off = lambda s: np.concatenate([[0], np.cumsum(s)[:-1]]).astype(np.int64)
+    return off(sa), off(sb), off(sy), (int(sa.sum()), int(sb.sum()), int(sy.sum()))
+
+
+def gen_batch_device(Ns, ms, ks, seed: int, device="cuda", shift: float = 1.0):
+    """The same recipe as gen_system for a whole batch, drawn with torch's
+    generator on `device` (fast for batches of ~100 GB) and packed back to
+    back (batch_offsets).  Returns packed complex128 tensors (A, B, y)."""
+    import torch
+    Ns = np.asarray(Ns, np.int64)
+    ms = np.asarray(ms, np.int64)
+    ks = np.asarray(ks, np.int64)
+    offA, offB, offY, (nA, nB, nY) = batch_offsets(Ns, ms, ks)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    A = torch.empty(nA, dtype=torch.complex128, device=device)
+    B = torch.empty(max(nB, 1), dtype=torch.complex128, device=device)
+    y = torch.empty(nY, dtype=torch.complex128, device=device)
+
+    def cn_t(shape):
+        z = torch.randn(tuple(shape) + (2,), generator=gen, device=device, dtype=torch.float64) * np.sqrt(0.5)
+        return torch.view_as_complex(z)
+
+    for m in sorted(set(ms.tolist())):
+        sel = np.nonzero(ms == m)[0]
+        nblk = int(Ns[sel].sum())
+        nbb = int((Ns[sel] - 1).sum())
+        Bc = cn_t((nbb, m, m)) * (0.5 / np.sqrt(m))
+        Gc = cn_t((nblk, m, m))
+        Ac = Gc @ Gc.conj().transpose(1, 2) / m
+        del Gc
+        nb = torch.empty(nbb, dtype=torch.float64, device=device)
+        for c0 in range(0, nbb, 16384):          # cuSOLVER's batched eigensolver wants modest batches
+            bc = Bc[c0:c0 + 16384]
+            nb[c0:c0 + 16384] = torch.sqrt(torch.linalg.eigvalsh(bc.conj().transpose(1, 2) @ bc)[:, -1].clamp_min(0.0))
+        # per-block diagonal shift: ||B_{j-1}|| + ||B_j|| + shift, within each system
+        dsh = torch.full((nblk,), float(shift), dtype=torch.float64, device=device)
+        a0 = b0 = 0
+        left_idx, right_idx, nb_idx = [], [], []
+        for i in sel:
+            N = int(Ns[i])
+            if N > 1:
+                left_idx.append(np.arange(a0 + 1, a0 + N))     # block j >= 1 gets ||B_{j-1}||
+                right_idx.append(np.arange(a0, a0 + N - 1))    # block j <= N-2 gets ||B_j||
+                nb_idx.append(np.arange(b0, b0 + N - 1))
+            a0 += N
+            b0 += N - 1
+        if nb_idx:
+            li = torch.from_numpy(np.concatenate(left_idx)).to(device)
+            ri = torch.from_numpy(np.concatenate(right_idx)).to(device)
+            bi = torch.from_numpy(np.concatenate(nb_idx)).to(device)
+            dsh.index_add_(0, li, nb[bi])
+            dsh.index_add_(0, ri, nb[bi])
+        idx = torch.arange(m, device=device)
+        Ac[:, idx, idx] += dsh[:, None].to(torch.complex128)
+        Ac = 0.5 * (Ac + Ac.conj().transpose(1, 2))
+        Ac[:, idx, idx] = Ac[:, idx, idx].real.to(torch.complex128)
+        ktot = int((Ns[sel] * m * ks[sel]).sum())
+        yc = cn_t((ktot,))
+        a0 = b0 = y0 = 0
+        for i in sel:
+            N, k = int(Ns[i]), int(ks[i])
+            A[offA[i]:offA[i] + N * m * m] = Ac[a0:a0 + N].reshape(-1)
+            if N > 1:
+                B[offB[i]:offB[i] + (N - 1) * m * m] = Bc[b0:b0 + N - 1].reshape(-1)
+            y[offY[i]:offY[i] + N * m * k] = yc[y0:y0 + N * m * k]
+            a0 += N
+            b0 += N - 1
+            y0 += N * m * k
+        del Ac, Bc, yc
+    return A, B, y
