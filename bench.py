@@ -241,6 +241,69 @@ def run_batched(args):
     print(json.dumps(line), flush=True)
 
 
+ADJ_N, ADJ_M, ADJ_K, ADJ_SEED = 1 << 16, 16, 8, 2000
+ADJ_WORKLOAD = ("differentiation: factor + solve + crsolve_backward (re-solve and gA, gB outer products), "
+                "N=2^16, m=16, k=8, complex128, loss Re sum(conj(c) x)")
+
+
+def adjoint_flops_per_row(m: int, k: int) -> float:
+    """gA (lower triangle, two k-term products per entry) + gB (full, two)."""
+    return 8.0 * (m * (m + 1) / 2 + m * m) * 2 * k
+
+
+def run_adjoint(args):
+    import torch
+    import paper_1807_00370_gb300 as crs
+    torch.cuda.set_device(0)
+    N, m, k = ADJ_N, ADJ_M, ADJ_K
+    A, B, y = synthetic.gen_system(N, m, k, seed=ADJ_SEED)
+    c = synthetic.gen_cotangent(N, m, k, seed=ADJ_SEED)
+    dA, dB, dy, dc = (torch.from_numpy(a).cuda() for a in (A, B, y, c))
+    plan = crs.Plan(N, m, k)
+    x = torch.empty_like(dy)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        crs.crsolve_factor(plan, dA, dB)
+        crs.crsolve_solve(plan, dy, x)
+        return crs.crsolve_backward(plan, x, dc)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    launches0 = crs.crsolve_launch_count(plan)
+    crs.crsolve_timing_enable(plan, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    recs = crs.crsolve_timing_read(plan)
+    crs.crsolve_timing_enable(plan, False)
+    ms_step = e0.elapsed_time(e1) / args.steps
+    adj_ms = sum(r[3] for r in recs if r[0] == "adjoint_outer") / args.steps
+    flops = N * (flops_per_block_row(m, k) + flops_solve_per_odd_block(m, k) + adjoint_flops_per_row(m, k))
+    peak_tf = FP64_PEAK_GFLOPS / 1e3
+    by = {}
+    for kind, _, _, kms in recs:
+        by[kind] = by.get(kind, 0.0) + kms / args.steps
+    line = {
+        "metric": "block-rows/s", "value": N / (ms_step * 1e-3), "unit": "block-rows/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        "config": {"workload": ADJ_WORKLOAD, "N": N, "m": m, "k": k, "seed": ADJ_SEED},
+        "roofline": {"bound": "alu", "kernel": "whole forward + backward step",
+                     "achieved": flops / (ms_step * 1e-3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
+                     "frac": flops / (ms_step * 1e-3) / 1e12 / peak_tf, "traffic": None,
+                     "adjoint_outer_frac": (N * adjoint_flops_per_row(m, k) / (adj_ms * 1e-3) / 1e12 / peak_tf)
+                     if adj_ms else None},
+        "kernels": {kk: {"ms_per_step": v} for kk, v in by.items()},
+        "gpu_launches": crs.crsolve_launch_count(plan) - launches0, "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -250,7 +313,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "adjoint"])
     ap.add_argument("--nsys", type=int, default=4096, help="systems of the batched workload")
     ap.add_argument("--log2n", type=int, default=20,
                     help="log2 of the block count (smaller cases are for profiling only)")
@@ -259,6 +322,8 @@ def main():
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "adjoint":
+        return run_adjoint(args)
 
     import torch
     import paper_1807_00370_gb300 as crs
