@@ -304,6 +304,60 @@ def run_adjoint(args):
     print(json.dumps(line), flush=True)
 
 
+MIX_N, MIX_M, MIX_K, MIX_SEED = 1 << 14, 64, 32, 4000
+MIX_WORKLOAD = ("precision: FP32 fine levels + FP64 coarse levels, FP64 residual and iterative refinement, "
+                "N=2^14, m=64, k=32, complex, kappa in {1e2, 1e4, 1e6}")
+
+
+def run_mixed(args):
+    """For each kappa: the mixed form and the plain FP64 path on the same system."""
+    import torch
+    import paper_1807_00370_gb300 as crs
+    from paper_1807_00370_gb300 import _native as nat
+    torch.cuda.set_device(0)
+    shifts = json.load(open(os.path.join(ROOT, "tests", "golden", "kappa_shifts.json")))["mixed_N2p14_m64_k32"]
+    N, m, k = MIX_N, MIX_M, MIX_K
+    stream = torch.cuda.current_stream()
+    runs = []
+    for kap in ("1e+02", "1e+04", "1e+06"):
+        A, B, y = synthetic.gen_system(N, m, k, seed=MIX_SEED, shift=shifts["shifts"][kap])
+        dA, dB, dy = (torch.from_numpy(a).cuda() for a in (A, B, y))
+        res = {}
+        for name, prec in (("mixed", nat.CRSOLVE_MIXED), ("fp64", nat.CRSOLVE_FP64)):
+            plan = crs.Plan(N, m, k, precision=prec)
+            x = torch.empty_like(dy)
+            for _ in range(max(args.warmup, 1)):
+                crs.crsolve_factor(plan, dA, dB)
+                crs.crsolve_solve(plan, dy, x)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(args.steps):
+                crs.crsolve_factor(plan, dA, dB)
+                crs.crsolve_solve(plan, dy, x)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            res[name] = {"ms": e0.elapsed_time(e1) / args.steps, "x": x,
+                         "stats": crs.crsolve_mixed_stats(plan) if prec == nat.CRSOLVE_MIXED else None}
+        err = float((torch.linalg.norm(res["mixed"]["x"] - res["fp64"]["x"]) / torch.linalg.norm(res["fp64"]["x"])).item())
+        runs.append({"kappa": float(kap), "shift": shifts["shifts"][kap], "mixed_ms": res["mixed"]["ms"],
+                     "fp64_ms": res["fp64"]["ms"], "speedup": res["fp64"]["ms"] / res["mixed"]["ms"],
+                     "rel_err_vs_fp64_path": err, "refinement": res["mixed"]["stats"]})
+    peak_tf = FP64_PEAK_GFLOPS / 1e3
+    best = min(runs, key=lambda r: r["mixed_ms"])
+    line = {
+        "metric": "block-rows/s", "value": N / (runs[0]["mixed_ms"] * 1e-3), "unit": "block-rows/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": runs[0]["mixed_ms"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 fine levels / c128",
+        "data": "synthetic", "config": {"workload": MIX_WORKLOAD, "N": N, "m": m, "k": k, "seed": MIX_SEED,
+                                        "value_is": "kappa ~ 1e2"},
+        "runs": runs,
+        "fp64_path_frac_of_peak": N * flops_per_block_row(m, k) / (runs[0]["fp64_ms"] * 1e-3) / 1e12 / peak_tf,
+        "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -313,7 +367,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "adjoint"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "adjoint", "mixed"])
     ap.add_argument("--nsys", type=int, default=4096, help="systems of the batched workload")
     ap.add_argument("--log2n", type=int, default=20,
                     help="log2 of the block count (smaller cases are for profiling only)")
@@ -324,6 +378,8 @@ def main():
         return run_batched(args)
     if args.workload == "adjoint":
         return run_adjoint(args)
+    if args.workload == "mixed":
+        return run_mixed(args)
 
     import torch
     import paper_1807_00370_gb300 as crs

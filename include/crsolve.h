@@ -264,6 +264,22 @@ int crsolve_timing_enable(crsolve_plan p, int32_t enable);
  * in out, the number available in *count; then clears the records. */
 int crsolve_timing_read(crsolve_plan p, crsolve_kernel_time *out, int32_t cap, int32_t *count);
 
+/*
+ * Mixed precision (plans created with CRSOLVE_MIXED).  The fine levels of the
+ * reduction (all levels with more than 64 blocks) are factored and solved in
+ * FP32; the coarsest levels, the breakdown decision, the residual
+ * r = y - A x and the iterative refinement x += A~^{-1} r are FP64.  In this
+ * mode crsolve_factor and crsolve_solve synchronise the stream, and A and B
+ * must stay valid and unchanged until the plan is re-factored or destroyed
+ * (the residual reads them).  A breakdown in the FP32 levels is re-decided by
+ * an FP64 factorisation, and refinement that does not contract falls back to
+ * the FP64 path, so the flags are always the FP64 ones.
+ * crsolve_mixed_stats reports the last solve: FP64 residuals computed,
+ * delta = |last correction|_inf / |x|_inf, rho = observed contraction per
+ * refinement step, and whether the FP64 path was used instead.
+ */
+int crsolve_mixed_stats(crsolve_plan p, int32_t *iterations, double *delta, double *rho, int32_t *fp64_fallback);
+
 /* Kernels this plan has launched since it was created. */
 int crsolve_launch_count(crsolve_plan p, int64_t *count);
 

@@ -63,6 +63,8 @@ SIGNATURES = {
     "crsolve_timing_enable": (ctypes.c_int, [_P, _I32]),
     "crsolve_timing_read": (ctypes.c_int, [_P, ctypes.POINTER(CrsolveKernelTime), _I32, ctypes.POINTER(_I32)]),
     "crsolve_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
+    "crsolve_mixed_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double),
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I32)]),
     "crsolve_tile_set": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32]),
     "crsolve_batch_create": (ctypes.c_int, [_I32, _P, _P, _P, ctypes.POINTER(_P)]),
     "crsolve_batch_tile_set": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32]),

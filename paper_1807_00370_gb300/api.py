@@ -16,7 +16,7 @@ from . import _native as nat
 __all__ = ["Plan", "crsolve_plan_create", "crsolve_factor", "crsolve_solve", "crsolve_backward",
            "crsolve_info_get", "crsolve_solve_host", "crsolve_plan_levels",
            "crsolve_debug_level_system", "crsolve_timing_enable", "crsolve_timing_read",
-           "crsolve_launch_count", "crsolve_tile_set", "crsolve_tile_get", "crsolve_solve_noalloc", "solve", "CRSolveFn",
+           "crsolve_launch_count", "crsolve_mixed_stats", "crsolve_tile_set", "crsolve_tile_get", "crsolve_solve_noalloc", "solve", "CRSolveFn",
            "NotPositiveDefinite"]
 
 
@@ -194,6 +194,15 @@ def crsolve_timing_read(plan: Plan, cap: int = 1 << 16):
     n = ctypes.c_int32()
     nat.check(nat.load().crsolve_timing_read(plan.handle, buf, cap, ctypes.byref(n)), "crsolve_timing_read")
     return [(nat.KERNEL_KINDS[buf[i].kind], buf[i].level, buf[i].units, buf[i].ms) for i in range(min(n.value, cap))]
+
+
+def crsolve_mixed_stats(plan: Plan) -> dict:
+    it, fb = ctypes.c_int32(), ctypes.c_int32()
+    dl, rho = ctypes.c_double(), ctypes.c_double()
+    nat.check(nat.load().crsolve_mixed_stats(plan.handle, ctypes.byref(it), ctypes.byref(dl), ctypes.byref(rho),
+                                             ctypes.byref(fb)), "crsolve_mixed_stats")
+    return {"iterations": int(it.value), "delta": float(dl.value), "rho": float(rho.value),
+            "fp64_fallback": bool(fb.value)}
 
 
 def crsolve_launch_count(plan: Plan) -> int:

@@ -138,7 +138,7 @@ __device__ __noinline__ void run_system(const BatchArgs &ba, const SysDesc &d, i
         }
         __syncthreads();
         for (int64_t c = 0, nc = crs_num_ctas(sa.no, sa.nb); c < nc; ++c) {
-            factor_chunk<MT>(sa, c, smem);
+            factor_chunk<MT, double>(sa, c, smem);
             __syncthreads();
         }
         if (threadIdx.x == 0) {
@@ -149,7 +149,7 @@ __device__ __noinline__ void run_system(const BatchArgs &ba, const SysDesc &d, i
         const int ncc = (k + sa.kc - 1) / sa.kc;
         for (int64_t c = 0, nc = crs_num_ctas(sa.no, sa.nb); c < nc; ++c)
             for (int cc = 0; cc < ncc; ++cc) {
-                solve_down_chunk<MT>(sa, c, cc, smem);
+                solve_down_chunk<MT, double>(sa, c, cc, smem);
                 __syncthreads();
             }
     }
@@ -164,7 +164,7 @@ __device__ __noinline__ void run_system(const BatchArgs &ba, const SysDesc &d, i
         const int ncc = (k + sa.kc - 1) / sa.kc;
         for (int64_t c = 0, nc = crs_num_ctas(sa.no, sa.nb); c < nc; ++c)
             for (int cc = 0; cc < ncc; ++cc) {
-                solve_up_chunk<MT>(sa, c, cc, smem);
+                solve_up_chunk<MT, double>(sa, c, cc, smem);
                 __syncthreads();
             }
     }
@@ -240,8 +240,8 @@ size_t batch_smem(const crsolve_batch_s *b) {
     for (const auto &d : b->sys) present[d.mt == 4 ? 0 : d.mt == 8 ? 1 : d.mt == 16 ? 2 : d.mt == 32 ? 3 : 4] = true;
     for (int i = 0; i < 5; ++i) {
         if (!present[i]) continue;
-        smem = std::max(smem, crs::factor_smem_bytes(kMtList[i], b->tiles.nbf[i]));
-        smem = std::max(smem, crs::solve_smem_bytes(kMtList[i], b->tiles.nbs[i], b->tiles.kc[i], 3));
+        smem = std::max(smem, crs::factor_smem_bytes(kMtList[i], b->tiles.nbf[i], 8));
+        smem = std::max(smem, crs::solve_smem_bytes(kMtList[i], b->tiles.nbs[i], b->tiles.kc[i], 3, 8));
     }
     return smem;
 }

@@ -40,17 +40,17 @@ template <int MT> struct Tri { static constexpr int n = MT * (MT + 1) / 2; };
 // --------------------------------------------------------------- helpers
 
 // z := L^{-1} z for one column z (shared memory, stride ld); L packed lower.
-template <int MT>
-__device__ __forceinline__ void trsv_lower_col(const z2 *Lb, const double *ivb, z2 *col, int ld, int m) {
+template <int MT, class R, class C>
+__device__ __forceinline__ void trsv_lower_col(const C *Lb, const R *ivb, C *col, int ld, int m) {
     if constexpr (MT <= 16) {
-        z2 z[MT];
+        C z[MT];
 #pragma unroll
         for (int r = 0; r < MT; ++r)
             if (r < m) z[r] = col[r * ld];
 #pragma unroll
         for (int r = 0; r < MT; ++r) {
             if (r < m) {
-                z2 acc = z[r];
+                C acc = z[r];
 #pragma unroll
                 for (int s = 0; s < r; ++s) zmsub(acc, Lb[tri(r, s)], z[s]);
                 z[r] = zscale(acc, ivb[r]);
@@ -61,7 +61,7 @@ __device__ __forceinline__ void trsv_lower_col(const z2 *Lb, const double *ivb, 
             if (r < m) col[r * ld] = z[r];
     } else {
         for (int r = 0; r < m; ++r) {
-            z2 acc = col[r * ld];
+            C acc = col[r * ld];
             for (int s = 0; s < r; ++s) zmsub(acc, Lb[tri(r, s)], col[s * ld]);
             col[r * ld] = zscale(acc, ivb[r]);
         }
@@ -69,17 +69,17 @@ __device__ __forceinline__ void trsv_lower_col(const z2 *Lb, const double *ivb, 
 }
 
 // z := L^{-H} z for one column z (shared memory, stride ld); L packed lower.
-template <int MT>
-__device__ __forceinline__ void trsv_lower_h_col(const z2 *Lb, const double *ivb, z2 *col, int ld, int m) {
+template <int MT, class R, class C>
+__device__ __forceinline__ void trsv_lower_h_col(const C *Lb, const R *ivb, C *col, int ld, int m) {
     if constexpr (MT <= 16) {
-        z2 z[MT];
+        C z[MT];
 #pragma unroll
         for (int r = 0; r < MT; ++r)
             if (r < m) z[r] = col[r * ld];
 #pragma unroll
         for (int r = MT - 1; r >= 0; --r) {
             if (r < m) {
-                z2 acc = z[r];
+                C acc = z[r];
 #pragma unroll
                 for (int s = r + 1; s < MT; ++s)
                     if (s < m) zmsub_ca(acc, Lb[tri(s, r)], z[s]);
@@ -91,7 +91,7 @@ __device__ __forceinline__ void trsv_lower_h_col(const z2 *Lb, const double *ivb
             if (r < m) col[r * ld] = z[r];
     } else {
         for (int r = m - 1; r >= 0; --r) {
-            z2 acc = col[r * ld];
+            C acc = col[r * ld];
             for (int s = r + 1; s < m; ++s) zmsub_ca(acc, Lb[tri(s, r)], col[s * ld]);
             col[r * ld] = zscale(acc, ivb[r]);
         }
@@ -102,17 +102,18 @@ __device__ __forceinline__ void trsv_lower_h_col(const z2 *Lb, const double *ivb
 
 // One chunk of nb odd blocks (chunk index `chunk`) of a factor level, run by
 // the whole CTA.  Uses the CTA's shared memory from smem_raw.
-template <int MT>
-__device__ __forceinline__ void factor_chunk(const LevelArgs &a, int64_t chunk, unsigned char *smem_raw) {
+template <int MT, class R>
+__device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chunk, unsigned char *smem_raw) {
+    using C = cplx_t<R>;
     constexpr int LDZ = 2 * MT, TRI = Tri<MT>::n;
     const int m = a.m, nb = a.nb, NT = blockDim.x, tid = threadIdx.x;
     const int mm = m * m, m2 = 2 * m;
     const int64_t t0 = chunk * nb;
     const int nbh = (int)min((int64_t)nb, a.no - t0);
-    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                        // [nb][TRI] L, later P^H P
-    z2 *sV = sL + (size_t)nb * TRI;                                    // [nb][TRI] even block t0+b
-    z2 *sZ = sV + (size_t)nb * TRI;                                    // [nb][MT][2MT] [P | Q]
-    double *sInv = reinterpret_cast<double *>(sZ + (size_t)nb * MT * LDZ);  // [nb][MT]
+    C *sL = reinterpret_cast<C *>(smem_raw);                        // [nb][TRI] L, later P^H P
+    C *sV = sL + (size_t)nb * TRI;                                    // [nb][TRI] even block t0+b
+    C *sZ = sV + (size_t)nb * TRI;                                    // [nb][MT][2MT] [P | Q]
+    R *sInv = reinterpret_cast<R *>(sZ + (size_t)nb * MT * LDZ);  // [nb][MT]
 
     // stage the lower triangles of A_2t and A_2t+1, B_{2t-1} (P part) and
     // B_{2t}^H (Q part)
@@ -122,13 +123,13 @@ __device__ __forceinline__ void factor_chunk(const LevelArgs &a, int64_t chunk, 
         if (r >= c) {
             sL[b * TRI + tri(r, c)] = a.A[pos * mm + rem];
             if (t < a.ne) {
-                z2 v = a.A[(pos + 1) * mm + rem];
-                if (r == c) v.y = 0.0;
+                C v = a.A[(pos + 1) * mm + rem];
+                if (r == c) v.y = R(0);
                 sV[b * TRI + tri(r, c)] = v;
             }
         }
-        sZ[(b * MT + r) * LDZ + c] = (pos >= 1) ? a.B[(pos - 1) * mm + rem] : zmk(0.0, 0.0);
-        sZ[(b * MT + c) * LDZ + m + r] = (pos + 1 < a.Nl) ? zconj(a.B[pos * mm + rem]) : zmk(0.0, 0.0);
+        sZ[(b * MT + r) * LDZ + c] = (pos >= 1) ? a.B[(pos - 1) * mm + rem] : zmk(R(0), R(0));
+        sZ[(b * MT + c) * LDZ + m + r] = (pos + 1 < a.Nl) ? zconj(a.B[pos * mm + rem]) : zmk(R(0), R(0));
     }
     __syncthreads();
 
@@ -142,21 +143,21 @@ __device__ __forceinline__ void factor_chunk(const LevelArgs &a, int64_t chunk, 
         for (int e = tid; e < dpad + nbh * below; e += NT) {
             if (e < nbh) {
                 const int b = e;
-                z2 *Lb = sL + b * TRI;
-                double d = Lb[tri(c, c)].x;
+                C *Lb = sL + b * TRI;
+                R d = Lb[tri(c, c)].x;
                 for (int s = 0; s < c; ++s) {
-                    const z2 l = Lb[tri(c, s)];
-                    d = fma(-l.x, l.x, d);
-                    d = fma(-l.y, l.y, d);
+                    const C l = Lb[tri(c, s)];
+                    d = fmx(-l.x, l.x, d);
+                    d = fmx(-l.y, l.y, d);
                 }
-                if (!(d > 0.0)) report_fail(a.status, a.level, 2 * (t0 + b) + 1);
-                const double iv = rsqrt(d);
+                if (!(d > R(0))) report_fail(a.status, a.level, 2 * (t0 + b) + 1);
+                const R iv = rsq(d);
                 sInv[b * MT + c] = iv;
-                Lb[tri(c, c)] = zmk(d * iv, 0.0);
+                Lb[tri(c, c)] = zmk(d * iv, R(0));
             } else if (e >= dpad) {
                 const int e2 = e - dpad, b = e2 / below, r = c + 1 + (e2 - b * below);
-                z2 *Lb = sL + b * TRI;
-                z2 u = Lb[tri(r, c)];
+                C *Lb = sL + b * TRI;
+                C u = Lb[tri(r, c)];
                 for (int s = 0; s < c; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(c, s)]);
                 Lb[tri(r, c)] = u;
             }
@@ -164,7 +165,7 @@ __device__ __forceinline__ void factor_chunk(const LevelArgs &a, int64_t chunk, 
         __syncthreads();
         for (int e = tid; e < nbh * below; e += NT) {
             const int b = e / below, r = c + 1 + (e - b * below);
-            z2 *p = sL + b * TRI + tri(r, c);
+            C *p = sL + b * TRI + tri(r, c);
             *p = zscale(*p, sInv[b * MT + c]);
         }
         __syncthreads();
@@ -175,14 +176,14 @@ __device__ __forceinline__ void factor_chunk(const LevelArgs &a, int64_t chunk, 
         const int b = e / m2, col = e - b * m2;
         const int64_t pos = 2 * (t0 + b);
         if (col < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
-        trsv_lower_col<MT>(sL + b * TRI, sInv + b * MT, sZ + b * MT * LDZ + col, LDZ, m);
+        trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sZ + b * MT * LDZ + col, LDZ, m);
     }
     __syncthreads();
 
     // keep L, 1/diag(L) and Z for the solves
     for (int e = tid; e < nbh * mm; e += NT) {
         const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        a.L[(t0 + b) * mm + rem] = (r >= c) ? sL[b * TRI + tri(r, c)] : zmk(0.0, 0.0);
+        a.L[(t0 + b) * mm + rem] = (r >= c) ? sL[b * TRI + tri(r, c)] : zmk(R(0), R(0));
     }
     for (int e = tid; e < nbh * m; e += NT) {
         const int b = e / m, r = e - b * m;
@@ -199,23 +200,23 @@ __device__ __forceinline__ void factor_chunk(const LevelArgs &a, int64_t chunk, 
     // term instead of 4).  Parts: Q^H Q is subtracted from the right even
     // block V_t in place, P^H P is kept in sW (the L buffer, free now) for the
     // left even block, and Q^H P = -F goes to the next level's B.
-    z2 *sW = sL;
+    C *sW = sL;
     const int ndiag = nbh * m2, dpadh = (ndiag + 31) & ~31, noff = m2 * (m2 - 1) / 2;
     for (int e = tid; e < dpadh + nbh * noff; e += NT) {
         if (e < ndiag) {
             const int b = e / m2, p = e - b * m2;
             const int64_t t = t0 + b;
             if (p < m ? (t == 0) : (2 * t + 1 >= a.Nl)) continue;
-            const z2 *Zb = sZ + b * MT * LDZ + p;
-            double d = 0.0;
+            const C *Zb = sZ + b * MT * LDZ + p;
+            R d = R(0);
 #pragma unroll
             for (int s = 0; s < MT; ++s)
                 if (s < m) {
-                    const z2 v = Zb[s * LDZ];
-                    d = fma(v.x, v.x, d);
-                    d = fma(v.y, v.y, d);
+                    const C v = Zb[s * LDZ];
+                    d = fmx(v.x, v.x, d);
+                    d = fmx(v.y, v.y, d);
                 }
-            if (p < m) sW[b * TRI + tri(p, p)] = zmk(d, 0.0);
+            if (p < m) sW[b * TRI + tri(p, p)] = zmk(d, R(0));
             else sV[b * TRI + tri(p - m, p - m)].x -= d;
         } else if (e >= dpadh) {
             const int e2 = e - dpadh, b = e2 / noff, g = e2 - b * noff;
@@ -224,15 +225,15 @@ __device__ __forceinline__ void factor_chunk(const LevelArgs &a, int64_t chunk, 
             const bool hasL = t >= 1, hasR = 2 * t + 1 < a.Nl;
             const int kind = (p < m) ? 0 : (q >= m ? 1 : 2);  // P^H P, Q^H Q, Q^H P
             if (kind == 0 ? !hasL : (kind == 1 ? !hasR : !(hasL && hasR))) continue;
-            const z2 *Zb = sZ + b * MT * LDZ;
-            z2 acc = zmk(0.0, 0.0);
+            const C *Zb = sZ + b * MT * LDZ;
+            C acc = zmk(R(0), R(0));
 #pragma unroll
             for (int s = 0; s < MT; ++s)
                 if (s < m) zmac_ca(acc, Zb[s * LDZ + p], Zb[s * LDZ + q]);
             if (kind == 0) {
                 sW[b * TRI + tri(p, q)] = acc;
             } else if (kind == 1) {
-                z2 &v = sV[b * TRI + tri(p - m, q - m)];
+                C &v = sV[b * TRI + tri(p - m, q - m)];
                 v = zsub(v, acc);
             } else {
                 a.Bn[(t - 1) * mm + (p - m) * m + q] = zneg(acc);
@@ -253,8 +254,8 @@ __device__ __forceinline__ void factor_chunk(const LevelArgs &a, int64_t chunk, 
             if (a.inline_fix) {
                 // the previous chunk (same CTA, earlier) left V_{j-1} = A - Q^H Q
                 const int64_t o = (j - 1) * mm;
-                z2 v = zsub(a.An[o + r * m + c], sW[f]);
-                if (r == c) v.y = 0.0;
+                C v = zsub(a.An[o + r * m + c], sW[f]);
+                if (r == c) v.y = R(0);
                 a.An[o + r * m + c] = v;
                 if (r != c) a.An[o + c * m + r] = zconj(v);
             } else {
@@ -262,7 +263,7 @@ __device__ __forceinline__ void factor_chunk(const LevelArgs &a, int64_t chunk, 
             }
         }
         if (j >= a.ne) continue;
-        z2 v = sV[b * TRI + f];
+        C v = sV[b * TRI + f];
         if (b + 1 < nbh) v = zsub(v, sW[(b + 1) * TRI + f]);
         a.An[j * mm + r * m + c] = v;
         if (r != c) a.An[j * mm + c * m + r] = zconj(v);
@@ -272,7 +273,9 @@ __device__ __forceinline__ void factor_chunk(const LevelArgs &a, int64_t chunk, 
 // Even block j = c * nb - 1 on the boundary between chunk c-1 and chunk c of
 // a factor level: subtract P^H P of odd block c * nb, left by chunk c in
 // Wbd[c].  Items e = first, first + stride, ... of (chunks - 1) * m(m+1)/2.
-__device__ __forceinline__ void factor_fix_items(const LevelArgs &a, int64_t first, int64_t stride) {
+template <class R>
+__device__ __forceinline__ void factor_fix_items(const LevelArgsT<R> &a, int64_t first, int64_t stride) {
+    using C = cplx_t<R>;
     const int m = a.m, mm = m * m, nl = m * (m + 1) / 2;
     const int64_t ncta = crs_num_ctas(a.no, a.nb), total = (ncta - 1) * nl;
     for (int64_t e = first; e < total; e += stride) {
@@ -280,8 +283,8 @@ __device__ __forceinline__ void factor_fix_items(const LevelArgs &a, int64_t fir
         const int f = (int)(e - (c - 1) * nl);
         const int p = tri_row(f), q = f - p * (p + 1) / 2;
         const int64_t j = c * a.nb - 1;
-        z2 v = zsub(a.An[j * mm + p * m + q], a.Wbd[c * mm + p * m + q]);
-        if (p == q) v.y = 0.0;
+        C v = zsub(a.An[j * mm + p * m + q], a.Wbd[c * mm + p * m + q]);
+        if (p == q) v.y = R(0);
         a.An[j * mm + p * m + q] = v;
         if (p != q) a.An[j * mm + q * m + p] = zconj(v);
     }
@@ -291,20 +294,21 @@ __device__ __forceinline__ void factor_fix_items(const LevelArgs &a, int64_t fir
 
 // One chunk of nb odd blocks and right-hand-side columns [cchunk*kc, +kc)
 // of a down-sweep level, run by the whole CTA.
-template <int MT>
-__device__ __forceinline__ void solve_down_chunk(const LevelArgs &a, int64_t chunk, int cchunk,
+template <int MT, class R>
+__device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t chunk, int cchunk,
                                                  unsigned char *smem_raw) {
+    using C = cplx_t<R>;
     constexpr int TRI = Tri<MT>::n;
     const int m = a.m, k = a.k, nb = a.nb, kc = a.kc, NT = blockDim.x, tid = threadIdx.x;
     const int mm = m * m, m2 = 2 * m, mk = m * k;
     const int c0 = cchunk * kc, kw = min(kc, k - c0);
     const int64_t t0 = chunk * nb;
     const int nbh = (int)min((int64_t)nb, a.no - t0);
-    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                           // [nb][TRI]
-    z2 *sR = sL + (size_t)nb * TRI;                                       // [nb][MT][kc] r of odd t0+b
-    z2 *sV = sR + (size_t)nb * MT * kc;                                   // [nb][MT][kc] v of even t0+b
-    z2 *sW = sV + (size_t)nb * MT * kc;                                   // [nb][MT][kc] P^H r of odd t0+b
-    double *sInv = reinterpret_cast<double *>(sW + (size_t)nb * MT * kc);  // [nb][MT]
+    C *sL = reinterpret_cast<C *>(smem_raw);                           // [nb][TRI]
+    C *sR = sL + (size_t)nb * TRI;                                       // [nb][MT][kc] r of odd t0+b
+    C *sV = sR + (size_t)nb * MT * kc;                                   // [nb][MT][kc] v of even t0+b
+    C *sW = sV + (size_t)nb * MT * kc;                                   // [nb][MT][kc] P^H r of odd t0+b
+    R *sInv = reinterpret_cast<R *>(sW + (size_t)nb * MT * kc);  // [nb][MT]
 
     for (int e = tid; e < nbh * mm; e += NT) {
         const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
@@ -324,7 +328,7 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgs &a, int64_t chu
 
     for (int e = tid; e < nbh * kw; e += NT) {
         const int b = e / kw, c = e - b * kw;
-        trsv_lower_col<MT>(sL + b * TRI, sInv + b * MT, sR + b * MT * kc + c, kc, m);
+        trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sR + b * MT * kc + c, kc, m);
     }
     __syncthreads();
 
@@ -338,16 +342,16 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgs &a, int64_t chu
         const int b = e / (kw * m2), rem = e - b * (kw * m2), c = rem / m2, p = rem - c * m2;
         const int64_t t = t0 + b;
         if (p < m ? (t == 0) : (2 * t + 1 >= a.Nl)) continue;
-        const z2 *Zt = a.Z + t * (int64_t)(m * m2) + p;
-        const z2 *Rb = sR + b * MT * kc + c;
-        z2 acc = zmk(0.0, 0.0);
+        const C *Zt = a.Z + t * (int64_t)(m * m2) + p;
+        const C *Rb = sR + b * MT * kc + c;
+        C acc = zmk(R(0), R(0));
 #pragma unroll
         for (int s = 0; s < MT; ++s)
             if (s < m) zmac_ca(acc, __ldg(Zt + s * m2), Rb[s * kc]);
         if (p < m) {
             sW[(b * MT + p) * kc + c] = acc;
         } else {
-            z2 &v = sV[(b * MT + p - m) * kc + c];
+            C &v = sV[(b * MT + p - m) * kc + c];
             v = zsub(v, acc);
         }
     }
@@ -365,14 +369,15 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgs &a, int64_t chu
             }
         }
         if (j >= a.ne) continue;
-        z2 v = sV[(b * MT + r) * kc + c];
+        C v = sV[(b * MT + r) * kc + c];
         if (b + 1 < nbh) v = zsub(v, sW[((b + 1) * MT + r) * kc + c]);
         a.yn[j * mk + r * k + c0 + c] = v;
     }
 }
 
 // Even block j = c * nb - 1 on a chunk boundary: subtract P^H r of odd block c * nb.
-__device__ __forceinline__ void solve_down_fix_items(const LevelArgs &a, int64_t first, int64_t stride) {
+template <class R>
+__device__ __forceinline__ void solve_down_fix_items(const LevelArgsT<R> &a, int64_t first, int64_t stride) {
     const int64_t mk = (int64_t)a.m * a.k, ncta = crs_num_ctas(a.no, a.nb), total = (ncta - 1) * mk;
     for (int64_t e = first; e < total; e += stride) {
         const int64_t c = 1 + e / mk, rem = e - (c - 1) * mk, j = c * a.nb - 1;
@@ -384,23 +389,24 @@ __device__ __forceinline__ void solve_down_fix_items(const LevelArgs &a, int64_t
 
 // One chunk of nb odd blocks and right-hand-side columns [cchunk*kc, +kc)
 // of an up-sweep level, run by the whole CTA.
-template <int MT>
-__device__ __forceinline__ void solve_up_chunk(const LevelArgs &a, int64_t chunk, int cchunk,
+template <int MT, class R>
+__device__ __forceinline__ void solve_up_chunk(const LevelArgsT<R> &a, int64_t chunk, int cchunk,
                                                unsigned char *smem_raw) {
+    using C = cplx_t<R>;
     constexpr int TRI = Tri<MT>::n;
     const int m = a.m, k = a.k, nb = a.nb, kc = a.kc, NT = blockDim.x, tid = threadIdx.x;
     const int mm = m * m, m2 = 2 * m, mk = m * k;
     const int c0 = cchunk * kc, kw = min(kc, k - c0);
     const int64_t t0 = chunk * nb;
     const int nbh = (int)min((int64_t)nb, a.no - t0);
-    z2 *sL = reinterpret_cast<z2 *>(smem_raw);                                // [nb][TRI]
-    z2 *sW = sL + (size_t)nb * TRI;                                            // [nb][MT][kc]
-    z2 *sX = sW + (size_t)nb * MT * kc;                                        // [nb][2MT][kc]
-    double *sInv = reinterpret_cast<double *>(sX + (size_t)nb * 2 * MT * kc);  // [nb][MT]
+    C *sL = reinterpret_cast<C *>(smem_raw);                                // [nb][TRI]
+    C *sW = sL + (size_t)nb * TRI;                                            // [nb][MT][kc]
+    C *sX = sW + (size_t)nb * MT * kc;                                        // [nb][2MT][kc]
+    R *sInv = reinterpret_cast<R *>(sX + (size_t)nb * 2 * MT * kc);  // [nb][MT]
 
     if (a.level == 0 && *a.status != CRS_NO_FAIL) {
         // the factorisation broke down: the result is NaN
-        const z2 nan2 = zmk(__longlong_as_double(0x7ff8000000000000ll), __longlong_as_double(0x7ff8000000000000ll));
+        const C nan2 = zmk(qnan(R()), qnan(R()));
         for (int e = tid; e < nbh * m * kw; e += NT) {
             const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
             const int64_t t = t0 + b;
@@ -423,8 +429,8 @@ __device__ __forceinline__ void solve_up_chunk(const LevelArgs &a, int64_t chunk
         const int64_t t = t0 + b;
         sW[(b * MT + r) * kc + c] = a.r[t * mk + r * k + c0 + c];
         // [x_left; x_right] = [xn_{t-1}; xn_t], zero past the boundary
-        sX[(b * 2 * MT + r) * kc + c] = (t >= 1) ? a.xn[(t - 1) * mk + r * k + c0 + c] : zmk(0.0, 0.0);
-        const z2 xr = (t < a.ne) ? a.xn[t * mk + r * k + c0 + c] : zmk(0.0, 0.0);
+        sX[(b * 2 * MT + r) * kc + c] = (t >= 1) ? a.xn[(t - 1) * mk + r * k + c0 + c] : zmk(R(0), R(0));
+        const C xr = (t < a.ne) ? a.xn[t * mk + r * k + c0 + c] : zmk(R(0), R(0));
         sX[(b * 2 * MT + m + r) * kc + c] = xr;
         if (t < a.ne) a.x[(2 * t + 1) * mk + r * k + c0 + c] = xr;  // even unknowns
     }
@@ -434,9 +440,9 @@ __device__ __forceinline__ void solve_up_chunk(const LevelArgs &a, int64_t chunk
     for (int e = tid; e < nbh * m * kw; e += NT) {
         const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
         const int64_t t = t0 + b;
-        const z2 *Zr = a.Z + t * (int64_t)(m * m2) + r * m2;
-        const z2 *Xb = sX + b * 2 * MT * kc + c;
-        z2 acc = sW[(b * MT + r) * kc + c];
+        const C *Zr = a.Z + t * (int64_t)(m * m2) + r * m2;
+        const C *Xb = sX + b * 2 * MT * kc + c;
+        C acc = sW[(b * MT + r) * kc + c];
 #pragma unroll
         for (int s = 0; s < 2 * MT; ++s)
             if (s < m2) zmsub(acc, __ldg(Zr + s), Xb[s * kc]);
@@ -447,7 +453,7 @@ __device__ __forceinline__ void solve_up_chunk(const LevelArgs &a, int64_t chunk
     // x_odd = L^{-H} w
     for (int e = tid; e < nbh * kw; e += NT) {
         const int b = e / kw, c = e - b * kw;
-        trsv_lower_h_col<MT>(sL + b * TRI, sInv + b * MT, sW + b * MT * kc + c, kc, m);
+        trsv_lower_h_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sW + b * MT * kc + c, kc, m);
     }
     __syncthreads();
     for (int e = tid; e < nbh * m * kw; e += NT) {

@@ -12,46 +12,62 @@
 namespace crs {
 
 typedef double2 z2;
+typedef float2 c2;
+
+// complex type of a real type
+template <class R> struct Cplx;
+template <> struct Cplx<double> { using type = double2; };
+template <> struct Cplx<float> { using type = float2; };
+template <class R> using cplx_t = typename Cplx<R>::type;
 
 #define CRS_NO_FAIL 0xFFFFFFFFFFFFFFFFull
 
+__device__ __forceinline__ double fmx(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fmx(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double rsq(double v) { return rsqrt(v); }
+__device__ __forceinline__ float rsq(float v) { return rsqrtf(v); }
+__device__ __forceinline__ double qnan(double) { return __longlong_as_double(0x7ff8000000000000ll); }
+__device__ __forceinline__ float qnan(float) { return __int_as_float(0x7fc00000); }
+
 __device__ __forceinline__ z2 zmk(double re, double im) { return make_double2(re, im); }
-__device__ __forceinline__ z2 zconj(z2 a) { return make_double2(a.x, -a.y); }
-// negation by flipping sign bits (integer pipe, no FP64 instruction)
+__device__ __forceinline__ c2 zmk(float re, float im) { return make_float2(re, im); }
+template <class C> __device__ __forceinline__ C zconj(C a) { C r = a; r.y = -a.y; return r; }
+template <class C> __device__ __forceinline__ C zsub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <class C, class R> __device__ __forceinline__ C zscale(C a, R s) { C r; r.x = a.x * s; r.y = a.y * s; return r; }
+// negation by flipping sign bits (integer pipe, no floating-point instruction)
 __device__ __forceinline__ double dneg_bits(double v) {
     return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
 }
-__device__ __forceinline__ z2 zneg(z2 a) { return make_double2(dneg_bits(a.x), dneg_bits(a.y)); }
-__device__ __forceinline__ z2 zscale(z2 a, double s) { return make_double2(a.x * s, a.y * s); }
-__device__ __forceinline__ z2 zsub(z2 a, z2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float dneg_bits(float v) { return __int_as_float(__float_as_int(v) ^ (int)0x80000000u); }
+template <class C> __device__ __forceinline__ C zneg(C a) { C r; r.x = dneg_bits(a.x); r.y = dneg_bits(a.y); return r; }
 
 // acc -= a * b
-__device__ __forceinline__ void zmsub(z2 &acc, z2 a, z2 b) {
-    acc.x = fma(-a.x, b.x, acc.x);
-    acc.x = fma(a.y, b.y, acc.x);
-    acc.y = fma(-a.x, b.y, acc.y);
-    acc.y = fma(-a.y, b.x, acc.y);
+template <class C> __device__ __forceinline__ void zmsub(C &acc, C a, C b) {
+    acc.x = fmx(-a.x, b.x, acc.x);
+    acc.x = fmx(a.y, b.y, acc.x);
+    acc.y = fmx(-a.x, b.y, acc.y);
+    acc.y = fmx(-a.y, b.x, acc.y);
 }
 // acc -= a * conj(b)
-__device__ __forceinline__ void zmsub_cb(z2 &acc, z2 a, z2 b) {
-    acc.x = fma(-a.x, b.x, acc.x);
-    acc.x = fma(-a.y, b.y, acc.x);
-    acc.y = fma(-a.y, b.x, acc.y);
-    acc.y = fma(a.x, b.y, acc.y);
+template <class C> __device__ __forceinline__ void zmsub_cb(C &acc, C a, C b) {
+    acc.x = fmx(-a.x, b.x, acc.x);
+    acc.x = fmx(-a.y, b.y, acc.x);
+    acc.y = fmx(-a.y, b.x, acc.y);
+    acc.y = fmx(a.x, b.y, acc.y);
 }
 // acc -= conj(a) * b
-__device__ __forceinline__ void zmsub_ca(z2 &acc, z2 a, z2 b) {
-    acc.x = fma(-a.x, b.x, acc.x);
-    acc.x = fma(-a.y, b.y, acc.x);
-    acc.y = fma(-a.x, b.y, acc.y);
-    acc.y = fma(a.y, b.x, acc.y);
+template <class C> __device__ __forceinline__ void zmsub_ca(C &acc, C a, C b) {
+    acc.x = fmx(-a.x, b.x, acc.x);
+    acc.x = fmx(-a.y, b.y, acc.x);
+    acc.y = fmx(-a.x, b.y, acc.y);
+    acc.y = fmx(a.y, b.x, acc.y);
 }
 // acc += conj(a) * b
-__device__ __forceinline__ void zmac_ca(z2 &acc, z2 a, z2 b) {
-    acc.x = fma(a.x, b.x, acc.x);
-    acc.x = fma(a.y, b.y, acc.x);
-    acc.y = fma(a.x, b.y, acc.y);
-    acc.y = fma(-a.y, b.x, acc.y);
+template <class C> __device__ __forceinline__ void zmac_ca(C &acc, C a, C b) {
+    acc.x = fmx(a.x, b.x, acc.x);
+    acc.x = fmx(a.y, b.y, acc.x);
+    acc.y = fmx(a.x, b.y, acc.y);
+    acc.y = fmx(-a.y, b.x, acc.y);
 }
 
 // Record a breakdown: the smallest (level, 1-based local block) key wins.
@@ -69,27 +85,31 @@ __device__ __forceinline__ int tri_row(int f) {
 
 // Arguments of one reduction level (Sec. 2 eq. Formulas on a level with Nl
 // blocks; odd blocks t = 0..no-1 sit at 0-based position 2t, even blocks
-// j' = 0..ne-1 at 2j'+1).
-struct LevelArgs {
+// j' = 0..ne-1 at 2j'+1), in real type R (double: the FP64 path; float: the
+// FP32 levels of the mixed-precision path).
+template <class R>
+struct LevelArgsT {
+    using C = cplx_t<R>;
     int64_t Nl, no, ne;
     int m, k, nb, kc, level;
     int inline_fix;     // 1: one CTA runs the chunks of the level in order and completes each
                         // chunk-boundary even block itself (no Wbd / cbd, no fix-up pass)
-    const z2 *A;        // [Nl][m][m] level system (lower triangle read)
-    const z2 *B;        // [Nl-1][m][m]
-    z2 *L;              // [no][m][m]  Cholesky factors (lower, upper zero)
-    double *inv;        // [no][m]     1 / diag(L)
-    z2 *Z;              // [no][m][2m] [P | Q] = L^{-1} [B_{i-1} | B_i^H]
-    z2 *Wbd;            // [ncta][m][m] P^H P of each CTA's first odd block (CTA-boundary scratch)
-    z2 *An;             // [ne][m][m]  next level diagonal blocks
-    z2 *Bn;             // [ne-1][m][m] next level sub-diagonal blocks
-    const z2 *y;        // [Nl][m][k]  level right-hand side
-    z2 *r;              // [no][m][k]  L^{-1} y_odd
-    z2 *cbd;            // [ncta][m][k] P^H r of each CTA's first odd block (CTA-boundary scratch)
-    z2 *yn;             // [ne][m][k]  next level right-hand side
-    const z2 *xn;       // [ne][m][k]  next level solution
-    z2 *x;              // [Nl][m][k]  level solution
+    const C *A;         // [Nl][m][m] level system (lower triangle read)
+    const C *B;         // [Nl-1][m][m]
+    C *L;               // [no][m][m]  Cholesky factors (lower, upper zero)
+    R *inv;             // [no][m]     1 / diag(L)
+    C *Z;               // [no][m][2m] [P | Q] = L^{-1} [B_{i-1} | B_i^H]
+    C *Wbd;             // [ncta][m][m] P^H P of each CTA's first odd block (CTA-boundary scratch)
+    C *An;              // [ne][m][m]  next level diagonal blocks
+    C *Bn;              // [ne-1][m][m] next level sub-diagonal blocks
+    const C *y;         // [Nl][m][k]  level right-hand side
+    C *r;               // [no][m][k]  L^{-1} y_odd
+    C *cbd;             // [ncta][m][k] P^H r of each CTA's first odd block (CTA-boundary scratch)
+    C *yn;              // [ne][m][k]  next level right-hand side
+    const C *xn;        // [ne][m][k]  next level solution
+    C *x;               // [Nl][m][k]  level solution
     unsigned long long *status;
 };
+using LevelArgs = LevelArgsT<double>;
 
 }  // namespace crs

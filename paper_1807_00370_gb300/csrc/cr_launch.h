@@ -17,8 +17,8 @@ struct TileShape {
 TileShape tile_shape(int mt);
 bool set_tile_shape(int mt, const TileShape &ts, size_t smem_limit);
 int pick_mt(int m);                                  // 4, 8, 16, 32, 64 or 0
-size_t factor_smem_bytes(int mt, int nb);
-size_t solve_smem_bytes(int mt, int nb, int kc, int panels);
+size_t factor_smem_bytes(int mt, int nb, int rsize = 8);           // rsize: 8 FP64, 4 FP32
+size_t solve_smem_bytes(int mt, int nb, int kc, int panels, int rsize = 8);
 cudaError_t prepare_kernels(int mt);                 // raise shared-memory limits once per device
 
 // Odd blocks per CTA of a level with `no` odd blocks (the tile's maximum,
@@ -31,15 +31,27 @@ inline int64_t num_ctas(int64_t no, int nb) { return crs_num_ctas(no, nb); }
 
 // Factor sweep of one level (a.nb set by factor_nb): the odd-block kernel
 // (Cholesky, P, Q, Z^H Z, and the even blocks that lie inside its CTA), then
-// the fix-up of the even blocks on CTA boundaries.
-cudaError_t launch_factor_odd(int mt, const LevelArgs &a, cudaStream_t s);
-cudaError_t launch_factor_fix(const LevelArgs &a, int nsm, cudaStream_t s);
+// the fix-up of the even blocks on CTA boundaries.  FP64 and FP32 versions.
+cudaError_t launch_factor_odd(int mt, const LevelArgsT<double> &a, cudaStream_t s);
+cudaError_t launch_factor_odd(int mt, const LevelArgsT<float> &a, cudaStream_t s);
+cudaError_t launch_factor_fix(const LevelArgsT<double> &a, int nsm, cudaStream_t s);
+cudaError_t launch_factor_fix(const LevelArgsT<float> &a, int nsm, cudaStream_t s);
 // Down sweep of one level (a.nb, a.kc set): r, Z^H r and the next level's
 // right-hand side inside each CTA, then the CTA-boundary fix-up.
-cudaError_t launch_solve_down_odd(int mt, const LevelArgs &a, cudaStream_t s);
-cudaError_t launch_solve_down_fix(const LevelArgs &a, int nsm, cudaStream_t s);
+cudaError_t launch_solve_down_odd(int mt, const LevelArgsT<double> &a, cudaStream_t s);
+cudaError_t launch_solve_down_odd(int mt, const LevelArgsT<float> &a, cudaStream_t s);
+cudaError_t launch_solve_down_fix(const LevelArgsT<double> &a, int nsm, cudaStream_t s);
+cudaError_t launch_solve_down_fix(const LevelArgsT<float> &a, int nsm, cudaStream_t s);
 // Up sweep of one level (x of this level from the next level's x).
-cudaError_t launch_solve_up(int mt, const LevelArgs &a, cudaStream_t s);
+cudaError_t launch_solve_up(int mt, const LevelArgsT<double> &a, cudaStream_t s);
+cudaError_t launch_solve_up(int mt, const LevelArgsT<float> &a, cudaStream_t s);
+// Mixed-precision helpers (cr_mixed.cu).
+cudaError_t launch_to_f32(const z2 *in, c2 *out, int64_t n, int nsm, cudaStream_t s);
+cudaError_t launch_to_f64(const c2 *in, z2 *out, int64_t n, int nsm, cudaStream_t s);
+cudaError_t launch_update(z2 *x, const c2 *d, int64_t n, int first, unsigned long long *norms, int nsm,
+                          cudaStream_t s);
+cudaError_t launch_residual(int64_t N, int m, int k, const z2 *A, const z2 *B, const z2 *x, const z2 *y, z2 *r,
+                            int nsm, cudaStream_t s);
 // Adjoint outer products gA, gB from x and gy.
 cudaError_t launch_adjoint_outer(int64_t N, int m, int k, const z2 *x, const z2 *gy, z2 *gA,
                                  z2 *gB, int nsm, cudaStream_t s);

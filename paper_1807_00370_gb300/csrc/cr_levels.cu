@@ -6,30 +6,32 @@
 
 namespace crs {
 
-template <int MT>
-__global__ void __launch_bounds__(256) k_factor_odd(LevelArgs a) {
+template <int MT, class R>
+__global__ void __launch_bounds__(256) k_factor_odd(LevelArgsT<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    factor_chunk<MT>(a, blockIdx.x, smem_raw);
+    factor_chunk<MT, R>(a, blockIdx.x, smem_raw);
 }
 
-__global__ void __launch_bounds__(256) k_factor_fix(LevelArgs a) {
-    factor_fix_items(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+template <class R>
+__global__ void __launch_bounds__(256) k_factor_fix(LevelArgsT<R> a) {
+    factor_fix_items<R>(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
-template <int MT>
-__global__ void __launch_bounds__(256) k_solve_down_odd(LevelArgs a) {
+template <int MT, class R>
+__global__ void __launch_bounds__(256) k_solve_down_odd(LevelArgsT<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    solve_down_chunk<MT>(a, blockIdx.x, blockIdx.y, smem_raw);
+    solve_down_chunk<MT, R>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
-__global__ void __launch_bounds__(256) k_solve_down_fix(LevelArgs a) {
-    solve_down_fix_items(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
+template <class R>
+__global__ void __launch_bounds__(256) k_solve_down_fix(LevelArgsT<R> a) {
+    solve_down_fix_items<R>(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
 }
 
-template <int MT>
-__global__ void __launch_bounds__(256) k_solve_up(LevelArgs a) {
+template <int MT, class R>
+__global__ void __launch_bounds__(256) k_solve_up(LevelArgsT<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    solve_up_chunk<MT>(a, blockIdx.x, blockIdx.y, smem_raw);
+    solve_up_chunk<MT, R>(a, blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -110,8 +112,8 @@ bool set_tile_shape(int mt, const TileShape &ts, size_t smem_limit) {
     if (i < 0 || ts.nb_factor < 1 || ts.nb_solve < 1 || ts.kc_max < 1 || ts.threads < 32 ||
         ts.threads > 256 || ts.threads % 32)
         return false;
-    if (factor_smem_bytes(mt, ts.nb_factor) > smem_limit ||
-        solve_smem_bytes(mt, ts.nb_solve, ts.kc_max, 3) > smem_limit)
+    if (factor_smem_bytes(mt, ts.nb_factor, 8) > smem_limit ||
+        solve_smem_bytes(mt, ts.nb_solve, ts.kc_max, 3, 8) > smem_limit)
         return false;
     g_tiles[i] = ts;
     return true;
@@ -126,28 +128,35 @@ int pick_mt(int m) {
     return 0;
 }
 
-// Per block: packed L (later P^H P) and packed V, Z = [P | Q], 1/diag(L).
-size_t factor_smem_bytes(int mt, int nb) {
-    const size_t tri = (size_t)mt * (mt + 1) / 2;
-    return (size_t)nb * ((2 * tri + 2 * (size_t)mt * mt) * sizeof(z2) + (size_t)mt * sizeof(double));
+// Per block: packed L (later P^H P) and packed V, Z = [P | Q], 1/diag(L);
+// rsize = bytes of the real type (8 for FP64, 4 for FP32).
+size_t factor_smem_bytes(int mt, int nb, int rsize) {
+    const size_t tri = (size_t)mt * (mt + 1) / 2, cs = 2 * (size_t)rsize;
+    return (size_t)nb * ((2 * tri + 2 * (size_t)mt * mt) * cs + (size_t)mt * rsize);
 }
 
 // Per block: packed L, `panels` right-hand-side panels of MT x kc (3 down, 3 up), 1/diag(L).
-size_t solve_smem_bytes(int mt, int nb, int kc, int panels) {
-    const size_t tri = (size_t)mt * (mt + 1) / 2;
-    return (size_t)nb * (tri * sizeof(z2) + (size_t)mt * kc * sizeof(z2) * panels + (size_t)mt * sizeof(double));
+size_t solve_smem_bytes(int mt, int nb, int kc, int panels, int rsize) {
+    const size_t tri = (size_t)mt * (mt + 1) / 2, cs = 2 * (size_t)rsize;
+    return (size_t)nb * (tri * cs + (size_t)mt * kc * cs * panels + (size_t)mt * rsize);
 }
 
 // Allow every kernel the device's full opt-in shared memory, so that any
 // tile shape that set_tile_shape accepted can launch.
+template <int MT, class R>
+static cudaError_t prepare_mt_r(int smem_optin) {
+    cudaError_t e;
+    e = cudaFuncSetAttribute(k_factor_odd<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_solve_down_odd<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_solve_up<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+}
+
 template <int MT>
 static cudaError_t prepare_mt(int smem_optin) {
-    cudaError_t e;
-    e = cudaFuncSetAttribute(k_factor_odd<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_solve_down_odd<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_solve_up<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+    const cudaError_t e = prepare_mt_r<MT, double>(smem_optin);
+    return e != cudaSuccess ? e : prepare_mt_r<MT, float>(smem_optin);
 }
 
 cudaError_t prepare_kernels(int mt) {
@@ -187,57 +196,78 @@ static unsigned grid_1d(int64_t items, int nsm) {
     return (unsigned)g;
 }
 
-template <int MT>
-static cudaError_t factor_odd_mt(const LevelArgs &a, cudaStream_t s) {
+template <int MT, class R>
+static cudaError_t factor_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const unsigned grid = (unsigned)num_ctas(a.no, a.nb);
-    k_factor_odd<MT><<<grid, tile_shape(MT).threads, factor_smem_bytes(MT, a.nb), s>>>(a);
+    k_factor_odd<MT, R><<<grid, tile_shape(MT).threads, factor_smem_bytes(MT, a.nb, sizeof(R)), s>>>(a);
     return cudaGetLastError();
 }
 
-template <int MT>
-static cudaError_t solve_down_odd_mt(const LevelArgs &a, cudaStream_t s) {
+template <int MT, class R>
+static cudaError_t solve_down_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const dim3 grid((unsigned)num_ctas(a.no, a.nb), (unsigned)((a.k + a.kc - 1) / a.kc));
-    k_solve_down_odd<MT><<<grid, tile_shape(MT).threads, solve_smem_bytes(MT, a.nb, a.kc, 3), s>>>(a);
+    k_solve_down_odd<MT, R><<<grid, tile_shape(MT).threads, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
     return cudaGetLastError();
 }
 
-template <int MT>
-static cudaError_t solve_up_mt(const LevelArgs &a, cudaStream_t s) {
+template <int MT, class R>
+static cudaError_t solve_up_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const dim3 grid((unsigned)num_ctas(a.no, a.nb), (unsigned)((a.k + a.kc - 1) / a.kc));
-    k_solve_up<MT><<<grid, tile_shape(MT).threads, solve_smem_bytes(MT, a.nb, a.kc, 3), s>>>(a);
+    k_solve_up<MT, R><<<grid, tile_shape(MT).threads, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
     return cudaGetLastError();
 }
 
-#define CRS_DISPATCH(fn, mt, ...)                   \
-    switch (mt) {                                   \
-        case 4: return fn<4>(__VA_ARGS__);          \
-        case 8: return fn<8>(__VA_ARGS__);          \
-        case 16: return fn<16>(__VA_ARGS__);        \
-        case 32: return fn<32>(__VA_ARGS__);        \
-        case 64: return fn<64>(__VA_ARGS__);        \
-        default: return cudaErrorInvalidValue;      \
+#define CRS_DISPATCH(fn, R, mt, ...)                 \
+    switch (mt) {                                    \
+        case 4: return fn<4, R>(__VA_ARGS__);        \
+        case 8: return fn<8, R>(__VA_ARGS__);        \
+        case 16: return fn<16, R>(__VA_ARGS__);      \
+        case 32: return fn<32, R>(__VA_ARGS__);      \
+        case 64: return fn<64, R>(__VA_ARGS__);      \
+        default: return cudaErrorInvalidValue;       \
     }
 
-cudaError_t launch_factor_odd(int mt, const LevelArgs &a, cudaStream_t s) {
-    CRS_DISPATCH(factor_odd_mt, mt, a, s)
-}
-cudaError_t launch_factor_fix(const LevelArgs &a, int nsm, cudaStream_t s) {
+template <class R>
+static cudaError_t factor_fix_r(const LevelArgsT<R> &a, int nsm, cudaStream_t s) {
     const int64_t ncta = num_ctas(a.no, a.nb);
     if (ncta < 2) return cudaSuccess;
-    k_factor_fix<<<grid_1d((ncta - 1) * (a.m * (a.m + 1) / 2), nsm), 256, 0, s>>>(a);
+    k_factor_fix<R><<<grid_1d((ncta - 1) * (a.m * (a.m + 1) / 2), nsm), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_solve_down_odd(int mt, const LevelArgs &a, cudaStream_t s) {
-    CRS_DISPATCH(solve_down_odd_mt, mt, a, s)
-}
-cudaError_t launch_solve_down_fix(const LevelArgs &a, int nsm, cudaStream_t s) {
+
+template <class R>
+static cudaError_t solve_down_fix_r(const LevelArgsT<R> &a, int nsm, cudaStream_t s) {
     const int64_t ncta = num_ctas(a.no, a.nb);
     if (ncta < 2) return cudaSuccess;
-    k_solve_down_fix<<<grid_1d((ncta - 1) * a.m * a.k, nsm), 256, 0, s>>>(a);
+    k_solve_down_fix<R><<<grid_1d((ncta - 1) * a.m * a.k, nsm), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
-cudaError_t launch_solve_up(int mt, const LevelArgs &a, cudaStream_t s) {
-    CRS_DISPATCH(solve_up_mt, mt, a, s)
+
+cudaError_t launch_factor_odd(int mt, const LevelArgsT<double> &a, cudaStream_t s) {
+    CRS_DISPATCH(factor_odd_mt, double, mt, a, s)
+}
+cudaError_t launch_factor_odd(int mt, const LevelArgsT<float> &a, cudaStream_t s) {
+    CRS_DISPATCH(factor_odd_mt, float, mt, a, s)
+}
+cudaError_t launch_factor_fix(const LevelArgsT<double> &a, int nsm, cudaStream_t s) { return factor_fix_r(a, nsm, s); }
+cudaError_t launch_factor_fix(const LevelArgsT<float> &a, int nsm, cudaStream_t s) { return factor_fix_r(a, nsm, s); }
+cudaError_t launch_solve_down_odd(int mt, const LevelArgsT<double> &a, cudaStream_t s) {
+    CRS_DISPATCH(solve_down_odd_mt, double, mt, a, s)
+}
+cudaError_t launch_solve_down_odd(int mt, const LevelArgsT<float> &a, cudaStream_t s) {
+    CRS_DISPATCH(solve_down_odd_mt, float, mt, a, s)
+}
+cudaError_t launch_solve_down_fix(const LevelArgsT<double> &a, int nsm, cudaStream_t s) {
+    return solve_down_fix_r(a, nsm, s);
+}
+cudaError_t launch_solve_down_fix(const LevelArgsT<float> &a, int nsm, cudaStream_t s) {
+    return solve_down_fix_r(a, nsm, s);
+}
+cudaError_t launch_solve_up(int mt, const LevelArgsT<double> &a, cudaStream_t s) {
+    CRS_DISPATCH(solve_up_mt, double, mt, a, s)
+}
+cudaError_t launch_solve_up(int mt, const LevelArgsT<float> &a, cudaStream_t s) {
+    CRS_DISPATCH(solve_up_mt, float, mt, a, s)
 }
 
 cudaError_t launch_adjoint_outer(int64_t N, int m, int k, const z2 *x, const z2 *gy, z2 *gA, z2 *gB,

@@ -25,6 +25,11 @@ struct LevelPlan {
     size_t offR, offYn, offXn;       // solve: r of this level, y and x of level l + 1
 };
 
+// Mixed precision: levels below `lT` run in FP32 (their own layout), the
+// coarsest levels (N_l <= kMixedCoarse blocks) and the refinement in FP64.
+constexpr int64_t kMixedCoarse = 64;
+constexpr int kMixedMaxIter = 40;
+
 }  // namespace
 
 struct crsolve_plan_s {
@@ -39,6 +44,14 @@ struct crsolve_plan_s {
     size_t ws_bytes = 0;
     bool factored = false;
     bool prepared = false;
+    // mixed precision
+    int lT = 0;                                  // first FP64 level
+    std::vector<LevelPlan> lev32;                // FP32 layout of levels < lT
+    size_t offWbd32 = 0, offCbd32 = 0, offA32 = 0, offB32 = 0, offY32 = 0, offX32 = 0, offR64 = 0, offNorms = 0;
+    const crsolve_z *A64 = nullptr, *B64 = nullptr;  // the caller's FP64 system, read by the residual
+    bool fallback = false;                       // FP32 factor broke down: everything in FP64
+    int last_iters = 0;
+    double last_delta = 0.0, last_rho = 0.0;
     // instrumentation
     bool timing = false;
     struct Rec { int kind, level; int64_t units; cudaEvent_t e0, e1; };
@@ -76,6 +89,31 @@ crs::LevelArgs level_args(const crsolve_plan_s *p, int l, const z2 *A0, const z2
     a.cbd = reinterpret_cast<z2 *>(ws + p->offCbd);
     a.yn = reinterpret_cast<z2 *>(ws + L.offYn);
     a.xn = reinterpret_cast<const z2 *>(ws + L.offXn);
+    a.status = reinterpret_cast<unsigned long long *>(ws + p->offStatus);
+    return a;
+}
+
+crs::LevelArgsT<float> level_args32(const crsolve_plan_s *p, int l) {
+    const LevelPlan &L = p->lev32[l];
+    crs::LevelArgsT<float> a{};
+    a.Nl = L.Nl; a.no = L.no; a.ne = L.ne;
+    a.m = p->m; a.level = l;
+    char *ws = p->ws;
+    using C = crs::c2;
+    a.A = reinterpret_cast<const C *>(ws + (l == 0 ? p->offA32 : p->lev32[l - 1].offAn));
+    a.B = reinterpret_cast<const C *>(ws + (l == 0 ? p->offB32 : p->lev32[l - 1].offBn));
+    a.L = reinterpret_cast<C *>(ws + L.offL);
+    a.inv = reinterpret_cast<float *>(ws + L.offInv);
+    a.Z = reinterpret_cast<C *>(ws + L.offZ);
+    a.Wbd = reinterpret_cast<C *>(ws + p->offWbd32);
+    a.An = reinterpret_cast<C *>(ws + L.offAn);
+    a.Bn = reinterpret_cast<C *>(ws + L.offBn);
+    a.r = reinterpret_cast<C *>(ws + L.offR);
+    a.cbd = reinterpret_cast<C *>(ws + p->offCbd32);
+    a.yn = reinterpret_cast<C *>(ws + L.offYn);
+    a.xn = reinterpret_cast<const C *>(ws + L.offXn);
+    a.y = reinterpret_cast<const C *>(ws + (l == 0 ? p->offY32 : p->lev32[l - 1].offYn));
+    a.x = reinterpret_cast<C *>(ws + (l == 0 ? p->offX32 : p->lev32[l - 1].offXn));
     a.status = reinterpret_cast<unsigned long long *>(ws + p->offStatus);
     return a;
 }
@@ -170,6 +208,175 @@ int do_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     return CRSOLVE_OK;
 }
 
+// ---- mixed precision ------------------------------------------------------
+
+// Factor: FP32 levels 0..lT-1, the level-lT system converted to FP64, FP64
+// levels lT.. .  A breakdown in the FP32 levels is re-decided by a full FP64
+// factorisation, so that the reported flags are always the FP64 ones.
+int mixed_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
+    const size_t mm = (size_t)p->m * p->m;
+    char *ws = p->ws;
+    p->A64 = reinterpret_cast<const crsolve_z *>(A);
+    p->B64 = reinterpret_cast<const crsolve_z *>(B);
+    p->fallback = false;
+    if (cudaMemsetAsync(ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess) return CRSOLVE_ECUDA;
+    if (crs::launch_to_f32(A, reinterpret_cast<crs::c2 *>(ws + p->offA32), p->N * (int64_t)mm, p->nsm, s) ||
+        (p->N > 1 && crs::launch_to_f32(B, reinterpret_cast<crs::c2 *>(ws + p->offB32), (p->N - 1) * (int64_t)mm,
+                                         p->nsm, s)))
+        return CRSOLVE_ECUDA;
+    int rc;
+    for (int l = 0; l < p->lT; ++l) {
+        crs::LevelArgsT<float> a = level_args32(p, l);
+        a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
+        if ((rc = launch(p, CRSOLVE_K_FACTOR_ODD, l, a.no, s, [&] { return crs::launch_factor_odd(p->mt, a, s); })))
+            return rc;
+        if (crs::num_ctas(a.no, a.nb) > 1 &&
+            (rc = launch(p, CRSOLVE_K_FACTOR_FIX, l, crs::num_ctas(a.no, a.nb) - 1, s,
+                         [&] { return crs::launch_factor_fix(a, p->nsm, s); })))
+            return rc;
+    }
+    // the level-lT system to FP64, into the FP64 layout's slot for it
+    const LevelPlan &Lb = p->lev32[p->lT - 1];
+    if (crs::launch_to_f64(reinterpret_cast<const crs::c2 *>(ws + Lb.offAn), reinterpret_cast<z2 *>(ws + p->lev[p->lT - 1].offAn),
+                           Lb.ne * (int64_t)mm, p->nsm, s) ||
+        crs::launch_to_f64(reinterpret_cast<const crs::c2 *>(ws + Lb.offBn), reinterpret_cast<z2 *>(ws + p->lev[p->lT - 1].offBn),
+                           (Lb.ne > 1 ? Lb.ne - 1 : 0) * (int64_t)mm, p->nsm, s))
+        return CRSOLVE_ECUDA;
+    for (int l = p->lT; l < (int)p->lev.size(); ++l) {
+        crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
+        a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
+        if ((rc = launch(p, CRSOLVE_K_FACTOR_ODD, l, a.no, s, [&] { return crs::launch_factor_odd(p->mt, a, s); })))
+            return rc;
+        if (crs::num_ctas(a.no, a.nb) > 1 &&
+            (rc = launch(p, CRSOLVE_K_FACTOR_FIX, l, crs::num_ctas(a.no, a.nb) - 1, s,
+                         [&] { return crs::launch_factor_fix(a, p->nsm, s); })))
+            return rc;
+    }
+    unsigned long long st = 0;
+    if (cudaMemcpyAsync(&st, ws + p->offStatus, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    p->factored = true;
+    if (st != CRS_NO_FAIL) {
+        p->fallback = true;
+        return do_factor(p, A, B, s);
+    }
+    return CRSOLVE_OK;
+}
+
+// One correction solve d = A~^{-1} r with the mixed factorisation: r (FP64)
+// -> FP32, FP32 down sweep, FP64 coarse levels, FP32 up sweep -> d (FP32).
+int mixed_correction(crsolve_plan_s *p, int k, const z2 *r, cudaStream_t s) {
+    char *ws = p->ws;
+    const int64_t mk = (int64_t)p->m * k;
+    const int nlev = (int)p->lev.size();
+    int rc;
+    if (crs::launch_to_f32(r, reinterpret_cast<crs::c2 *>(ws + p->offY32), p->N * mk, p->nsm, s)) return CRSOLVE_ECUDA;
+    for (int l = 0; l < p->lT; ++l) {
+        crs::LevelArgsT<float> a = level_args32(p, l);
+        a.k = k;
+        a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
+        a.kc = crs::solve_kc(p->mt, k);
+        if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s, [&] { return crs::launch_solve_down_odd(p->mt, a, s); })))
+            return rc;
+        if (crs::num_ctas(a.no, a.nb) > 1 &&
+            (rc = launch(p, CRSOLVE_K_SOLVE_DOWN_FIX, l, crs::num_ctas(a.no, a.nb) - 1, s,
+                         [&] { return crs::launch_solve_down_fix(a, p->nsm, s); })))
+            return rc;
+    }
+    const LevelPlan &Lb = p->lev32[p->lT - 1];
+    if (crs::launch_to_f64(reinterpret_cast<const crs::c2 *>(ws + Lb.offYn), reinterpret_cast<z2 *>(ws + p->lev[p->lT - 1].offYn),
+                           Lb.ne * mk, p->nsm, s))
+        return CRSOLVE_ECUDA;
+    for (int l = p->lT; l < nlev; ++l) {
+        crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
+        a.k = k;
+        a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
+        a.kc = crs::solve_kc(p->mt, k);
+        a.y = reinterpret_cast<const z2 *>(ws + p->lev[l - 1].offYn);
+        if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s, [&] { return crs::launch_solve_down_odd(p->mt, a, s); })))
+            return rc;
+        if (crs::num_ctas(a.no, a.nb) > 1 &&
+            (rc = launch(p, CRSOLVE_K_SOLVE_DOWN_FIX, l, crs::num_ctas(a.no, a.nb) - 1, s,
+                         [&] { return crs::launch_solve_down_fix(a, p->nsm, s); })))
+            return rc;
+    }
+    for (int l = nlev - 1; l >= p->lT; --l) {
+        crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
+        a.k = k;
+        a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
+        a.kc = crs::solve_kc(p->mt, k);
+        a.x = reinterpret_cast<z2 *>(ws + p->lev[l - 1].offXn);
+        if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, l, a.no, s, [&] { return crs::launch_solve_up(p->mt, a, s); })))
+            return rc;
+    }
+    if (crs::launch_to_f32(reinterpret_cast<const z2 *>(ws + p->lev[p->lT - 1].offXn), reinterpret_cast<crs::c2 *>(ws + Lb.offXn),
+                           Lb.ne * mk, p->nsm, s))
+        return CRSOLVE_ECUDA;
+    for (int l = p->lT - 1; l >= 0; --l) {
+        crs::LevelArgsT<float> a = level_args32(p, l);
+        a.k = k;
+        a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
+        a.kc = crs::solve_kc(p->mt, k);
+        if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, l, a.no, s, [&] { return crs::launch_solve_up(p->mt, a, s); })))
+            return rc;
+    }
+    return CRSOLVE_OK;
+}
+
+// Iterative refinement: x_0 = A~^{-1} y, then r_i = y - A x_i in FP64 and
+// x_{i+1} = x_i + A~^{-1} r_i.  With delta_i = |d_i|_inf / |x_{i+1}|_inf and
+// rho = delta_i / delta_{i-1} (the observed contraction), the error of
+// x_{i+1} is about rho * delta_i; stop when that is below 1e-13 (or delta_i
+// is at FP64 resolution).  No contraction (rho > 0.5 twice) switches to the
+// FP64 path.
+int mixed_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
+    char *ws = p->ws;
+    const int64_t n = p->N * (int64_t)p->m * k;
+    unsigned long long *norms = reinterpret_cast<unsigned long long *>(ws + p->offNorms);
+    z2 *r = reinterpret_cast<z2 *>(ws + p->offR64);
+    const crs::c2 *d = reinterpret_cast<const crs::c2 *>(ws + p->offX32);
+    double prev = 0.0, rho = 1.0;
+    int slow = 0, rc;
+    p->last_iters = 0;
+    for (int it = 0; it < kMixedMaxIter; ++it) {
+        if (it > 0) {
+            if (crs::launch_residual(p->N, p->m, k, reinterpret_cast<const z2 *>(p->A64),
+                                     reinterpret_cast<const z2 *>(p->B64), x, y, r, p->nsm, s))
+                return CRSOLVE_ECUDA;
+            p->last_iters = it;
+        }
+        if ((rc = mixed_correction(p, k, it == 0 ? y : r, s))) return rc;
+        if (cudaMemsetAsync(norms, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess ||
+            crs::launch_update(x, d, n, it == 0, norms, p->nsm, s))
+            return CRSOLVE_ECUDA;
+        unsigned long long hn[2];
+        if (cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaStreamSynchronize(s) != cudaSuccess)
+            return CRSOLVE_ECUDA;
+        double dn, xn;
+        memcpy(&dn, &hn[0], 8);
+        memcpy(&xn, &hn[1], 8);
+        const double delta = xn > 0 ? dn / xn : 0.0;
+        if (!(delta == delta)) break;                       // NaN: give up on FP32
+        if (it > 0) {
+            rho = prev > 0 ? delta / prev : 0.0;
+            if (rho * delta <= 1e-13 || delta <= 4.4e-16) {
+                p->last_delta = delta; p->last_rho = rho;
+                return CRSOLVE_OK;
+            }
+            slow = rho > 0.5 ? slow + 1 : 0;
+            if (slow >= 2) break;
+        }
+        prev = delta;
+        p->last_delta = delta; p->last_rho = rho;
+    }
+    // no convergence in mixed precision: factor and solve in FP64
+    p->fallback = true;
+    if ((rc = do_factor(p, reinterpret_cast<const z2 *>(p->A64), reinterpret_cast<const z2 *>(p->B64), s))) return rc;
+    return do_solve(p, k, y, x, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -180,7 +387,7 @@ int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, u
     *out_plan = nullptr;
     if (N < 1 || m < 1 || kmax < 1) return CRSOLVE_EINVAL;
     if (m > CRSOLVE_MAX_M || kmax > CRSOLVE_MAX_K) return CRSOLVE_EUNSUPPORTED;
-    if (precision != CRSOLVE_FP64) return CRSOLVE_EUNSUPPORTED;
+    if (precision != CRSOLVE_FP64 && precision != CRSOLVE_MIXED) return CRSOLVE_EUNSUPPORTED;
     if (flags & ~(uint32_t)CRSOLVE_PLAN_HOST_STAGING) return CRSOLVE_EINVAL;
     crsolve_plan_s *p = new (std::nothrow) crsolve_plan_s();
     if (!p) return CRSOLVE_ENOMEM;
@@ -221,6 +428,36 @@ int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, u
         p->offSY = take(cur, N * mk * zsz);
         p->offSX = take(cur, N * mk * zsz);
     }
+    if (precision == CRSOLVE_MIXED) {
+        // FP32 levels: all levels with more than kMixedCoarse blocks (at least one)
+        int lT = 0;
+        while (lT + 1 < (int)p->lev.size() && p->lev[lT].Nl > kMixedCoarse) ++lT;
+        if (lT == 0) lT = p->lev.size() > 1 ? 1 : 0;
+        p->lT = lT;
+        const size_t c32 = 8;
+        for (int l = 0; l < lT; ++l) {
+            const LevelPlan &L64 = p->lev[l];
+            LevelPlan L{};
+            L.Nl = L64.Nl; L.no = L64.no; L.ne = L64.ne;
+            L.offL = take(cur, L.no * mm * c32);
+            L.offInv = take(cur, L.no * (size_t)m * 4);
+            L.offZ = take(cur, L.no * 2 * mm * c32);
+            L.offR = take(cur, L.no * mk * c32);
+            L.offAn = take(cur, L.ne * mm * c32);
+            L.offBn = take(cur, (L.ne > 1 ? L.ne - 1 : 0) * mm * c32);
+            L.offYn = take(cur, L.ne * mk * c32);
+            L.offXn = take(cur, L.ne * mk * c32);
+            p->lev32.push_back(L);
+        }
+        p->offWbd32 = take(cur, no0 * mm * c32);
+        p->offCbd32 = take(cur, no0 * mk * c32);
+        p->offA32 = take(cur, N * mm * c32);
+        p->offB32 = take(cur, (N - 1) * mm * c32);
+        p->offY32 = take(cur, N * mk * c32);
+        p->offX32 = take(cur, N * mk * c32);
+        p->offR64 = take(cur, N * mk * zsz);
+        p->offNorms = take(cur, 16);
+    }
     p->total = cur;
     *out_plan = p;
     return CRSOLVE_OK;
@@ -248,6 +485,9 @@ int crsolve_factor(crsolve_plan p, const crsolve_z *A, const crsolve_z *B, void 
     int rc = check_device(p);
     if (rc) return rc;
     if ((rc = ensure_prepared(p))) return rc;
+    if (p->precision == CRSOLVE_MIXED && p->lT > 0)
+        return mixed_factor(p, reinterpret_cast<const z2 *>(A), reinterpret_cast<const z2 *>(B),
+                            static_cast<cudaStream_t>(stream));
     return do_factor(p, reinterpret_cast<const z2 *>(A), reinterpret_cast<const z2 *>(B),
                      static_cast<cudaStream_t>(stream));
 }
@@ -261,6 +501,9 @@ int crsolve_solve(crsolve_plan p, int32_t k, const crsolve_z *y, crsolve_z *x, v
     int rc = check_device(p);
     if (rc) return rc;
     if ((rc = ensure_prepared(p))) return rc;
+    if (p->precision == CRSOLVE_MIXED && p->lT > 0 && !p->fallback)
+        return mixed_solve(p, k, reinterpret_cast<const z2 *>(y), reinterpret_cast<z2 *>(x),
+                           static_cast<cudaStream_t>(stream));
     return do_solve(p, k, reinterpret_cast<const z2 *>(y), reinterpret_cast<z2 *>(x),
                     static_cast<cudaStream_t>(stream));
 }
@@ -376,6 +619,15 @@ int crsolve_timing_read(crsolve_plan p, crsolve_kernel_time *out, int32_t cap, i
     }
     p->recs.clear();
     p->pool_used = 0;
+    return CRSOLVE_OK;
+}
+
+int crsolve_mixed_stats(crsolve_plan p, int32_t *iterations, double *delta, double *rho, int32_t *fp64_fallback) {
+    if (!p) return CRSOLVE_EINVAL;
+    if (iterations) *iterations = p->last_iters;
+    if (delta) *delta = p->last_delta;
+    if (rho) *rho = p->last_rho;
+    if (fp64_fallback) *fp64_fallback = p->fallback ? 1 : 0;
     return CRSOLVE_OK;
 }
 
