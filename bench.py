@@ -123,6 +123,21 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sms)}
 
 
+def reduce_over_ranks(ms: float, units: int, device="cpu"):
+    """Max of the timed region and sum of the units over all ranks (the job's
+    clock is the slowest rank; the job's work is everyone's).  Works with any
+    torch.distributed backend (nccl on GPUs, gloo in the CPU tests)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms, units
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     return ws, int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0"))
@@ -190,7 +205,9 @@ def run_batched(args):
     Ns, ms, ks = Ns[:nsys], ms[:nsys], ks[:nsys]
     A, B, y = synthetic.gen_batch_device(Ns, ms, ks, seed=BATCH_SEED)
     x = torch.empty_like(y)
-    b = crs.Batch(Ns, ms, ks)
+    t_tune = time.perf_counter()
+    b = crs.Batch(Ns, ms, ks, tiles="auto")
+    t_tune = time.perf_counter() - t_tune
     rows = int(Ns.sum())
     flops = float((Ns * (25.33 * ms.astype(float) ** 3 + 40.0 * ms.astype(float) ** 2 * ks)).sum())
     stream = torch.cuda.current_stream()
@@ -229,7 +246,8 @@ def run_batched(args):
         "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": ms_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
         "config": {"workload": BATCH_WORKLOAD, "systems": len(Ns), "block_rows": rows, "seed": BATCH_SEED,
-                   "slots": b.nslots, "l2": "inputs larger than L2, no flush"},
+                   "slots": b.nslots, "l2": "inputs larger than L2, no flush",
+                   "tiles": {str(k): v for k, v in b.tiles.items()}, "autotune_s": t_tune},
         "roofline": {"bound": "alu", "kernel": "k_batch (whole step)", "achieved": flops / (ms_step * 1e-3) / 1e12,
                      "peak": peak_tf, "unit": "TFLOP/s", "frac": flops / (ms_step * 1e-3) / 1e12 / peak_tf,
                      "traffic": None},
@@ -434,10 +452,7 @@ def main():
     recs = crs.crsolve_timing_read(plan)
     crs.crsolve_timing_enable(plan, False)
     launches = crs.crsolve_launch_count(plan) - launches0
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, total_units = reduce_over_ranks(ms, N_BLOCKS * args.steps, dev)
 
     # per-kernel breakdown and the dominant kernel's roofline (FP64 pipe)
     by_kind = {}
@@ -452,7 +467,7 @@ def main():
     peak_tf = FP64_PEAK_GFLOPS / 1e3
     step_flops = N_BLOCKS * flops_per_block_row(M, K_RHS)
     ms_step = ms / args.steps
-    value = ws * N_BLOCKS * args.steps / (ms * 1e-3)
+    value = total_units / (ms * 1e-3)
 
     # measurement-side residual check (torch ops, not part of the solver)
     with torch.no_grad():

@@ -1,0 +1,139 @@
+"""Tile autotuner of the batched form.
+
+For every block-size class MT (4, 8, 16, 32, 64) present in a batch, it
+times the persistent batched kernel on a sample batch of that class and
+keeps the fastest (odd blocks per chunk in the factor step, odd blocks per
+chunk in the solve steps, right-hand-side columns per chunk).  Results are
+cached per GPU name and class in _build/tiles.json next to the library.
+The sample inputs come from torch's generator (their values do not matter
+for timing, only their shapes).
+"""
+from __future__ import annotations
+
+import json
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+from .batched import Batch, crsolve_batch_solve
+
+CACHE = os.path.join(_build.BUILD, "tiles.json")
+NB_CANDIDATES = (1, 2, 4, 8, 16, 32)
+KC_CANDIDATES = (8, 16, 32)
+
+
+def _mt(m: int) -> int:
+    for c in (4, 8, 16, 32, 64):
+        if m <= c:
+            return c
+    raise ValueError("m > 64")
+
+
+def _sample_inputs(Ns, ms, ks, device):
+    tot_a = int((Ns * ms * ms).sum())
+    tot_b = int(((Ns - 1) * ms * ms).sum())
+    tot_y = int((Ns * ms * ks).sum())
+    g = torch.Generator(device=device).manual_seed(1234)
+
+    def rnd(n):
+        return torch.view_as_complex(torch.randn(n, 2, generator=g, device=device, dtype=torch.float64))
+
+    A = rnd(tot_a) * 0.05
+    B = rnd(max(tot_b, 1)) * 0.05
+    # make every diagonal block strongly diagonal: A_j += (2 + small) I
+    off = 0
+    for N, m in zip(Ns, ms):
+        idx = torch.arange(m, device=device)
+        blk = A[off:off + N * m * m].view(N, m, m)
+        blk[:, idx, idx] += 4.0
+        off += N * m * m
+    return A, B, rnd(tot_y)
+
+
+def _time(b: Batch, A, B, y, x, reps=3) -> float:
+    crsolve_batch_solve(b, A, B, y, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        crsolve_batch_solve(b, A, B, y, x)
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_class(mt: int, m: int, k: int, device=None, n_blocks: int = 512, verbose: bool = False):
+    """Best (nb_factor, nb_solve, kc) for class mt on systems of size m, width k."""
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    nslots_guess = torch.cuda.get_device_properties(device).multi_processor_count * 2
+    nsys = 2 * nslots_guess
+    Ns = np.full(nsys, n_blocks, np.int64)
+    ms = np.full(nsys, m, np.int32)
+    ks = np.full(nsys, k, np.int32)
+    A, B, y = _sample_inputs(Ns, ms, ks, device)
+    x = torch.empty_like(y)
+    best = None
+
+    def trial(nbf, nbs, kc):
+        try:
+            b = Batch(Ns, ms, ks, device=device, tiles={mt: (nbf, nbs, kc)})
+        except RuntimeError:
+            return None                      # does not fit in shared memory
+        t = _time(b, A, B, y, x)
+        if verbose:
+            print(f"  mt={mt} nbf={nbf} nbs={nbs} kc={kc}: {t:.3f} ms")
+        return t
+
+    # factor chunk first (solve tile at its default), then the solve chunk
+    res_f = {}
+    for nbf in NB_CANDIDATES:
+        t = trial(nbf, 1, min(16, k))
+        if t is not None:
+            res_f[nbf] = t
+    nbf = min(res_f, key=res_f.get)
+    res_s = {}
+    for nbs in NB_CANDIDATES:
+        for kc in KC_CANDIDATES:
+            if kc > max(k, 8):
+                continue
+            t = trial(nbf, nbs, kc)
+            if t is not None:
+                res_s[(nbs, kc)] = t
+    (nbs, kc) = min(res_s, key=res_s.get)
+    best = (int(nbf), int(nbs), int(kc))
+    return best, {"factor": res_f, "solve": {f"{a},{c}": v for (a, c), v in res_s.items()}}
+
+
+def load_cache():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def tiles_for(ms, ks, device=None, use_cache: bool = True, verbose: bool = False):
+    """{mt: (nb_factor, nb_solve, kc)} for the classes present in a batch."""
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    name = torch.cuda.get_device_name(device)
+    cache = load_cache() if use_cache else {}
+    out, changed = {}, False
+    ms = np.asarray(ms)
+    ks = np.asarray(ks)
+    for mt in sorted({_mt(int(m)) for m in ms}):
+        key = f"{name}|mt={mt}"
+        if key not in cache:
+            sel = np.array([_mt(int(m)) == mt for m in ms])
+            m_rep = int(np.max(ms[sel]))
+            k_rep = int(np.median(ks[sel]))
+            best, table = tune_class(mt, m_rep, k_rep, device, verbose=verbose)
+            cache[key] = {"tile": best, "m": m_rep, "k": k_rep, "timings_ms": table}
+            changed = True
+        out[mt] = tuple(cache[key]["tile"])
+    if changed:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    return out

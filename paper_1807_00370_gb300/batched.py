@@ -36,6 +36,12 @@ class Batch:
         self.Ns = np.ascontiguousarray(Ns, dtype=np.int64)
         self.ms = np.ascontiguousarray(ms, dtype=np.int32)
         self.ks = np.ascontiguousarray(ks, dtype=np.int32)
+        if isinstance(tiles, str):
+            if tiles != "auto":
+                raise ValueError("tiles must be None, 'auto' or {mt: (nb_factor, nb_solve, kc)}")
+            from .autotune import tiles_for
+            tiles = tiles_for(self.ms, self.ks, self.device)
+        self.tiles = dict(tiles or {})
         self.nsys = len(self.Ns)
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):

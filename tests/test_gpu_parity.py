@@ -169,3 +169,48 @@ def test_solve_before_factor_is_an_error(cuda_ok):
     y = torch.zeros((8, 4, 1), dtype=torch.complex128, device="cuda")
     with pytest.raises(RuntimeError, match="not been factored"):
         crs.crsolve_solve(plan, y)
+
+
+# ------------------------------------------------------------------ full size
+# N = 2^20, m = 8, k = 4 in the launch configuration bench.py times.
+
+def _full(shift=1.0, indefinite=False):
+    A, B, y = synthetic.gen_system(1 << 20, 8, 4, seed=1000 if shift == 1.0 else 1001, shift=shift)
+    if indefinite:
+        A = synthetic.make_indefinite(A)
+    return A, B, y
+
+
+@pytest.mark.slow
+def test_full_size_matches_oracle(cuda_ok):
+    A, B, y = _full()
+    x, info, _ = run(A, B, y)
+    xo, io = oracle.cr_solve(A, B, y)
+    assert info == io and info["status"] == 0
+    assert rel_err(x, xo) <= TOL
+
+
+@pytest.mark.slow
+def test_full_size_kappa_1e6_matches_oracle(cuda_ok):
+    import json
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "kappa_shifts.json")
+    if not os.path.exists(path) or "plain_N2p20_m8_k4" not in json.load(open(path)):
+        pytest.skip("kappa_shifts.json lacks the N = 2^20 case")
+    shift = json.load(open(path))["plain_N2p20_m8_k4"]["shifts"]["1e+06"]
+    A, B, y = _full(shift=shift)
+    x, info, _ = run(A, B, y)
+    xo, io = oracle.cr_solve(A, B, y)
+    assert info == io and info["status"] == 0
+    assert rel_err(x, xo) <= 1e-10
+
+
+@pytest.mark.slow
+def test_full_size_indefinite_flag_matches_prediction(cuda_ok):
+    """A_{N/2} - 3I: first breakdown at (level 19, block 1, original block 2^19)."""
+    A, B, y = _full(indefinite=True)
+    assert np.linalg.eigvalsh(A[(1 << 19) - 1]).min() < 0
+    x, info, _ = run(A, B, y)
+    _, io = oracle.cr_solve(A, B, y)
+    assert info == io == {"status": 1, "level": 19, "block": 1, "orig_block": 1 << 19}
+    assert np.isnan(x).all()
