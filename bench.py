@@ -348,6 +348,7 @@ def run_mixed(args):
                 crs.crsolve_factor(plan, dA, dB)
                 crs.crsolve_solve(plan, dy, x)
             torch.cuda.synchronize()
+            crs.crsolve_timing_enable(plan, True)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(args.steps):
@@ -355,12 +356,17 @@ def run_mixed(args):
                 crs.crsolve_solve(plan, dy, x)
             e1.record(stream)
             torch.cuda.synchronize()
-            res[name] = {"ms": e0.elapsed_time(e1) / args.steps, "x": x,
+            by = {}
+            for kind, _, _, kms in crs.crsolve_timing_read(plan):
+                by[kind] = round(by.get(kind, 0.0) + kms / args.steps, 3)
+            crs.crsolve_timing_enable(plan, False)
+            res[name] = {"ms": e0.elapsed_time(e1) / args.steps, "x": x, "kernels_ms": by,
                          "stats": crs.crsolve_mixed_stats(plan) if prec == nat.CRSOLVE_MIXED else None}
         err = float((torch.linalg.norm(res["mixed"]["x"] - res["fp64"]["x"]) / torch.linalg.norm(res["fp64"]["x"])).item())
         runs.append({"kappa": float(kap), "shift": shifts["shifts"][kap], "mixed_ms": res["mixed"]["ms"],
                      "fp64_ms": res["fp64"]["ms"], "speedup": res["fp64"]["ms"] / res["mixed"]["ms"],
-                     "rel_err_vs_fp64_path": err, "refinement": res["mixed"]["stats"]})
+                     "rel_err_vs_fp64_path": err, "refinement": res["mixed"]["stats"],
+                     "mixed_kernels_ms": res["mixed"]["kernels_ms"], "fp64_kernels_ms": res["fp64"]["kernels_ms"]})
     peak_tf = FP64_PEAK_GFLOPS / 1e3
     best = min(runs, key=lambda r: r["mixed_ms"])
     line = {

@@ -245,7 +245,10 @@ enum crsolve_kernel_kind {
     CRSOLVE_K_SOLVE_DOWN_FIX = 3,  /* next level's right-hand side on CTA boundaries */
     CRSOLVE_K_SOLVE_UP = 4,        /* back-substitution of a level */
     CRSOLVE_K_ADJOINT = 5,         /* gA, gB outer products */
-    CRSOLVE_K_NANFILL = 6          /* NaN fill of gA / gB after a breakdown */
+    CRSOLVE_K_NANFILL = 6,         /* NaN fill of gA / gB after a breakdown */
+    CRSOLVE_K_RESIDUAL = 7,        /* mixed precision: FP64 residual y - A x */
+    CRSOLVE_K_CONVERT = 8,         /* mixed precision: FP64 <-> FP32 copies */
+    CRSOLVE_K_UPDATE = 9           /* mixed precision: x += d and norms */
 };
 
 typedef struct {

@@ -45,7 +45,7 @@ class CrsolveKernelTime(ctypes.Structure):
 
 
 KERNEL_KINDS = {0: "factor_odd", 1: "factor_fix", 2: "solve_down_odd", 3: "solve_down_fix",
-                4: "solve_up", 5: "adjoint_outer", 6: "nan_fill"}
+                4: "solve_up", 5: "adjoint_outer", 6: "nan_fill", 7: "residual", 8: "convert", 9: "update"}
 
 SIGNATURES = {
     "crsolve_plan_create": (ctypes.c_int, [_I64, _I32, _I32, _I32, _U32, ctypes.POINTER(_P)]),

@@ -98,6 +98,86 @@ __device__ __forceinline__ void trsv_lower_h_col(const C *Lb, const R *ivb, C *c
     }
 }
 
+// Blocked forward substitution Z := L^{-1} Z for every column of every block
+// of a chunk, run by the whole CTA (used for MT >= 32, where a column-by-
+// column substitution would be one long dependent chain per thread).  Rows
+// are taken in blocks of 16: the diagonal block is solved per column (a
+// chain of <= 16 rows), then the rows below are updated in parallel, one
+// item per (block, row, column).  Column (b, col) starts at
+// base + b * bstride + col, with row stride ld.  Ends with __syncthreads().
+template <int MT, class R, class C>
+__device__ __forceinline__ void trsm_lower_cta(const C *sL, const R *sInv, C *base, int bstride, int ld, int nbh,
+                                               int ncols, int m) {
+    constexpr int TRI = Tri<MT>::n, BS = 16;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    for (int rb = 0; rb < m; rb += BS) {
+        const int re = min(rb + BS, m);
+        for (int e = tid; e < nbh * ncols; e += NT) {
+            const int b = e / ncols, col = e - b * ncols;
+            const C *Lb = sL + b * TRI;
+            const R *ivb = sInv + b * MT;
+            C *z = base + b * bstride + col;
+            for (int r = rb; r < re; ++r) {
+                C acc = z[r * ld];
+                for (int s = rb; s < r; ++s) zmsub(acc, Lb[tri(r, s)], z[s * ld]);
+                z[r * ld] = zscale(acc, ivb[r]);
+            }
+        }
+        __syncthreads();
+        if (re < m) {
+            const int nr = m - re, per = nr * ncols;
+            for (int e = tid; e < nbh * per; e += NT) {
+                const int b = e / per, rem = e - b * per, r = re + rem / ncols, col = rem - (r - re) * ncols;
+                const C *Lr = sL + b * TRI + tri(r, 0);
+                C *z = base + b * bstride + col;
+                C acc = z[r * ld];
+#pragma unroll 4
+                for (int s = rb; s < re; ++s) zmsub(acc, Lr[s], z[s * ld]);
+                z[r * ld] = acc;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Blocked backward substitution Z := L^{-H} Z, the mirror of trsm_lower_cta:
+// row blocks from the bottom, the diagonal block per column, then the rows
+// above updated in parallel.  Ends with __syncthreads().
+template <int MT, class R, class C>
+__device__ __forceinline__ void trsm_lower_h_cta(const C *sL, const R *sInv, C *base, int bstride, int ld, int nbh,
+                                                 int ncols, int m) {
+    constexpr int TRI = Tri<MT>::n, BS = 16;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    for (int re = m; re > 0; re -= BS) {
+        const int rb = max(re - BS, 0);
+        for (int e = tid; e < nbh * ncols; e += NT) {
+            const int b = e / ncols, col = e - b * ncols;
+            const C *Lb = sL + b * TRI;
+            const R *ivb = sInv + b * MT;
+            C *z = base + b * bstride + col;
+            for (int r = re - 1; r >= rb; --r) {
+                C acc = z[r * ld];
+                for (int s = r + 1; s < re; ++s) zmsub_ca(acc, Lb[tri(s, r)], z[s * ld]);
+                z[r * ld] = zscale(acc, ivb[r]);
+            }
+        }
+        __syncthreads();
+        if (rb > 0) {
+            const int per = rb * ncols;
+            for (int e = tid; e < nbh * per; e += NT) {
+                const int b = e / per, rem = e - b * per, r = rem / ncols, col = rem - r * ncols;
+                const C *Lb = sL + b * TRI;
+                C *z = base + b * bstride + col;
+                C acc = z[r * ld];
+#pragma unroll 4
+                for (int s = rb; s < re; ++s) zmsub_ca(acc, Lb[tri(s, r)], z[s * ld]);
+                z[r * ld] = acc;
+            }
+            __syncthreads();
+        }
+    }
+}
+
 // ------------------------------------------------------------ factor: odd
 
 // One chunk of nb odd blocks (chunk index `chunk`) of a factor level, run by
@@ -172,13 +252,17 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
     }
 
     // Z := L^{-1} Z, one item per (block, column); zero columns stay zero
-    for (int e = tid; e < nbh * m2; e += NT) {
-        const int b = e / m2, col = e - b * m2;
-        const int64_t pos = 2 * (t0 + b);
-        if (col < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
-        trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sZ + b * MT * LDZ + col, LDZ, m);
+    if constexpr (MT >= 32) {
+        trsm_lower_cta<MT, R, C>(sL, sInv, sZ, MT * LDZ, LDZ, nbh, m2, m);
+    } else {
+        for (int e = tid; e < nbh * m2; e += NT) {
+            const int b = e / m2, col = e - b * m2;
+            const int64_t pos = 2 * (t0 + b);
+            if (col < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
+            trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sZ + b * MT * LDZ + col, LDZ, m);
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     // keep L, 1/diag(L) and Z for the solves
     for (int e = tid; e < nbh * mm; e += NT) {
@@ -326,11 +410,15 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t
     }
     __syncthreads();
 
-    for (int e = tid; e < nbh * kw; e += NT) {
-        const int b = e / kw, c = e - b * kw;
-        trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sR + b * MT * kc + c, kc, m);
+    if constexpr (MT >= 32) {
+        trsm_lower_cta<MT, R, C>(sL, sInv, sR, MT * kc, kc, nbh, kw, m);
+    } else {
+        for (int e = tid; e < nbh * kw; e += NT) {
+            const int b = e / kw, c = e - b * kw;
+            trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sR + b * MT * kc + c, kc, m);
+        }
+        __syncthreads();
     }
-    __syncthreads();
 
     for (int e = tid; e < nbh * m * kw; e += NT) {
         const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
@@ -451,11 +539,15 @@ __device__ __forceinline__ void solve_up_chunk(const LevelArgsT<R> &a, int64_t c
     __syncthreads();
 
     // x_odd = L^{-H} w
-    for (int e = tid; e < nbh * kw; e += NT) {
-        const int b = e / kw, c = e - b * kw;
-        trsv_lower_h_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sW + b * MT * kc + c, kc, m);
+    if constexpr (MT >= 32) {
+        trsm_lower_h_cta<MT, R, C>(sL, sInv, sW, MT * kc, kc, nbh, kw, m);
+    } else {
+        for (int e = tid; e < nbh * kw; e += NT) {
+            const int b = e / kw, c = e - b * kw;
+            trsv_lower_h_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sW + b * MT * kc + c, kc, m);
+        }
+        __syncthreads();
     }
-    __syncthreads();
     for (int e = tid; e < nbh * m * kw; e += NT) {
         const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
         a.x[(2 * (t0 + b)) * mk + r * k + c0 + c] = sW[(b * MT + r) * kc + c];

@@ -51,7 +51,9 @@ __global__ void __launch_bounds__(256) k_update(z2 *__restrict__ x, const c2 *__
 }
 
 // r_j = y_j - A_j x_j - B_{j-1} x_{j-1} - B_j^H x_{j+1}; one thread per entry
-// (j, a, c), three dot products of length m in FP64.
+// (j, a, c), three dot products of length m in FP64.  The Hermitian A_j is
+// read from its lower triangle in three loops (s < a, s = a, s > a) and the
+// conjugations are folded into the FMAs, so each term is exactly 4 DFMA.
 __global__ void __launch_bounds__(256) k_residual(int64_t N, int m, int k, const z2 *__restrict__ A,
                                                   const z2 *__restrict__ B, const z2 *__restrict__ x,
                                                   const z2 *__restrict__ y, z2 *__restrict__ r) {
@@ -61,18 +63,21 @@ __global__ void __launch_bounds__(256) k_residual(int64_t N, int m, int k, const
         const int rem = (int)(e - j * mk), a = rem / k, c = rem - a * k;
         z2 acc = y[e];
         const z2 *Aj = A + j * mm, *xj = x + j * mk + c;
-        for (int s = 0; s < m; ++s) {
-            // Hermitian A_j from its lower triangle, real diagonal
-            z2 h = s < a ? Aj[a * m + s] : (s > a ? zconj(Aj[s * m + a]) : zmk(Aj[a * m + a].x, 0.0));
-            zmsub(acc, h, xj[(int64_t)s * k]);
+        for (int s = 0; s < a; ++s) zmsub(acc, __ldg(Aj + a * m + s), __ldg(xj + (int64_t)s * k));
+        {
+            const double d = __ldg(&Aj[a * m + a].x);
+            const z2 xv = __ldg(xj + (int64_t)a * k);
+            acc.x = fma(-d, xv.x, acc.x);
+            acc.y = fma(-d, xv.y, acc.y);
         }
+        for (int s = a + 1; s < m; ++s) zmsub_ca(acc, __ldg(Aj + s * m + a), __ldg(xj + (int64_t)s * k));
         if (j >= 1) {
             const z2 *Bl = B + (j - 1) * mm + a * m, *xl = x + (j - 1) * mk + c;
-            for (int s = 0; s < m; ++s) zmsub(acc, Bl[s], xl[(int64_t)s * k]);
+            for (int s = 0; s < m; ++s) zmsub(acc, __ldg(Bl + s), __ldg(xl + (int64_t)s * k));
         }
         if (j + 1 < N) {
             const z2 *Br = B + j * mm + a, *xr = x + (j + 1) * mk + c;
-            for (int s = 0; s < m; ++s) zmsub(acc, zconj(Br[(int64_t)s * m]), xr[(int64_t)s * k]);
+            for (int s = 0; s < m; ++s) zmsub_ca(acc, __ldg(Br + (int64_t)s * m), __ldg(xr + (int64_t)s * k));
         }
         r[e] = acc;
     }

@@ -220,11 +220,16 @@ int mixed_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
     p->B64 = reinterpret_cast<const crsolve_z *>(B);
     p->fallback = false;
     if (cudaMemsetAsync(ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess) return CRSOLVE_ECUDA;
-    if (crs::launch_to_f32(A, reinterpret_cast<crs::c2 *>(ws + p->offA32), p->N * (int64_t)mm, p->nsm, s) ||
-        (p->N > 1 && crs::launch_to_f32(B, reinterpret_cast<crs::c2 *>(ws + p->offB32), (p->N - 1) * (int64_t)mm,
-                                         p->nsm, s)))
-        return CRSOLVE_ECUDA;
     int rc;
+    if ((rc = launch(p, CRSOLVE_K_CONVERT, 0, p->N, s, [&] {
+             return crs::launch_to_f32(A, reinterpret_cast<crs::c2 *>(ws + p->offA32), p->N * (int64_t)mm, p->nsm, s);
+         })))
+        return rc;
+    if (p->N > 1 && (rc = launch(p, CRSOLVE_K_CONVERT, 0, p->N - 1, s, [&] {
+                         return crs::launch_to_f32(B, reinterpret_cast<crs::c2 *>(ws + p->offB32),
+                                                   (p->N - 1) * (int64_t)mm, p->nsm, s);
+                     })))
+        return rc;
     for (int l = 0; l < p->lT; ++l) {
         crs::LevelArgsT<float> a = level_args32(p, l);
         a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
@@ -237,11 +242,16 @@ int mixed_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
     }
     // the level-lT system to FP64, into the FP64 layout's slot for it
     const LevelPlan &Lb = p->lev32[p->lT - 1];
-    if (crs::launch_to_f64(reinterpret_cast<const crs::c2 *>(ws + Lb.offAn), reinterpret_cast<z2 *>(ws + p->lev[p->lT - 1].offAn),
-                           Lb.ne * (int64_t)mm, p->nsm, s) ||
-        crs::launch_to_f64(reinterpret_cast<const crs::c2 *>(ws + Lb.offBn), reinterpret_cast<z2 *>(ws + p->lev[p->lT - 1].offBn),
-                           (Lb.ne > 1 ? Lb.ne - 1 : 0) * (int64_t)mm, p->nsm, s))
-        return CRSOLVE_ECUDA;
+    if ((rc = launch(p, CRSOLVE_K_CONVERT, p->lT, Lb.ne, s, [&] {
+             cudaError_t e = crs::launch_to_f64(reinterpret_cast<const crs::c2 *>(ws + Lb.offAn),
+                                                reinterpret_cast<z2 *>(ws + p->lev[p->lT - 1].offAn),
+                                                Lb.ne * (int64_t)mm, p->nsm, s);
+             if (e != cudaSuccess) return e;
+             return crs::launch_to_f64(reinterpret_cast<const crs::c2 *>(ws + Lb.offBn),
+                                       reinterpret_cast<z2 *>(ws + p->lev[p->lT - 1].offBn),
+                                       (Lb.ne > 1 ? Lb.ne - 1 : 0) * (int64_t)mm, p->nsm, s);
+         })))
+        return rc;
     for (int l = p->lT; l < (int)p->lev.size(); ++l) {
         crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
         a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
@@ -271,7 +281,10 @@ int mixed_correction(crsolve_plan_s *p, int k, const z2 *r, cudaStream_t s) {
     const int64_t mk = (int64_t)p->m * k;
     const int nlev = (int)p->lev.size();
     int rc;
-    if (crs::launch_to_f32(r, reinterpret_cast<crs::c2 *>(ws + p->offY32), p->N * mk, p->nsm, s)) return CRSOLVE_ECUDA;
+    if ((rc = launch(p, CRSOLVE_K_CONVERT, 0, p->N, s, [&] {
+             return crs::launch_to_f32(r, reinterpret_cast<crs::c2 *>(ws + p->offY32), p->N * mk, p->nsm, s);
+         })))
+        return rc;
     for (int l = 0; l < p->lT; ++l) {
         crs::LevelArgsT<float> a = level_args32(p, l);
         a.k = k;
@@ -285,9 +298,11 @@ int mixed_correction(crsolve_plan_s *p, int k, const z2 *r, cudaStream_t s) {
             return rc;
     }
     const LevelPlan &Lb = p->lev32[p->lT - 1];
-    if (crs::launch_to_f64(reinterpret_cast<const crs::c2 *>(ws + Lb.offYn), reinterpret_cast<z2 *>(ws + p->lev[p->lT - 1].offYn),
-                           Lb.ne * mk, p->nsm, s))
-        return CRSOLVE_ECUDA;
+    if ((rc = launch(p, CRSOLVE_K_CONVERT, p->lT, Lb.ne, s, [&] {
+             return crs::launch_to_f64(reinterpret_cast<const crs::c2 *>(ws + Lb.offYn),
+                                       reinterpret_cast<z2 *>(ws + p->lev[p->lT - 1].offYn), Lb.ne * mk, p->nsm, s);
+         })))
+        return rc;
     for (int l = p->lT; l < nlev; ++l) {
         crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
         a.k = k;
@@ -310,9 +325,11 @@ int mixed_correction(crsolve_plan_s *p, int k, const z2 *r, cudaStream_t s) {
         if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, l, a.no, s, [&] { return crs::launch_solve_up(p->mt, a, s); })))
             return rc;
     }
-    if (crs::launch_to_f32(reinterpret_cast<const z2 *>(ws + p->lev[p->lT - 1].offXn), reinterpret_cast<crs::c2 *>(ws + Lb.offXn),
-                           Lb.ne * mk, p->nsm, s))
-        return CRSOLVE_ECUDA;
+    if ((rc = launch(p, CRSOLVE_K_CONVERT, p->lT, Lb.ne, s, [&] {
+             return crs::launch_to_f32(reinterpret_cast<const z2 *>(ws + p->lev[p->lT - 1].offXn),
+                                       reinterpret_cast<crs::c2 *>(ws + Lb.offXn), Lb.ne * mk, p->nsm, s);
+         })))
+        return rc;
     for (int l = p->lT - 1; l >= 0; --l) {
         crs::LevelArgsT<float> a = level_args32(p, l);
         a.k = k;
@@ -341,15 +358,18 @@ int mixed_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     p->last_iters = 0;
     for (int it = 0; it < kMixedMaxIter; ++it) {
         if (it > 0) {
-            if (crs::launch_residual(p->N, p->m, k, reinterpret_cast<const z2 *>(p->A64),
-                                     reinterpret_cast<const z2 *>(p->B64), x, y, r, p->nsm, s))
-                return CRSOLVE_ECUDA;
+            if ((rc = launch(p, CRSOLVE_K_RESIDUAL, 0, p->N, s, [&] {
+                     return crs::launch_residual(p->N, p->m, k, reinterpret_cast<const z2 *>(p->A64),
+                                                 reinterpret_cast<const z2 *>(p->B64), x, y, r, p->nsm, s);
+                 })))
+                return rc;
             p->last_iters = it;
         }
         if ((rc = mixed_correction(p, k, it == 0 ? y : r, s))) return rc;
-        if (cudaMemsetAsync(norms, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess ||
-            crs::launch_update(x, d, n, it == 0, norms, p->nsm, s))
-            return CRSOLVE_ECUDA;
+        if (cudaMemsetAsync(norms, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return CRSOLVE_ECUDA;
+        if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s,
+                         [&] { return crs::launch_update(x, d, n, it == 0, norms, p->nsm, s); })))
+            return rc;
         unsigned long long hn[2];
         if (cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
