@@ -333,8 +333,13 @@ def run_mixed(args):
     import paper_1807_00370_gb300 as crs
     from paper_1807_00370_gb300 import _native as nat
     torch.cuda.set_device(0)
-    shifts = json.load(open(os.path.join(ROOT, "tests", "golden", "kappa_shifts.json")))["mixed_N2p14_m64_k32"]
     N, m, k = MIX_N, MIX_M, MIX_K
+    name = "mixed_N2p14_m64_k32"
+    if args.log2n != 20 and args.log2n != 14:          # smaller cases are for profiling only
+        N = 1 << args.log2n
+        name = f"mixed_N2p{args.log2n}_m64_k32"
+    table = json.load(open(os.path.join(ROOT, "tests", "golden", "kappa_shifts.json")))
+    shifts = table.get(name, {"shifts": {"1e+02": 1.0, "1e+04": 1.0, "1e+06": 1.0}})
     stream = torch.cuda.current_stream()
     runs = []
     for kap in ("1e+02", "1e+04", "1e+06"):

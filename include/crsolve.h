@@ -268,9 +268,9 @@ int crsolve_timing_enable(crsolve_plan p, int32_t enable);
 int crsolve_timing_read(crsolve_plan p, crsolve_kernel_time *out, int32_t cap, int32_t *count);
 
 /*
- * Mixed precision (plans created with CRSOLVE_MIXED).  The fine levels of the
- * reduction (all levels with more than 64 blocks) are factored and solved in
- * FP32; the coarsest levels, the breakdown decision, the residual
+ * Mixed precision (plans created with CRSOLVE_MIXED).  The levels of the
+ * reduction with more than 2 blocks are factored and solved in FP32; the two
+ * coarsest levels, the breakdown decision, the residual
  * r = y - A x and the iterative refinement x += A~^{-1} r are FP64.  In this
  * mode crsolve_factor and crsolve_solve synchronise the stream, and A and B
  * must stay valid and unchanged until the plan is re-factored or destroyed

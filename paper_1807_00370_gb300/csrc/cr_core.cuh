@@ -393,6 +393,10 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t
     C *sV = sR + (size_t)nb * MT * kc;                                   // [nb][MT][kc] v of even t0+b
     C *sW = sV + (size_t)nb * MT * kc;                                   // [nb][MT][kc] P^H r of odd t0+b
     R *sInv = reinterpret_cast<R *>(sW + (size_t)nb * MT * kc);  // [nb][MT]
+    // FP32 with MT >= 32: Z is staged in shared memory too ([nb][MT][2MT]);
+    // at FP32 speed its loads from L2 would otherwise dominate the products
+    constexpr bool kStageZ = (sizeof(R) == 4 && MT >= 32);
+    C *sZs = reinterpret_cast<C *>(sInv + (size_t)nb * MT + (((size_t)nb * MT) & 1));
 
     for (int e = tid; e < nbh * mm; e += NT) {
         const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
@@ -407,6 +411,12 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t
         const int64_t t = t0 + b;
         sR[(b * MT + r) * kc + c] = a.y[(2 * t) * mk + r * k + c0 + c];
         if (t < a.ne) sV[(b * MT + r) * kc + c] = a.y[(2 * t + 1) * mk + r * k + c0 + c];
+    }
+    if constexpr (kStageZ) {
+        for (int e = tid; e < nbh * m * m2; e += NT) {
+            const int b = e / (m * m2), rem = e - b * (m * m2), r = rem / m2, c = rem - r * m2;
+            sZs[(b * MT + r) * 2 * MT + c] = a.Z[(t0 + b) * (int64_t)(m * m2) + rem];
+        }
     }
     __syncthreads();
 
@@ -426,21 +436,64 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t
     }
     // Z^H r: rows p < m give P^H r (kept in sW for the left even block), rows
     // p >= m give Q^H r (subtracted from the right even block in place)
-    for (int e = tid; e < nbh * kw * m2; e += NT) {
-        const int b = e / (kw * m2), rem = e - b * (kw * m2), c = rem / m2, p = rem - c * m2;
-        const int64_t t = t0 + b;
-        if (p < m ? (t == 0) : (2 * t + 1 >= a.Nl)) continue;
-        const C *Zt = a.Z + t * (int64_t)(m * m2) + p;
-        const C *Rb = sR + b * MT * kc + c;
-        C acc = zmk(R(0), R(0));
+    if constexpr (kStageZ) {
+        // FP32: register tiles of 4 rows p x 2 columns c per thread (6 shared
+        // loads per 8 complex FMAs instead of 2 per 1)
+        constexpr int TP = 4, TC = 2;
+        const int np = (m2 + TP - 1) / TP, ncl = (kw + TC - 1) / TC;
+        for (int e = tid; e < nbh * np * ncl; e += NT) {
+            const int b = e / (np * ncl), rem = e - b * (np * ncl), pt = rem / ncl, ct = rem - pt * ncl;
+            const int p0 = pt * TP, cl0 = ct * TC;
+            const C *Zs = sZs + b * MT * 2 * MT;
+            const C *Rb = sR + b * MT * kc;
+            C acc[TP][TC];
 #pragma unroll
-        for (int s = 0; s < MT; ++s)
-            if (s < m) zmac_ca(acc, __ldg(Zt + s * m2), Rb[s * kc]);
-        if (p < m) {
-            sW[(b * MT + p) * kc + c] = acc;
-        } else {
-            C &v = sV[(b * MT + p - m) * kc + c];
-            v = zsub(v, acc);
+            for (int i = 0; i < TP; ++i)
+#pragma unroll
+                for (int j = 0; j < TC; ++j) acc[i][j] = zmk(R(0), R(0));
+            for (int s = 0; s < m; ++s) {
+                C zv[TP], rv[TC];
+#pragma unroll
+                for (int i = 0; i < TP; ++i) zv[i] = (p0 + i < m2) ? Zs[s * 2 * MT + p0 + i] : zmk(R(0), R(0));
+#pragma unroll
+                for (int j = 0; j < TC; ++j) rv[j] = (cl0 + j < kw) ? Rb[s * kc + cl0 + j] : zmk(R(0), R(0));
+#pragma unroll
+                for (int i = 0; i < TP; ++i)
+#pragma unroll
+                    for (int j = 0; j < TC; ++j) zmac_ca(acc[i][j], zv[i], rv[j]);
+            }
+            const int64_t t = t0 + b;
+#pragma unroll
+            for (int i = 0; i < TP; ++i)
+#pragma unroll
+                for (int j = 0; j < TC; ++j) {
+                    const int p = p0 + i, c = cl0 + j;
+                    if (p >= m2 || c >= kw) continue;
+                    if (p < m) {
+                        if (t >= 1) sW[(b * MT + p) * kc + c] = acc[i][j];
+                    } else if (2 * t + 1 < a.Nl) {
+                        C &v = sV[(b * MT + p - m) * kc + c];
+                        v = zsub(v, acc[i][j]);
+                    }
+                }
+        }
+    } else {
+        for (int e = tid; e < nbh * kw * m2; e += NT) {
+            const int b = e / (kw * m2), rem = e - b * (kw * m2), c = rem / m2, p = rem - c * m2;
+            const int64_t t = t0 + b;
+            if (p < m ? (t == 0) : (2 * t + 1 >= a.Nl)) continue;
+            const C *Rb = sR + b * MT * kc + c;
+            const C *Zt = a.Z + t * (int64_t)(m * m2) + p;
+            C acc = zmk(R(0), R(0));
+#pragma unroll
+            for (int s = 0; s < MT; ++s)
+                if (s < m) zmac_ca(acc, __ldg(Zt + s * m2), Rb[s * kc]);
+            if (p < m) {
+                sW[(b * MT + p) * kc + c] = acc;
+            } else {
+                C &v = sV[(b * MT + p - m) * kc + c];
+                v = zsub(v, acc);
+            }
         }
     }
     __syncthreads();
@@ -491,6 +544,8 @@ __device__ __forceinline__ void solve_up_chunk(const LevelArgsT<R> &a, int64_t c
     C *sW = sL + (size_t)nb * TRI;                                            // [nb][MT][kc]
     C *sX = sW + (size_t)nb * MT * kc;                                        // [nb][2MT][kc]
     R *sInv = reinterpret_cast<R *>(sX + (size_t)nb * 2 * MT * kc);  // [nb][MT]
+    constexpr bool kStageZ = (sizeof(R) == 4 && MT >= 32);                     // see solve_down_chunk
+    C *sZs = reinterpret_cast<C *>(sInv + (size_t)nb * MT + (((size_t)nb * MT) & 1));
 
     if (a.level == 0 && *a.status != CRS_NO_FAIL) {
         // the factorisation broke down: the result is NaN
@@ -522,19 +577,59 @@ __device__ __forceinline__ void solve_up_chunk(const LevelArgsT<R> &a, int64_t c
         sX[(b * 2 * MT + m + r) * kc + c] = xr;
         if (t < a.ne) a.x[(2 * t + 1) * mk + r * k + c0 + c] = xr;  // even unknowns
     }
+    if constexpr (kStageZ) {
+        for (int e = tid; e < nbh * m * m2; e += NT) {
+            const int b = e / (m * m2), rem = e - b * (m * m2), r = rem / m2, c = rem - r * m2;
+            sZs[(b * MT + r) * 2 * MT + c] = a.Z[(t0 + b) * (int64_t)(m * m2) + rem];
+        }
+    }
     __syncthreads();
 
     // w = r - P x_left - Q x_right
-    for (int e = tid; e < nbh * m * kw; e += NT) {
-        const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
-        const int64_t t = t0 + b;
-        const C *Zr = a.Z + t * (int64_t)(m * m2) + r * m2;
-        const C *Xb = sX + b * 2 * MT * kc + c;
-        C acc = sW[(b * MT + r) * kc + c];
+    if constexpr (kStageZ) {
+        // FP32: register tiles of 2 rows x 2 columns per thread
+        constexpr int TR = 2, TC = 2;
+        const int nrt = (m + TR - 1) / TR, ncl = (kw + TC - 1) / TC;
+        for (int e = tid; e < nbh * nrt * ncl; e += NT) {
+            const int b = e / (nrt * ncl), rem = e - b * (nrt * ncl), rt = rem / ncl, ct = rem - rt * ncl;
+            const int r0 = rt * TR, cl0 = ct * TC;
+            const C *Zs = sZs + b * MT * 2 * MT;
+            const C *Xb = sX + b * 2 * MT * kc;
+            C acc[TR][TC];
 #pragma unroll
-        for (int s = 0; s < 2 * MT; ++s)
-            if (s < m2) zmsub(acc, __ldg(Zr + s), Xb[s * kc]);
-        sW[(b * MT + r) * kc + c] = acc;
+            for (int i = 0; i < TR; ++i)
+#pragma unroll
+                for (int j = 0; j < TC; ++j)
+                    acc[i][j] = (r0 + i < m && cl0 + j < kw) ? sW[(b * MT + r0 + i) * kc + cl0 + j] : zmk(R(0), R(0));
+            for (int s = 0; s < m2; ++s) {
+                C zv[TR], xv[TC];
+#pragma unroll
+                for (int i = 0; i < TR; ++i) zv[i] = (r0 + i < m) ? Zs[(r0 + i) * 2 * MT + s] : zmk(R(0), R(0));
+#pragma unroll
+                for (int j = 0; j < TC; ++j) xv[j] = (cl0 + j < kw) ? Xb[s * kc + cl0 + j] : zmk(R(0), R(0));
+#pragma unroll
+                for (int i = 0; i < TR; ++i)
+#pragma unroll
+                    for (int j = 0; j < TC; ++j) zmsub(acc[i][j], zv[i], xv[j]);
+            }
+#pragma unroll
+            for (int i = 0; i < TR; ++i)
+#pragma unroll
+                for (int j = 0; j < TC; ++j)
+                    if (r0 + i < m && cl0 + j < kw) sW[(b * MT + r0 + i) * kc + cl0 + j] = acc[i][j];
+        }
+    } else {
+        for (int e = tid; e < nbh * m * kw; e += NT) {
+            const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
+            const int64_t t = t0 + b;
+            const C *Xb = sX + b * 2 * MT * kc + c;
+            C acc = sW[(b * MT + r) * kc + c];
+            const C *Zr = a.Z + t * (int64_t)(m * m2) + r * m2;
+#pragma unroll
+            for (int s = 0; s < 2 * MT; ++s)
+                if (s < m2) zmsub(acc, __ldg(Zr + s), Xb[s * kc]);
+            sW[(b * MT + r) * kc + c] = acc;
+        }
     }
     __syncthreads();
 

@@ -26,7 +26,12 @@ cudaError_t prepare_kernels(int mt);                 // raise shared-memory limi
 // right-hand-side chunk width of the solve kernels.
 int factor_nb(int mt, int64_t no, int nsm);
 int solve_nb(int mt, int64_t no, int nsm);
-int solve_kc(int mt, int k);
+int solve_kc(int mt, int k, int64_t no, int nsm);
+// the same for the FP32 levels of the mixed-precision form
+TileShape tile_shape32(int mt);
+int factor_nb32(int mt, int64_t no, int nsm);
+int solve_nb32(int mt, int64_t no, int nsm);
+int solve_kc32(int mt, int k, int64_t no, int nsm);
 inline int64_t num_ctas(int64_t no, int nb) { return crs_num_ctas(no, nb); }
 
 // Factor sweep of one level (a.nb set by factor_nb): the odd-block kernel

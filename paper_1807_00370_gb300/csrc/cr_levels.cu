@@ -107,6 +107,17 @@ TileShape tile_shape(int mt) {
     return i < 0 ? TileShape{0, 0, 0, 0} : g_tiles[i];
 }
 
+// FP32 levels of the mixed-precision form: narrower right-hand-side chunks at
+// MT >= 32 so that the staged Z still leaves room for two CTAs per SM.
+static const TileShape g_tiles32[5] = {
+    {32, 32, 32, 256}, {16, 16, 16, 256}, {4, 8, 16, 256}, {2, 2, 16, 256}, {1, 1, 16, 256},
+};
+
+TileShape tile_shape32(int mt) {
+    const int i = mt_slot(mt);
+    return i < 0 ? TileShape{0, 0, 0, 0} : g_tiles32[i];
+}
+
 bool set_tile_shape(int mt, const TileShape &ts, size_t smem_limit) {
     const int i = mt_slot(mt);
     if (i < 0 || ts.nb_factor < 1 || ts.nb_solve < 1 || ts.kc_max < 1 || ts.threads < 32 ||
@@ -135,10 +146,13 @@ size_t factor_smem_bytes(int mt, int nb, int rsize) {
     return (size_t)nb * ((2 * tri + 2 * (size_t)mt * mt) * cs + (size_t)mt * rsize);
 }
 
-// Per block: packed L, `panels` right-hand-side panels of MT x kc (3 down, 3 up), 1/diag(L).
+// Per block: packed L, `panels` right-hand-side panels of MT x kc (3 down, 3 up), 1/diag(L),
+// and for FP32 with MT >= 32 the staged Z [MT][2MT] (after 8 bytes of alignment padding).
 size_t solve_smem_bytes(int mt, int nb, int kc, int panels, int rsize) {
     const size_t tri = (size_t)mt * (mt + 1) / 2, cs = 2 * (size_t)rsize;
-    return (size_t)nb * (tri * cs + (size_t)mt * kc * cs * panels + (size_t)mt * rsize);
+    size_t b = (size_t)nb * (tri * cs + (size_t)mt * kc * cs * panels + (size_t)mt * rsize);
+    if (rsize == 4 && mt >= 32) b += 8 + (size_t)nb * mt * 2 * mt * cs;
+    return b;
 }
 
 // Allow every kernel the device's full opt-in shared memory, so that any
@@ -183,9 +197,28 @@ static int level_nb(int nb_max, int64_t no, int nsm) {
 
 int factor_nb(int mt, int64_t no, int nsm) { return level_nb(tile_shape(mt).nb_factor, no, nsm); }
 int solve_nb(int mt, int64_t no, int nsm) { return level_nb(tile_shape(mt).nb_solve, no, nsm); }
-int solve_kc(int mt, int k) {
-    const int kmax = tile_shape(mt).kc_max;
-    return k < kmax ? k : kmax;
+// Right-hand-side columns per solve CTA: the tile's chunk, narrowed on levels
+// with few odd blocks so that the column chunks still spread over about two
+// CTAs per SM (the columns of a triangular solve are independent).
+static int spread_kc(int kmax, int k, int64_t ncta_blocks, int nsm) {
+    int kc = k < kmax ? k : kmax;
+    const int64_t want = 2 * (int64_t)nsm;
+    if (ncta_blocks * ((k + kc - 1) / kc) < want) {
+        const int64_t chunks = (want + ncta_blocks - 1) / ncta_blocks;
+        int64_t c = (k + chunks - 1) / chunks;
+        if (c < 1) c = 1;
+        if (c < kc) kc = (int)c;
+    }
+    return kc;
+}
+
+int solve_kc(int mt, int k, int64_t no, int nsm) {
+    return spread_kc(tile_shape(mt).kc_max, k, num_ctas(no, solve_nb(mt, no, nsm)), nsm);
+}
+int factor_nb32(int mt, int64_t no, int nsm) { return level_nb(tile_shape32(mt).nb_factor, no, nsm); }
+int solve_nb32(int mt, int64_t no, int nsm) { return level_nb(tile_shape32(mt).nb_solve, no, nsm); }
+int solve_kc32(int mt, int k, int64_t no, int nsm) {
+    return spread_kc(tile_shape32(mt).kc_max, k, num_ctas(no, solve_nb32(mt, no, nsm)), nsm);
 }
 
 static unsigned grid_1d(int64_t items, int nsm) {

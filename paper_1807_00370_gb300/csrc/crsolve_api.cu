@@ -26,8 +26,9 @@ struct LevelPlan {
 };
 
 // Mixed precision: levels below `lT` run in FP32 (their own layout), the
-// coarsest levels (N_l <= kMixedCoarse blocks) and the refinement in FP64.
-constexpr int64_t kMixedCoarse = 64;
+// coarsest levels (N_l <= kMixedCoarse blocks: the last two) and the
+// refinement in FP64.
+constexpr int64_t kMixedCoarse = 2;
 constexpr int kMixedMaxIter = 40;
 
 }  // namespace
@@ -185,7 +186,7 @@ int do_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
         crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
         a.k = k;
         a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
-        a.kc = crs::solve_kc(p->mt, k);
+        a.kc = crs::solve_kc(p->mt, k, a.no, p->nsm);
         a.y = (l == 0) ? y : reinterpret_cast<const z2 *>(p->ws + p->lev[l - 1].offYn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s,
                          [&] { return crs::launch_solve_down_odd(p->mt, a, s); })))
@@ -199,7 +200,7 @@ int do_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
         crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
         a.k = k;
         a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
-        a.kc = crs::solve_kc(p->mt, k);
+        a.kc = crs::solve_kc(p->mt, k, a.no, p->nsm);
         a.x = (l == 0) ? x : reinterpret_cast<z2 *>(p->ws + p->lev[l - 1].offXn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, l, a.no, s,
                          [&] { return crs::launch_solve_up(p->mt, a, s); })))
@@ -232,7 +233,7 @@ int mixed_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
         return rc;
     for (int l = 0; l < p->lT; ++l) {
         crs::LevelArgsT<float> a = level_args32(p, l);
-        a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
+        a.nb = crs::factor_nb32(p->mt, a.no, p->nsm);
         if ((rc = launch(p, CRSOLVE_K_FACTOR_ODD, l, a.no, s, [&] { return crs::launch_factor_odd(p->mt, a, s); })))
             return rc;
         if (crs::num_ctas(a.no, a.nb) > 1 &&
@@ -288,8 +289,8 @@ int mixed_correction(crsolve_plan_s *p, int k, const z2 *r, cudaStream_t s) {
     for (int l = 0; l < p->lT; ++l) {
         crs::LevelArgsT<float> a = level_args32(p, l);
         a.k = k;
-        a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
-        a.kc = crs::solve_kc(p->mt, k);
+        a.nb = crs::solve_nb32(p->mt, a.no, p->nsm);
+        a.kc = crs::solve_kc32(p->mt, k, a.no, p->nsm);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s, [&] { return crs::launch_solve_down_odd(p->mt, a, s); })))
             return rc;
         if (crs::num_ctas(a.no, a.nb) > 1 &&
@@ -307,7 +308,7 @@ int mixed_correction(crsolve_plan_s *p, int k, const z2 *r, cudaStream_t s) {
         crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
         a.k = k;
         a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
-        a.kc = crs::solve_kc(p->mt, k);
+        a.kc = crs::solve_kc(p->mt, k, a.no, p->nsm);
         a.y = reinterpret_cast<const z2 *>(ws + p->lev[l - 1].offYn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s, [&] { return crs::launch_solve_down_odd(p->mt, a, s); })))
             return rc;
@@ -320,7 +321,7 @@ int mixed_correction(crsolve_plan_s *p, int k, const z2 *r, cudaStream_t s) {
         crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
         a.k = k;
         a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
-        a.kc = crs::solve_kc(p->mt, k);
+        a.kc = crs::solve_kc(p->mt, k, a.no, p->nsm);
         a.x = reinterpret_cast<z2 *>(ws + p->lev[l - 1].offXn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, l, a.no, s, [&] { return crs::launch_solve_up(p->mt, a, s); })))
             return rc;
@@ -333,8 +334,8 @@ int mixed_correction(crsolve_plan_s *p, int k, const z2 *r, cudaStream_t s) {
     for (int l = p->lT - 1; l >= 0; --l) {
         crs::LevelArgsT<float> a = level_args32(p, l);
         a.k = k;
-        a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
-        a.kc = crs::solve_kc(p->mt, k);
+        a.nb = crs::solve_nb32(p->mt, a.no, p->nsm);
+        a.kc = crs::solve_kc32(p->mt, k, a.no, p->nsm);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, l, a.no, s, [&] { return crs::launch_solve_up(p->mt, a, s); })))
             return rc;
     }

@@ -138,7 +138,7 @@ extern "C" int crsolve_solve_noalloc(int64_t N, int32_t m, int32_t k, const crso
     for (int l = 0; l < nlev; ++l) {
         crs::LevelArgs a = args(l);
         a.nb = crs::solve_nb(mt, a.no, nsm);
-        a.kc = crs::solve_kc(mt, k);
+        a.kc = crs::solve_kc(mt, k, a.no, nsm);
         if (crs::launch_solve_down_odd(mt, a, s) != cudaSuccess) return CRSOLVE_ECUDA;
         if (crs::num_ctas(a.no, a.nb) > 1 && crs::launch_solve_down_fix(a, nsm, s) != cudaSuccess)
             return CRSOLVE_ECUDA;
@@ -146,7 +146,7 @@ extern "C" int crsolve_solve_noalloc(int64_t N, int32_t m, int32_t k, const crso
     for (int l = nlev - 1; l >= 0; --l) {
         crs::LevelArgs a = args(l);
         a.nb = crs::solve_nb(mt, a.no, nsm);
-        a.kc = crs::solve_kc(mt, k);
+        a.kc = crs::solve_kc(mt, k, a.no, nsm);
         if (crs::launch_solve_up(mt, a, s) != cudaSuccess) return CRSOLVE_ECUDA;
     }
     if (info) {
