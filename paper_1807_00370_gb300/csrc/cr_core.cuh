@@ -27,7 +27,10 @@
 // The level kernels run one chunk per CTA; the batched kernel runs all chunks
 // of all levels of one system in one CTA.
 #pragma once
+#include <type_traits>
+
 #include "cr_device.cuh"
+#include "cr_tc.cuh"
 
 __host__ __device__ inline int64_t crs_num_ctas(int64_t no, int nb) { return (no + nb - 1) / nb; }
 
@@ -178,6 +181,132 @@ __device__ __forceinline__ void trsm_lower_h_cta(const C *sL, const R *sInv, C *
     }
 }
 
+// ---------------------------------------------- FP32 Schur products (tcgen05)
+
+// Shared memory of the tensor-core Schur product: 1 KB for the mbarrier and
+// the TMEM address, then an A (2MT x KS) and a B (4MT x KS) operand stage for
+// each of the three TF32 pieces of the FP32 operands.
+constexpr int kTcKS = 16;
+__host__ __device__ constexpr size_t tc_stage_bytes(int mt) {
+    return 1024 + 3 * ((size_t)(2 * mt) * kTcKS * 4 + (size_t)(4 * mt) * kTcKS * 4);
+}
+
+// Lower triangle of Z^H Z for one block on the tensor cores (FP32 levels of
+// the mixed form, MT = 64).  With X = [Re Z; Im Z] and Y = [Im Z; -Re Z]
+// (2m x 2m real, rows s' = 0..2m-1), Re(Z^H Z) = X^T X and Im(Z^H Z) = X^T Y,
+// so D = X^T [X | Y] is one real product with M = 2MT = 128, N = 4MT = 256 and
+// K = 2m, accumulated in TMEM over K-stages of 16.  Every FP32 operand is
+// split exactly into three TF32 pieces x = x1 + x2 + x3 (11 significant bits
+// each), and the six products x1 y1, x1 y2, x2 y1, x1 y3, x2 y2, x3 y1 (smallest
+// first) are accumulated in FP32: the dropped terms are below 2^-33 of the
+// product, so the result has the accuracy of FP32 arithmetic, which the
+// iterative refinement needs (a two-piece split, 2^-22, costs refinement
+// steps).  Warps 0-3 then read D (row p = lane of TMEM) and route entry
+// (p, q), q <= p: P^H P to sW, Q^H Q subtracted from sV, Q^H P negated to the
+// next level's B.  Returns false if a wait gave up.
+template <int MT>
+__device__ bool herk_tc_f32(const LevelArgsT<float> &a, int64_t t, const float2 *Zb, float2 *sWb, float2 *sVb,
+                            unsigned char *stage, int &phase) {
+    constexpr int M = 2 * MT, N = 4 * MT, KS = kTcKS;
+    const int m = a.m, m2 = 2 * m, NT = blockDim.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mm = m * m;
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(stage);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(stage + 16);
+    unsigned char *Ap[3], *Bp[3];
+    for (int i = 0; i < 3; ++i) {
+        Ap[i] = stage + 1024 + i * (M * KS * 4);
+        Bp[i] = stage + 1024 + 3 * (M * KS * 4) + i * (N * KS * 4);
+    }
+    const uint32_t tmem = *tmem_slot;
+    constexpr uint32_t idesc = idesc_tf32(M, N);
+    bool ok = true;
+    auto xval = [&](int sp, int i) -> float {
+        if (sp >= m2 || i >= m2) return 0.f;
+        return sp < m ? Zb[sp * 2 * MT + i].x : Zb[(sp - m) * 2 * MT + i].y;
+    };
+    auto yval = [&](int sp, int j) -> float {
+        if (sp >= m2 || j >= m2) return 0.f;
+        return sp < m ? Zb[sp * 2 * MT + j].y : -Zb[(sp - m) * 2 * MT + j].x;
+    };
+    auto split3 = [](float v, uint32_t &p1, uint32_t &p2, uint32_t &p3) {
+        p1 = cvt_tf32(v);
+        const float r1 = v - __uint_as_float(p1);
+        p2 = cvt_tf32(r1);
+        p3 = cvt_tf32(r1 - __uint_as_float(p2));
+    };
+    const int nst = (m2 + KS - 1) / KS;
+    for (int ks = 0; ks < nst; ++ks) {
+        for (int e = tid; e < M * KS; e += NT) {
+            const int kk = e / M, i = e - kk * M;
+            uint32_t p1, p2, p3;
+            split3(xval(ks * KS + kk, i), p1, p2, p3);
+            const int o = kmaj_off(i, kk, KS);
+            *reinterpret_cast<uint32_t *>(Ap[0] + o) = p1;
+            *reinterpret_cast<uint32_t *>(Ap[1] + o) = p2;
+            *reinterpret_cast<uint32_t *>(Ap[2] + o) = p3;
+        }
+        for (int e = tid; e < N * KS; e += NT) {
+            const int kk = e / N, n = e - kk * N;
+            uint32_t p1, p2, p3;
+            split3(n < M ? xval(ks * KS + kk, n) : yval(ks * KS + kk, n - M), p1, p2, p3);
+            const int o = kmaj_off(n, kk, KS);
+            *reinterpret_cast<uint32_t *>(Bp[0] + o) = p1;
+            *reinterpret_cast<uint32_t *>(Bp[1] + o) = p2;
+            *reinterpret_cast<uint32_t *>(Bp[2] + o) = p3;
+        }
+        fence_async_smem();
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        if (tid == 0) {
+            // (A piece, B piece), smallest terms first
+            const int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
+            for (int pass = 0; pass < 6; ++pass)
+                for (int kq = 0; kq < KS / 8; ++kq) {
+                    const uint64_t ad = umma_desc(smem_u32(Ap[pa[pass]]) + kq * 256, 128, (KS / 4) * 128);
+                    const uint64_t bd = umma_desc(smem_u32(Bp[pb[pass]]) + kq * 256, 128, (KS / 4) * 128);
+                    mma_tf32(tmem, ad, bd, idesc, (ks > 0 || pass > 0 || kq > 0) ? 1u : 0u);
+                }
+            tc_commit(smem_u32(mbar));
+        }
+        ok = mbar_wait(smem_u32(mbar), (uint32_t)phase, 1 << 24) && ok;
+        phase ^= 1;
+        tc_fence_after();
+    }
+    if (warp < 4) {
+        const int p = warp * 32 + lane;
+        const bool hasL = t >= 1, hasR = 2 * t + 1 < a.Nl;
+        for (int c = 0; c < M / 32; ++c) {
+            if (c * 32 > warp * 32 + 31) break;              // no entry q <= p in this column chunk
+            uint32_t vr[32], vi[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), vr);
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(M + c * 32), vi);
+            if (!ok || p >= m2) continue;
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                const int q = c * 32 + j;
+                if (q > p || q >= m2) continue;
+                const float dr = __uint_as_float(vr[j]), di = (q == p) ? 0.f : __uint_as_float(vi[j]);
+                if (p < m) {
+                    if (hasL) sWb[tri(p, q)] = make_float2(dr, di);
+                } else if (q >= m) {
+                    if (hasR) {
+                        float2 &v = sVb[tri(p - m, q - m)];
+                        v.x -= dr;
+                        v.y -= di;
+                    }
+                } else if (hasL && hasR) {
+                    a.Bn[(t - 1) * mm + (p - m) * m + q] = make_float2(-dr, -di);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return ok;
+}
+
 // ------------------------------------------------------------ factor: odd
 
 // One chunk of nb odd blocks (chunk index `chunk`) of a factor level, run by
@@ -279,12 +408,29 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
     }
     __syncthreads();
 
-    // Lower triangle of Z^H Z, one item per entry.  The 2m real diagonal
-    // entries of each block come first, in warps of their own (2 FMA per
-    // term instead of 4).  Parts: Q^H Q is subtracted from the right even
-    // block V_t in place, P^H P is kept in sW (the L buffer, free now) for the
-    // left even block, and Q^H P = -F goes to the next level's B.
+    // Lower triangle of Z^H Z.  Parts: Q^H Q is subtracted from the right
+    // even block V_t in place, P^H P is kept in sW (the L buffer, free now) for
+    // the left even block, and Q^H P = -F goes to the next level's B.
     C *sW = sL;
+    if constexpr (std::is_same<R, float>::value && MT == 64) {
+        // FP32 levels of the mixed form: on the tensor cores (tcgen05, TF32 x 3)
+        unsigned char *stage = reinterpret_cast<unsigned char *>(
+            (reinterpret_cast<uintptr_t>(sInv + (size_t)nb * MT) + 1023) & ~(uintptr_t)1023);
+        if (tid == 0) mbar_init(smem_u32(stage), 1);
+        if (tid < 32) tmem_alloc(smem_u32(stage + 16), 2 * 2 * MT);
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        int phase = 0;
+        bool ok = true;
+        for (int b = 0; b < nbh; ++b)
+            ok = herk_tc_f32<MT>(a, t0 + b, sZ + b * MT * LDZ, sW + b * TRI, sV + b * TRI, stage, phase) && ok;
+        if (tid < 32) tmem_dealloc(*reinterpret_cast<uint32_t *>(stage + 16), 2 * 2 * MT);
+        if (!ok && tid == 0 && a.err) atomicExch(a.err, 1);
+        __syncthreads();
+    } else {
+    // One item per entry.  The 2m real diagonal entries of each block come
+    // first, in warps of their own (2 FMA per term instead of 4).
     const int ndiag = nbh * m2, dpadh = (ndiag + 31) & ~31, noff = m2 * (m2 - 1) / 2;
     for (int e = tid; e < dpadh + nbh * noff; e += NT) {
         if (e < ndiag) {
@@ -325,6 +471,7 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
         }
     }
     __syncthreads();
+    }
 
     // V_j = (A_2j+1 - Q^H Q) - P^H P for the even blocks j = t0 + b.  The
     // CTA's last one misses its right neighbour's P^H P when that neighbour

@@ -109,6 +109,7 @@ struct LevelArgsT {
     const C *xn;        // [ne][m][k]  next level solution
     C *x;               // [Nl][m][k]  level solution
     unsigned long long *status;
+    int *err;           // nullable: set to 1 if a bounded device-side wait gave up
 };
 using LevelArgs = LevelArgsT<double>;
 

@@ -143,7 +143,9 @@ int pick_mt(int m) {
 // rsize = bytes of the real type (8 for FP64, 4 for FP32).
 size_t factor_smem_bytes(int mt, int nb, int rsize) {
     const size_t tri = (size_t)mt * (mt + 1) / 2, cs = 2 * (size_t)rsize;
-    return (size_t)nb * ((2 * tri + 2 * (size_t)mt * mt) * cs + (size_t)mt * rsize);
+    size_t b = (size_t)nb * ((2 * tri + 2 * (size_t)mt * mt) * cs + (size_t)mt * rsize);
+    if (rsize == 4 && mt == 64) b += 1024 + tc_stage_bytes(mt);   // tensor-core operand stages (1 KB aligned)
+    return b;
 }
 
 // Per block: packed L, `panels` right-hand-side panels of MT x kc (3 down, 3 up), 1/diag(L),

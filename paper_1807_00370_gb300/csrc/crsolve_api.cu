@@ -48,7 +48,8 @@ struct crsolve_plan_s {
     // mixed precision
     int lT = 0;                                  // first FP64 level
     std::vector<LevelPlan> lev32;                // FP32 layout of levels < lT
-    size_t offWbd32 = 0, offCbd32 = 0, offA32 = 0, offB32 = 0, offY32 = 0, offX32 = 0, offR64 = 0, offNorms = 0;
+    size_t offWbd32 = 0, offCbd32 = 0, offA32 = 0, offB32 = 0, offY32 = 0, offX32 = 0, offR64 = 0, offNorms = 0,
+           offErr = 0;
     const crsolve_z *A64 = nullptr, *B64 = nullptr;  // the caller's FP64 system, read by the residual
     bool fallback = false;                       // FP32 factor broke down: everything in FP64
     int last_iters = 0;
@@ -116,6 +117,7 @@ crs::LevelArgsT<float> level_args32(const crsolve_plan_s *p, int l) {
     a.y = reinterpret_cast<const C *>(ws + (l == 0 ? p->offY32 : p->lev32[l - 1].offYn));
     a.x = reinterpret_cast<C *>(ws + (l == 0 ? p->offX32 : p->lev32[l - 1].offXn));
     a.status = reinterpret_cast<unsigned long long *>(ws + p->offStatus);
+    a.err = reinterpret_cast<int *>(ws + p->offErr);
     return a;
 }
 
@@ -220,7 +222,9 @@ int mixed_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
     p->A64 = reinterpret_cast<const crsolve_z *>(A);
     p->B64 = reinterpret_cast<const crsolve_z *>(B);
     p->fallback = false;
-    if (cudaMemsetAsync(ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess) return CRSOLVE_ECUDA;
+    if (cudaMemsetAsync(ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess ||
+        cudaMemsetAsync(ws + p->offErr, 0, sizeof(int), s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
     int rc;
     if ((rc = launch(p, CRSOLVE_K_CONVERT, 0, p->N, s, [&] {
              return crs::launch_to_f32(A, reinterpret_cast<crs::c2 *>(ws + p->offA32), p->N * (int64_t)mm, p->nsm, s);
@@ -264,9 +268,12 @@ int mixed_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
             return rc;
     }
     unsigned long long st = 0;
+    int err = 0;
     if (cudaMemcpyAsync(&st, ws + p->offStatus, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaMemcpyAsync(&err, ws + p->offErr, sizeof(err), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return CRSOLVE_ECUDA;
+    if (err) return CRSOLVE_ETIMEOUT;
     p->factored = true;
     if (st != CRS_NO_FAIL) {
         p->fallback = true;
@@ -478,6 +485,7 @@ int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, u
         p->offX32 = take(cur, N * mk * c32);
         p->offR64 = take(cur, N * mk * zsz);
         p->offNorms = take(cur, 16);
+        p->offErr = take(cur, 16);
     }
     p->total = cur;
     *out_plan = p;
