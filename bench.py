@@ -45,6 +45,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # ~1.9 DFMA/clk/SM), 152 SMs, 2070 MHz maximum SM clock
 FP64_FMA_PER_CLK_SM, N_SM, SM_MAX_MHZ = 2, 152, 2070.0
 FP64_PEAK_GFLOPS = FP64_FMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ / 1e3
+# ncu: k_factor_odd<8, double>, level 0 of N = 2^18: dram 538.0 MB read + 625.1 MB written for 2^17 odd blocks
+TRAFFIC_PER_ODD_BLOCK = (538.0e6 + 625.1e6) / (1 << 17)
 
 
 def flops_factor_per_odd_block(m: int) -> float:
@@ -523,7 +525,11 @@ def main():
                        f"{ws} independent system(s), one per GPU"},
             "roofline": {"bound": "alu", "kernel": "k_factor_odd<8>, all levels",
                          "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                         "frac": (achieved / peak_tf) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak_tf) if achieved else None,
+                         "traffic": TRAFFIC_PER_ODD_BLOCK * (fac["units"] / max(fac["launches"], 1)),
+                         "traffic_note": "dram read+write per launch, scaled by odd blocks from the ncu capture of "
+                                         "level 0 at N=2^18 (1163 MB for 2^17 odd blocks; "
+                                         "profiles/k_factor_odd_m8_N2p18_level0.md)",
                          "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived)",
                          "flops_per_unit": flops_factor_per_odd_block(M), "units": fac["units"] // args.steps,
                          "launches_per_step": fac["launches"] // args.steps},
