@@ -288,14 +288,18 @@ int crsolve_launch_count(crsolve_plan p, int64_t *count);
 
 /*
  * Tile shape of block-size class mt (4, 8, 16, 32 or 64; a plan with block
- * size m uses the smallest class >= m): odd blocks per CTA of the factor and
- * of the solve kernels, right-hand-side columns per solve CTA, and threads
- * per CTA (a multiple of 32, at most 256).  Process-wide, for later launches.
- * crsolve_tile_set returns CRSOLVE_EINVAL for a shape that is out of range or
- * does not fit in the current device's shared memory.
+ * size m uses the smallest class >= m) of the FP64 kernels: odd blocks per
+ * CTA of the factor and of the solve kernels, right-hand-side columns per
+ * solve CTA (narrowed automatically on small levels), and threads per CTA of
+ * the factor and of the solve kernels (multiples of 32, at most 256).
+ * Process-wide, for later launches.  crsolve_tile_set returns CRSOLVE_EINVAL
+ * for a shape that is out of range or does not fit in the current device's
+ * shared memory.
  */
-int crsolve_tile_set(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc, int32_t threads);
-int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads);
+int crsolve_tile_set(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc, int32_t threads,
+                     int32_t threads_solve);
+int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads,
+                     int32_t *threads_solve);
 
 /* Number of levels of the plan (floor(log2 N) + 1) and the level sizes. */
 int crsolve_plan_levels(crsolve_plan p, int32_t *nlev, int64_t *sizes /* [nlev] or NULL */);

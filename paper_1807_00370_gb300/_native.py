@@ -65,7 +65,7 @@ SIGNATURES = {
     "crsolve_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "crsolve_mixed_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I32)]),
-    "crsolve_tile_set": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32]),
+    "crsolve_tile_set": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _I32]),
     "crsolve_batch_create": (ctypes.c_int, [_I32, _P, _P, _P, ctypes.POINTER(_P)]),
     "crsolve_batch_tile_set": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32]),
     "crsolve_batch_workspace_bytes": (ctypes.c_int, [_P, _SZ, ctypes.POINTER(_SZ), ctypes.POINTER(_I32)]),
@@ -76,7 +76,7 @@ SIGNATURES = {
     "crsolve_batch_info": (ctypes.c_int, [_P, _P, _P]),
     "crsolve_batch_destroy": (ctypes.c_int, [_P]),
     "crsolve_solve_noalloc": (ctypes.c_int, [_I64, _I32, _I32, _P, _P, _P, _P, ctypes.POINTER(CrsolveInfo), _P]),
-    "crsolve_tile_get": (ctypes.c_int, [_I32] + [ctypes.POINTER(_I32)] * 4),
+    "crsolve_tile_get": (ctypes.c_int, [_I32] + [ctypes.POINTER(_I32)] * 5),
 }
 
 

@@ -211,12 +211,14 @@ def crsolve_launch_count(plan: Plan) -> int:
     return int(c.value)
 
 
-def crsolve_tile_set(mt: int, nb_factor: int, nb_solve: int, kc: int, threads: int) -> None:
-    nat.check(nat.load().crsolve_tile_set(mt, nb_factor, nb_solve, kc, threads), "crsolve_tile_set")
+def crsolve_tile_set(mt: int, nb_factor: int, nb_solve: int, kc: int, threads: int,
+                     threads_solve: int | None = None) -> None:
+    nat.check(nat.load().crsolve_tile_set(mt, nb_factor, nb_solve, kc, threads,
+                                          threads if threads_solve is None else threads_solve), "crsolve_tile_set")
 
 
 def crsolve_tile_get(mt: int):
-    v = [ctypes.c_int32() for _ in range(4)]
+    v = [ctypes.c_int32() for _ in range(5)]
     nat.check(nat.load().crsolve_tile_get(mt, *[ctypes.byref(x) for x in v]), "crsolve_tile_get")
     return tuple(int(x.value) for x in v)
 

@@ -11,7 +11,8 @@ struct TileShape {
     int nb_factor;
     int nb_solve;
     int kc_max;
-    int threads;
+    int threads;        // threads per CTA of the factor kernels
+    int threads_solve;  // threads per CTA of the solve kernels
 };
 
 TileShape tile_shape(int mt);

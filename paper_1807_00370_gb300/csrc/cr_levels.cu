@@ -82,13 +82,15 @@ __global__ void k_nan_if_failed(z2 *x, int64_t n, const unsigned long long *stat
 
 // ------------------------------------------------------------- host side
 
-// Default tile shapes per block-size class; crsolve_tile_set overrides them.
+// Default tile shapes per block-size class (swept on a GB300: N = 2^20,
+// m = 8, k = 4; N = 2^16, m = 16, k = 8; N = 2^12, m = 32, k = 16;
+// N = 2^14, m = 64, k = 32); crsolve_tile_set overrides them.
 static TileShape g_tiles[5] = {
-    {32, 32, 32, 256},  // MT = 4
-    {16, 16, 16, 256},  // MT = 8
-    {4, 8, 16, 256},    // MT = 16
-    {2, 2, 32, 256},    // MT = 32
-    {1, 1, 32, 256},    // MT = 64
+    {32, 32, 32, 256, 256},  // MT = 4
+    {16, 16, 16, 256, 256},  // MT = 8
+    {8, 4, 8, 256, 128},     // MT = 16
+    {2, 1, 16, 256, 256},    // MT = 32
+    {1, 1, 16, 256, 256},    // MT = 64
 };
 
 static int mt_slot(int mt) {
@@ -104,24 +106,26 @@ static int mt_slot(int mt) {
 
 TileShape tile_shape(int mt) {
     const int i = mt_slot(mt);
-    return i < 0 ? TileShape{0, 0, 0, 0} : g_tiles[i];
+    return i < 0 ? TileShape{0, 0, 0, 0, 0} : g_tiles[i];
 }
 
 // FP32 levels of the mixed-precision form: narrower right-hand-side chunks at
 // MT >= 32 so that the staged Z still leaves room for two CTAs per SM.
 static const TileShape g_tiles32[5] = {
-    {32, 32, 32, 256}, {16, 16, 16, 256}, {4, 8, 16, 256}, {2, 2, 16, 256}, {1, 1, 16, 256},
+    {32, 32, 32, 256, 256}, {16, 16, 16, 256, 256}, {4, 8, 16, 256, 256}, {2, 2, 16, 256, 256},
+    {1, 1, 16, 256, 256},
 };
 
 TileShape tile_shape32(int mt) {
     const int i = mt_slot(mt);
-    return i < 0 ? TileShape{0, 0, 0, 0} : g_tiles32[i];
+    return i < 0 ? TileShape{0, 0, 0, 0, 0} : g_tiles32[i];
 }
 
 bool set_tile_shape(int mt, const TileShape &ts, size_t smem_limit) {
     const int i = mt_slot(mt);
     if (i < 0 || ts.nb_factor < 1 || ts.nb_solve < 1 || ts.kc_max < 1 || ts.threads < 32 ||
-        ts.threads > 256 || ts.threads % 32)
+        ts.threads > 256 || ts.threads % 32 || ts.threads_solve < 32 || ts.threads_solve > 256 ||
+        ts.threads_solve % 32)
         return false;
     if (factor_smem_bytes(mt, ts.nb_factor, 8) > smem_limit ||
         solve_smem_bytes(mt, ts.nb_solve, ts.kc_max, 3, 8) > smem_limit)
@@ -234,21 +238,24 @@ static unsigned grid_1d(int64_t items, int nsm) {
 template <int MT, class R>
 static cudaError_t factor_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const unsigned grid = (unsigned)num_ctas(a.no, a.nb);
-    k_factor_odd<MT, R><<<grid, tile_shape(MT).threads, factor_smem_bytes(MT, a.nb, sizeof(R)), s>>>(a);
+    const int th = sizeof(R) == 4 ? tile_shape32(MT).threads : tile_shape(MT).threads;
+    k_factor_odd<MT, R><<<grid, th, factor_smem_bytes(MT, a.nb, sizeof(R)), s>>>(a);
     return cudaGetLastError();
 }
 
 template <int MT, class R>
 static cudaError_t solve_down_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const dim3 grid((unsigned)num_ctas(a.no, a.nb), (unsigned)((a.k + a.kc - 1) / a.kc));
-    k_solve_down_odd<MT, R><<<grid, tile_shape(MT).threads, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
+    const int th = sizeof(R) == 4 ? tile_shape32(MT).threads_solve : tile_shape(MT).threads_solve;
+    k_solve_down_odd<MT, R><<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
     return cudaGetLastError();
 }
 
 template <int MT, class R>
 static cudaError_t solve_up_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const dim3 grid((unsigned)num_ctas(a.no, a.nb), (unsigned)((a.k + a.kc - 1) / a.kc));
-    k_solve_up<MT, R><<<grid, tile_shape(MT).threads, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
+    const int th = sizeof(R) == 4 ? tile_shape32(MT).threads_solve : tile_shape(MT).threads_solve;
+    k_solve_up<MT, R><<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
     return cudaGetLastError();
 }
 
