@@ -342,42 +342,63 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
     }
     __syncthreads();
 
-    // Cholesky, left-looking by columns.  Pass 1 of column c: the pivots
-    // (one item per block, in warps of their own so that the sqrt path does
-    // not diverge from the off-diagonal path), then the unscaled entries
-    // below the pivot.  Pass 2 scales them by 1 / pivot.
+    // Cholesky by panels of PW columns (one panel of m columns when MT < 32).
+    // Inside a panel, left-looking by columns: pass 1 of column c computes the
+    // pivots (one item per block, in warps of their own so that the sqrt path
+    // does not diverge from the off-diagonal path) and the unscaled entries
+    // below the pivot, summing only over the panel's earlier columns; pass 2
+    // scales them by 1 / pivot.  After a panel, the trailing lower triangle is
+    // updated in parallel (one item per entry), so the dependent chains of the
+    // column steps stay shorter than PW.
     const int dpad = (nbh + 31) & ~31;
-    for (int c = 0; c < m; ++c) {
-        const int below = m - c - 1;
-        for (int e = tid; e < dpad + nbh * below; e += NT) {
-            if (e < nbh) {
-                const int b = e;
-                C *Lb = sL + b * TRI;
-                R d = Lb[tri(c, c)].x;
-                for (int s = 0; s < c; ++s) {
-                    const C l = Lb[tri(c, s)];
-                    d = fmx(-l.x, l.x, d);
-                    d = fmx(-l.y, l.y, d);
+    const int PW = (MT >= 32) ? 16 : m;
+    for (int kb = 0; kb < m; kb += PW) {
+        const int ke = min(kb + PW, m);
+        for (int c = kb; c < ke; ++c) {
+            const int below = m - c - 1;
+            for (int e = tid; e < dpad + nbh * below; e += NT) {
+                if (e < nbh) {
+                    const int b = e;
+                    C *Lb = sL + b * TRI;
+                    R d = Lb[tri(c, c)].x;
+                    for (int s = kb; s < c; ++s) {
+                        const C l = Lb[tri(c, s)];
+                        d = fmx(-l.x, l.x, d);
+                        d = fmx(-l.y, l.y, d);
+                    }
+                    if (!(d > R(0))) report_fail(a.status, a.level, 2 * (t0 + b) + 1);
+                    const R iv = rsq(d);
+                    sInv[b * MT + c] = iv;
+                    Lb[tri(c, c)] = zmk(d * iv, R(0));
+                } else if (e >= dpad) {
+                    const int e2 = e - dpad, b = e2 / below, r = c + 1 + (e2 - b * below);
+                    C *Lb = sL + b * TRI;
+                    C u = Lb[tri(r, c)];
+                    for (int s = kb; s < c; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(c, s)]);
+                    Lb[tri(r, c)] = u;
                 }
-                if (!(d > R(0))) report_fail(a.status, a.level, 2 * (t0 + b) + 1);
-                const R iv = rsq(d);
-                sInv[b * MT + c] = iv;
-                Lb[tri(c, c)] = zmk(d * iv, R(0));
-            } else if (e >= dpad) {
-                const int e2 = e - dpad, b = e2 / below, r = c + 1 + (e2 - b * below);
-                C *Lb = sL + b * TRI;
-                C u = Lb[tri(r, c)];
-                for (int s = 0; s < c; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(c, s)]);
-                Lb[tri(r, c)] = u;
             }
+            __syncthreads();
+            for (int e = tid; e < nbh * below; e += NT) {
+                const int b = e / below, r = c + 1 + (e - b * below);
+                C *p = sL + b * TRI + tri(r, c);
+                *p = zscale(*p, sInv[b * MT + c]);
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        for (int e = tid; e < nbh * below; e += NT) {
-            const int b = e / below, r = c + 1 + (e - b * below);
-            C *p = sL + b * TRI + tri(r, c);
-            *p = zscale(*p, sInv[b * MT + c]);
+        if (ke < m) {
+            // A[r][q] -= sum_{s in panel} L[r][s] conj(L[q][s]) for ke <= q <= r < m
+            const int nr = m - ke, ntr = nr * (nr + 1) / 2;
+            for (int e = tid; e < nbh * ntr; e += NT) {
+                const int b = e / ntr, f = e - b * ntr, rr = tri_row(f), qq = f - rr * (rr + 1) / 2;
+                const int r = ke + rr, q = ke + qq;
+                C *Lb = sL + b * TRI;
+                C u = Lb[tri(r, q)];
+                for (int s = kb; s < ke; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(q, s)]);
+                Lb[tri(r, q)] = u;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 
     // Z := L^{-1} Z, one item per (block, column); zero columns stay zero
