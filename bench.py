@@ -165,6 +165,24 @@ def cpu_oracle_sample(seconds: float = 12.0, n_sample: int = 1 << 17):
     return value, cores, desc, (A, B, y, x)
 
 
+def oracle_rate(systems, seconds: float = 10.0, backward: bool = False):
+    """The CPU oracle as it stands, on the host cores, over a list of
+    (A, B, y[, c]) systems, repeated for about `seconds`; block-rows/s."""
+    import oracle
+    rows = sum(s[0].shape[0] for s in systems)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        for sysm in systems:
+            x, _ = oracle.cr_solve(*sysm[:3])
+            if backward:
+                oracle.cr_backward(sysm[0], sysm[1], x, sysm[3])
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return rows * reps / el, oracle.max_threads(), reps, el
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -258,6 +276,14 @@ def run_batched(args):
         "breakdown_count": sum(1 for r in infos if r["status"]),
         "gpu_launches": args.steps, "clocks": clocks, "e2e": None, "cpu_baseline": None,
     }
+    if not args.no_cpu_baseline:
+        rng = np.random.default_rng(0)
+        pick = rng.choice(len(Ns), 32, replace=False)
+        sample = [tuple(t.cpu().numpy() for t in b.system_view(int(i), A, B, y)) for i in pick]
+        v, cores, reps, el = oracle_rate(sample)
+        line["cpu_baseline"] = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{reps} passes over 32 randomly chosen systems of the batch "
+                                          f"({sum(s[0].shape[0] for s in sample)} block rows), {el:.1f} s"}
     print(json.dumps(line), flush=True)
 
 
@@ -321,6 +347,12 @@ def run_adjoint(args):
         "kernels": {kk: {"ms_per_step": v} for kk, v in by.items()},
         "gpu_launches": crs.crsolve_launch_count(plan) - launches0, "e2e": None, "cpu_baseline": None,
     }
+    if not args.no_cpu_baseline:
+        sA, sB, sy = synthetic.gen_system(1 << 12, m, k, seed=ADJ_SEED)
+        sc = synthetic.gen_cotangent(1 << 12, m, k, seed=ADJ_SEED)
+        v, cores, reps, el = oracle_rate([(sA, sB, sy, sc)], backward=True)
+        line["cpu_baseline"] = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{reps} oracle solve + backward of an N=2^12, m={m}, k={k} system, {el:.1f} s"}
     print(json.dumps(line), flush=True)
 
 
@@ -386,6 +418,11 @@ def run_mixed(args):
         "fp64_path_frac_of_peak": N * flops_per_block_row(m, k) / (runs[0]["fp64_ms"] * 1e-3) / 1e12 / peak_tf,
         "e2e": None, "cpu_baseline": None,
     }
+    if not args.no_cpu_baseline:
+        small = table.get("mixed_N2p10_m64_k32", {"shifts": {"1e+02": 1.0}})["shifts"]["1e+02"]
+        v, cores, reps, el = oracle_rate([synthetic.gen_system(1 << 10, m, k, seed=MIX_SEED, shift=small)])
+        line["cpu_baseline"] = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle",
+                                "sample": f"{reps} oracle solves of an N=2^10, m={m}, k={k}, kappa~1e2 system, {el:.1f} s"}
     print(json.dumps(line), flush=True)
 
 

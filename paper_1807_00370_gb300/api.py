@@ -264,22 +264,41 @@ class CRSolveFn(torch.autograd.Function):
     """x = A^{-1} y with the cyclic-reduction solver; backward by
     crsolve_backward (a Hermitian re-solve with the stored factors and fused
     outer products).  A_j is treated as Hermitian: its gradient is projected
-    onto Hermitian matrices."""
+    onto Hermitian matrices.
+
+    keep_factors=False trades compute for memory: the forward pass frees its
+    plan (the per-level factors and reduced systems) and keeps only A, B and
+    x; the backward pass re-factors A to get the factors back.  The
+    re-factorisation is deterministic, so the gradients are identical."""
 
     @staticmethod
-    def forward(ctx, A, B, y):
+    def forward(ctx, A, B, y, keep_factors: bool = True):
         N, m, _ = A.shape
+        A, B, y = A.contiguous(), None if B is None else B.contiguous(), y.contiguous()
         plan = Plan(N, m, y.shape[-1], device=A.device)
-        crsolve_factor(plan, A.contiguous(), None if B is None else B.contiguous())
-        x = crsolve_solve(plan, y.contiguous())
-        ctx.plan = plan
-        ctx.save_for_backward(x)
+        crsolve_factor(plan, A, B)
+        x = crsolve_solve(plan, y)
         ctx.has_B = B is not None
+        ctx.keep = bool(keep_factors)
+        if ctx.keep:
+            ctx.plan = plan
+            ctx.save_for_backward(x)
+        else:
+            plan.close()
+            del plan
+            ctx.save_for_backward(x, A, B if B is not None else A.new_empty(0))
         return x
 
     @staticmethod
     def backward(ctx, gx):
-        (x,) = ctx.saved_tensors
-        gy, gA, gB = crsolve_backward(ctx.plan, x, gx.contiguous(), ctx.needs_input_grad[0],
+        if ctx.keep:
+            (x,) = ctx.saved_tensors
+            plan = ctx.plan
+        else:
+            x, A, B = ctx.saved_tensors
+            N, m, _ = A.shape
+            plan = Plan(N, m, x.shape[-1], device=A.device)
+            crsolve_factor(plan, A, B if ctx.has_B else None)
+        gy, gA, gB = crsolve_backward(plan, x, gx.contiguous(), ctx.needs_input_grad[0],
                                       ctx.needs_input_grad[1] and ctx.has_B)
-        return gA, gB, gy if ctx.needs_input_grad[2] else None
+        return gA, gB, gy if ctx.needs_input_grad[2] else None, None

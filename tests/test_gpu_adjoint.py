@@ -106,3 +106,19 @@ def test_gradients_are_nan_after_breakdown(cuda_ok):
     c = synthetic.gen_cotangent(32, 4, 2, seed=5)
     x, gy, gA, gB = _backward(A, B, y, c)
     assert torch.isnan(gy).all() and torch.isnan(gA).all() and torch.isnan(gB).all()
+
+
+def test_recomputed_factors_give_identical_gradients(cuda_ok):
+    """keep_factors=False frees the plan after the forward pass and re-factors
+    in the backward pass; the gradients are bit-identical."""
+    N, m, k = 200, 8, 3
+    A, B, y = synthetic.gen_system(N, m, k, seed=77)
+    c = torch.from_numpy(synthetic.gen_cotangent(N, m, k, seed=77)).cuda()
+    grads = []
+    for keep in (True, False):
+        tA, tB, ty = (torch.from_numpy(a).cuda().requires_grad_() for a in (A, B, y))
+        x = crs.CRSolveFn.apply(tA, tB, ty, keep)
+        torch.real(torch.sum(torch.conj(c) * x)).backward()
+        grads.append((tA.grad, tB.grad, ty.grad))
+    for g1, g2 in zip(*grads):
+        assert torch.equal(g1, g2)
