@@ -18,6 +18,11 @@ Functions and the passages they follow:
   cr_backward  adjoint of x = A^{-1} y (the paper has no adjoint; this is the
                plain definition: gy = A^{-1} gx, gA = -herm(gy x^H),
                gB_j = -(gy_{j+1} x_j^H + x_{j+1} gy_j^H))
+  alg1_solve   the paper's own recursion, Algorithm 1 (Sec. 3): both the odd
+               system (U, E, u) and the even system (V, F, v) of eq. Formulas
+               are formed and solved recursively down to single blocks
+               (N a power of two)
+  alg1_split   one split of Algorithm 1 (eq. Formulas, both halves)
 """
 from __future__ import annotations
 
@@ -76,6 +81,10 @@ def _load():
         lib.oracle_matvec.restype = None
         lib.oracle_cr_backward.argtypes = [i64, i32, i32, P, P, P, P, P, P, P]
         lib.oracle_cr_backward.restype = i32
+        lib.oracle_alg1_solve.argtypes = [i64, i32, i32, P, P, P, P, ctypes.POINTER(OracleInfo)]
+        lib.oracle_alg1_solve.restype = i32
+        lib.oracle_alg1_split.argtypes = [i64, i32, i32, P, P, P, P, P, P, P, P, P]
+        lib.oracle_alg1_split.restype = i64
         lib.oracle_set_threads.argtypes = [i32]
         lib.oracle_set_threads.restype = None
         lib.oracle_max_threads.argtypes = []
@@ -167,3 +176,43 @@ def cr_backward(A, B, x, gx):
     st = lib.oracle_cr_backward(N, m, x.shape[2], _p(A), _p(B) if N > 1 else None, _p(x), _p(gx),
                                 _p(gy), _p(gA), _p(gB) if N > 1 else None)
     return gy, gA, gB, int(st)
+
+
+def alg1_solve(A, B, y):
+    """x = A^{-1} y by Algorithm 1 (N a power of two).  Returns (x, info dict);
+    info["level"] is the recursion depth of the first breakdown and
+    info["orig_block"] the smallest failing original block at that depth."""
+    lib = _load()
+    A, B, y = _c(A), _c(B), _c(y)
+    N, m = _shapes(A, B, y)
+    if N < 1 or N & (N - 1):
+        raise ValueError("Algorithm 1 needs N to be a power of two")
+    k = y.shape[2]
+    x = np.empty_like(y)
+    info = OracleInfo()
+    lib.oracle_alg1_solve(N, m, k, _p(A), _p(B) if N > 1 else None, _p(y), _p(x), ctypes.byref(info))
+    return x, {"status": info.status, "level": info.level, "block": info.block,
+               "orig_block": info.orig_block}
+
+
+def alg1_split(A, B, y=None):
+    """One split of Algorithm 1 on an even number of blocks.  Returns a dict
+    with U, E, u (odd system), V, F, v (even system) and fail (0 or the
+    smallest failing 1-based block index)."""
+    lib = _load()
+    A, B = _c(A), _c(B)
+    N, m = _shapes(A, B, y)
+    if N < 2 or N % 2:
+        raise ValueError("a split needs an even number of blocks")
+    h = N // 2
+    k = 1 if y is None else y.shape[2]
+    y = None if y is None else _c(y)
+    U = np.zeros((h, m, m), np.complex128)
+    V = np.zeros_like(U)
+    E = np.zeros((max(h - 1, 0), m, m), np.complex128)
+    F = np.zeros_like(E)
+    u = np.zeros((h, m, k), np.complex128) if y is not None else None
+    v = np.zeros_like(u) if y is not None else None
+    fail = lib.oracle_alg1_split(N, m, k, _p(A), _p(B), _p(y), _p(U), _p(E) if h > 1 else None, _p(u),
+                                 _p(V), _p(F) if h > 1 else None, _p(v))
+    return {"U": U, "E": E, "u": u, "V": V, "F": F, "v": v, "fail": int(fail)}

@@ -1,6 +1,8 @@
 /*
- * cr_oracle.c -- CPU reference for classic cyclic reduction (CR) on Hermitian
- * positive definite block-tridiagonal systems.
+ * cr_oracle.c -- CPU reference for cyclic reduction (CR) on Hermitian
+ * positive definite block-tridiagonal systems: classic CR (reduce to the even
+ * system, back-substitute the odd unknowns) and, at the end of the file, the
+ * paper's Algorithm 1 (reduce to both halves and recurse on both).
  *
  * TEST INFRASTRUCTURE ONLY.  This file is the correctness oracle: it is used by
  * the tests, by the package's smoke check and by the CPU-baseline leg of
@@ -408,4 +410,238 @@ int oracle_cr_backward(int64_t N, int m, int k, const zc *A, const zc *B, const 
                 }
     }
     return st;
+}
+
+/* ------------------------------------------------------------------------
+ * The paper's own method (Sec. 2 "Formulation of the Method" and Sec. 3,
+ * Algorithm 1): both halves are reduced.  For a system of n = 2^L blocks,
+ * with the boundary auxiliaries B_0 = B_n = 0 and A_0 = A_{n+1} = I, the odd
+ * system (U, E, u) and the even system (V, F, v) of eq. Formulas are, for
+ * j = 1..n/2,
+ *   U_j = A_{2j-1} - B_{2j-2} A_{2j-2}^{-1} B_{2j-2}^H - B_{2j-1}^H A_{2j}^{-1} B_{2j-1}
+ *   E_j = -B_{2j} A_{2j}^{-1} B_{2j-1}                              (j < n/2)
+ *   u_j = y_{2j-1} - B_{2j-2} A_{2j-2}^{-1} y_{2j-2} - B_{2j-1}^H A_{2j}^{-1} y_{2j}
+ *   V_j = A_{2j} - B_{2j-1} A_{2j-1}^{-1} B_{2j-1}^H - B_{2j}^H A_{2j+1}^{-1} B_{2j}
+ *   F_j = -B_{2j+1} A_{2j+1}^{-1} B_{2j}                            (j < n/2)
+ *   v_j = y_{2j} - B_{2j-1} A_{2j-1}^{-1} y_{2j-1} - B_{2j}^H A_{2j+1}^{-1} y_{2j+1}
+ * Every product G1^H M^{-1} G2 is formed by Sec. 4's rule: M = L L^H,
+ * (L\G1)^H (L\G2), and G^H M^{-1} G as the Hermitian (L\G)^H (L\G) built on
+ * its lower triangle.  Both systems are solved recursively down to single
+ * m x m blocks, which are solved by Cholesky; x is reassembled as
+ * x_{2j-1} = (x_o)_j, x_{2j} = (x_e)_j.
+ *
+ * Readings: n must be a power of two (Algorithm 1 assumes it).  Each A_i of a
+ * system is factored once, before the formulas use it.  Breakdown: a failing
+ * pivot of the factorisation of some A_i ends that subsystem; the reported
+ * failure is the smallest recursion depth with a failure and, within it, the
+ * smallest 1-based index of the failing block in the original system (the
+ * unknown x_i that the failing block belongs to).
+ * ------------------------------------------------------------------------ */
+
+/* G1^H M^{-1} G2 = (L\G1)^H (L\G2) for m x n1 and m x n2 operands. */
+static void chol_cross(int m, int n1, int n2, const zc *L, const zc *G1, const zc *G2, zc *out)
+{
+    zc *T1 = (zc *)malloc(sizeof(zc) * (size_t)m * n1);
+    zc *T2 = (zc *)malloc(sizeof(zc) * (size_t)m * n2);
+    memcpy(T1, G1, sizeof(zc) * (size_t)m * n1);
+    memcpy(T2, G2, sizeof(zc) * (size_t)m * n2);
+    forward_subst(m, n1, L, T1);
+    forward_subst(m, n2, L, T2);
+    ctrans_prod(m, n1, n2, T1, T2, out);
+    free(T1);
+    free(T2);
+}
+
+/* G^H M^{-1} G = (L\G)^H (L\G), exactly Hermitian, for an m x m operand G. */
+static void chol_herk(int m, const zc *L, const zc *G, zc *out)
+{
+    zc *T = (zc *)malloc(sizeof(zc) * (size_t)m * m);
+    memcpy(T, G, sizeof(zc) * (size_t)m * m);
+    forward_subst(m, m, L, T);
+    herk_lower(m, T, out);
+    free(T);
+}
+
+static void ctranspose(int m, const zc *X, zc *out)
+{
+    for (int a = 0; a < m; ++a)
+        for (int b = 0; b < m; ++b) out[a * m + b] = conj(X[b * m + a]);
+}
+
+/* The Hermitian matrix that the lower triangle of X describes. */
+static void herm_lower(int m, const zc *X, zc *out)
+{
+    for (int a = 0; a < m; ++a) {
+        for (int b = 0; b < a; ++b) {
+            out[a * m + b] = X[a * m + b];
+            out[b * m + a] = conj(X[a * m + b]);
+        }
+        out[a * m + a] = creal(X[a * m + a]);
+    }
+}
+
+/*
+ * One split of Algorithm 1 on a system of n blocks (n even): Cholesky of
+ * every A_i (i = 1..n), then eq. Formulas for both halves.  Outputs U, V
+ * [n/2][m][m], E, F [n/2-1][m][m], u, v [n/2][m][k] (u, v only when y is
+ * given).  Returns 0 or the smallest failing 1-based block index i.
+ */
+int64_t oracle_alg1_split(int64_t n, int m, int k, const zc *A, const zc *B, const zc *y,
+                          zc *U, zc *E, zc *u, zc *V, zc *F, zc *v)
+{
+    const size_t mm = (size_t)m * m, mk = (size_t)m * k;
+    const int64_t h = n / 2;
+    int64_t fail = 0;
+    /* chol[i] = Cholesky factor of A_i, i = 0..n+1 (A_0 = A_{n+1} = I) */
+    zc *chol = (zc *)calloc((size_t)(n + 2) * mm, sizeof(zc));
+    for (int a = 0; a < m; ++a) {
+        chol[a * m + a] = 1.0;
+        chol[(size_t)(n + 1) * mm + a * m + a] = 1.0;
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 1; i <= n; ++i) {
+        if (chol_lower(m, A + (i - 1) * mm, chol + i * mm)) {
+#pragma omp critical
+            { if (fail == 0 || i < fail) fail = i; }
+        }
+    }
+    if (fail) { free(chol); return fail; }
+    zc *zero = (zc *)calloc(mm + mk, sizeof(zc)), *zeroy = zero + mm;
+    /* B_i for i = 0..n (B_0 = B_n = 0) and y_i for i = 0..n+1 (y_0 = y_{n+1} = 0:
+     * they only ever meet the zero couplings of the auxiliaries) */
+#define BLK(i) (((i) >= 1 && (i) <= n - 1) ? B + ((i) - 1) * mm : zero)
+#define YV(i) (((i) >= 1 && (i) <= n) ? y + ((i) - 1) * mk : zeroy)
+#define LF(i) (chol + (i) * mm)
+
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 1; j <= h; ++j) {
+        zc *t = (zc *)malloc(sizeof(zc) * mm), *g = (zc *)malloc(sizeof(zc) * mm);
+        zc *g2 = (zc *)malloc(sizeof(zc) * mm), *tk = (zc *)malloc(sizeof(zc) * (mk ? mk : 1));
+        /* odd system, row j (unknown x_{2j-1}) */
+        zc *Uj = U + (j - 1) * mm;
+        herm_lower(m, A + (2 * j - 2) * mm, Uj);
+        ctranspose(m, BLK(2 * j - 2), g);                 /* B_{2j-2} A_{2j-2}^{-1} B_{2j-2}^H */
+        chol_herk(m, LF(2 * j - 2), g, t);
+        sub_into((int64_t)mm, Uj, t);
+        chol_herk(m, LF(2 * j), BLK(2 * j - 1), t);       /* B_{2j-1}^H A_{2j}^{-1} B_{2j-1} */
+        sub_into((int64_t)mm, Uj, t);
+        if (j < h) {                                      /* E_j = -B_{2j} A_{2j}^{-1} B_{2j-1} */
+            zc *Ej = E + (j - 1) * mm;
+            ctranspose(m, BLK(2 * j), g);
+            chol_cross(m, m, m, LF(2 * j), g, BLK(2 * j - 1), Ej);
+            for (size_t e = 0; e < mm; ++e) Ej[e] = -Ej[e];
+        }
+        if (y) {
+            zc *uj = u + (j - 1) * mk;
+            memcpy(uj, YV(2 * j - 1), sizeof(zc) * mk);
+            ctranspose(m, BLK(2 * j - 2), g);             /* B_{2j-2} A_{2j-2}^{-1} y_{2j-2} */
+            chol_cross(m, m, k, LF(2 * j - 2), g, YV(2 * j - 2), tk);
+            sub_into((int64_t)mk, uj, tk);
+            chol_cross(m, m, k, LF(2 * j), BLK(2 * j - 1), YV(2 * j), tk); /* B_{2j-1}^H A_{2j}^{-1} y_{2j} */
+            sub_into((int64_t)mk, uj, tk);
+        }
+        /* even system, row j (unknown x_{2j}) */
+        zc *Vj = V + (j - 1) * mm;
+        herm_lower(m, A + (2 * j - 1) * mm, Vj);
+        ctranspose(m, BLK(2 * j - 1), g);                 /* B_{2j-1} A_{2j-1}^{-1} B_{2j-1}^H */
+        chol_herk(m, LF(2 * j - 1), g, t);
+        sub_into((int64_t)mm, Vj, t);
+        chol_herk(m, LF(2 * j + 1), BLK(2 * j), t);       /* B_{2j}^H A_{2j+1}^{-1} B_{2j} */
+        sub_into((int64_t)mm, Vj, t);
+        if (j < h) {                                      /* F_j = -B_{2j+1} A_{2j+1}^{-1} B_{2j} */
+            zc *Fj = F + (j - 1) * mm;
+            ctranspose(m, BLK(2 * j + 1), g2);
+            chol_cross(m, m, m, LF(2 * j + 1), g2, BLK(2 * j), Fj);
+            for (size_t e = 0; e < mm; ++e) Fj[e] = -Fj[e];
+        }
+        if (y) {
+            zc *vj = v + (j - 1) * mk;
+            memcpy(vj, YV(2 * j), sizeof(zc) * mk);
+            ctranspose(m, BLK(2 * j - 1), g);             /* B_{2j-1} A_{2j-1}^{-1} y_{2j-1} */
+            chol_cross(m, m, k, LF(2 * j - 1), g, YV(2 * j - 1), tk);
+            sub_into((int64_t)mk, vj, tk);
+            chol_cross(m, m, k, LF(2 * j + 1), BLK(2 * j), YV(2 * j + 1), tk); /* B_{2j}^H A_{2j+1}^{-1} y_{2j+1} */
+            sub_into((int64_t)mk, vj, tk);
+        }
+        free(t); free(g); free(g2); free(tk);
+    }
+#undef BLK
+#undef YV
+#undef LF
+    free(zero);
+    free(chol);
+    return 0;
+}
+
+typedef struct { int have; int32_t level; int64_t orig; } alg1_fail;
+
+static void alg1_note(alg1_fail *f, int32_t level, int64_t orig)
+{
+    if (!f->have || level < f->level || (level == f->level && orig < f->orig)) {
+        f->have = 1;
+        f->level = level;
+        f->orig = orig;
+    }
+}
+
+/* SOLVER of Algorithm 1 on a subsystem of n blocks whose block i (1-based)
+ * is block orig0 + (i-1) * stride + 1 of the original system. */
+static void alg1_solver(int64_t n, int m, int k, const zc *A, const zc *B, const zc *y, zc *x, int32_t depth,
+                        int64_t orig0, int64_t stride, alg1_fail *fail)
+{
+    const size_t mm = (size_t)m * m, mk = (size_t)m * k;
+    if (n == 1) {
+        zc *L = (zc *)malloc(sizeof(zc) * mm);
+        if (chol_lower(m, A, L)) {
+            alg1_note(fail, depth, orig0 + 1);
+        } else {
+            memcpy(x, y, sizeof(zc) * mk);
+            forward_subst(m, k, L, x);
+            backward_subst(m, k, L, x);
+        }
+        free(L);
+        return;
+    }
+    const int64_t h = n / 2;
+    zc *U = (zc *)malloc(sizeof(zc) * mm * h), *V = (zc *)malloc(sizeof(zc) * mm * h);
+    zc *E = (zc *)malloc(sizeof(zc) * mm * (h > 1 ? h - 1 : 1)), *F = (zc *)malloc(sizeof(zc) * mm * (h > 1 ? h - 1 : 1));
+    zc *u = (zc *)malloc(sizeof(zc) * mk * h), *v = (zc *)malloc(sizeof(zc) * mk * h);
+    zc *xo = (zc *)malloc(sizeof(zc) * mk * h), *xe = (zc *)malloc(sizeof(zc) * mk * h);
+    int64_t f = oracle_alg1_split(n, m, k, A, B, y, U, E, u, V, F, v);
+    if (f) {
+        /* report every failing block of this subsystem at this depth */
+        zc *L = (zc *)malloc(sizeof(zc) * mm);
+        for (int64_t i = 1; i <= n; ++i)
+            if (chol_lower(m, A + (i - 1) * mm, L)) alg1_note(fail, depth, orig0 + (i - 1) * stride + 1);
+        free(L);
+    } else {
+        alg1_solver(h, m, k, U, E, u, xo, depth + 1, orig0, 2 * stride, fail);          /* x_o */
+        alg1_solver(h, m, k, V, F, v, xe, depth + 1, orig0 + stride, 2 * stride, fail); /* x_e */
+        for (int64_t j = 1; j <= h; ++j) {
+            memcpy(x + (2 * j - 2) * mk, xo + (j - 1) * mk, sizeof(zc) * mk);
+            memcpy(x + (2 * j - 1) * mk, xe + (j - 1) * mk, sizeof(zc) * mk);
+        }
+    }
+    free(U); free(V); free(E); free(F); free(u); free(v); free(xo); free(xe);
+}
+
+/* Full solve by Algorithm 1 (N a power of two).  Returns 0 (x written),
+ * 1 (not positive definite; x filled with NaN) or -1 (N not a power of two).
+ * info->level is the recursion depth of the first breakdown (0 = the input
+ * system, log2 N = the single blocks); the recursion numbers blocks only
+ * within each subsystem, so info->block repeats orig_block. */
+int oracle_alg1_solve(int64_t N, int m, int k, const zc *A, const zc *B, const zc *y, zc *x, oracle_info *info)
+{
+    if (N < 1 || (N & (N - 1))) return -1;
+    alg1_fail fail = {0, 0, 0};
+    alg1_solver(N, m, k, A, B, y, x, 0, 0, 1, &fail);
+    if (fail.have)
+        for (int64_t e = 0; e < N * (int64_t)m * k; ++e) x[e] = CMPLX(NAN, NAN);
+    if (info) {
+        info->status = fail.have;
+        info->level = fail.have ? fail.level : 0;
+        info->block = fail.have ? fail.orig : 0;
+        info->orig_block = fail.have ? fail.orig : 0;
+    }
+    return fail.have;
 }
