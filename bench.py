@@ -15,7 +15,11 @@ Prints one JSON line (rank 0).  Extra keys:
   cpu_baseline  the CPU oracle on the host cores on a bounded sample
   clocks        nvidia-smi samples taken during the timed region
 
---impl reference times the CPU oracle alone (the reference arm).
+--workload selects another form: batched (4096 uneven systems in one
+persistent launch), adjoint (factor + solve + crsolve_backward), mixed (FP32
+levels with FP64 refinement at kappa 1e2/1e4/1e6) or alg1 (the paper's
+Algorithm 1 on the plain workload's system, with classic reduction timed
+beside it).  --impl reference times the CPU oracle alone (the reference arm).
 Under torchrun (N > 1) every rank solves its own independent system (weak
 scaling; the only collectives are the timing barrier and max).
 """
@@ -426,6 +430,180 @@ def run_mixed(args):
     print(json.dumps(line), flush=True)
 
 
+ALG1_WORKLOAD = ("Algorithm 1 (both halves reduced at every level, Sec. 3), one HPD block-tridiagonal system: "
+                 "N=2^20 blocks, m=8, k=4, complex128")
+
+
+def alg1_flops(N: int, m: int, k: int) -> float:
+    """Algorithmic flops of one factor + solve by Algorithm 1 with N = 2^L:
+    L split levels that each eliminate all N blocks (factor as for an odd
+    block of classic reduction; down sweep r = L^{-1} y m^2 k/2 and Z^H r
+    2 m^2 k), then N single-block Cholesky solves (m^3/6 + m^2 k)."""
+    L = N.bit_length() - 1
+    per_level = N * (flops_factor_per_odd_block(m) + 8.0 * 2.5 * m * m * k)
+    base = N * 8.0 * (m ** 3 / 6.0 + m * m * k)
+    return L * per_level + base
+
+
+def run_alg1(args):
+    """One step = crsolve_factor + crsolve_solve of an Algorithm 1 plan on the
+    plain workload's system (same generator and seed)."""
+    import torch
+    import paper_1807_00370_gb300 as crs
+    from paper_1807_00370_gb300 import _native as nat
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    N = 1 << args.log2n
+    L = args.log2n
+    workload = ALG1_WORKLOAD.replace("N=2^20", f"N=2^{args.log2n}")
+    A, B, y = synthetic.gen_system(N, M, K_RHS, seed=SEED + rank)
+    dA, dB, dy = (torch.from_numpy(a).to(dev) for a in (A, B, y))
+    plan = crs.Plan(N, M, K_RHS, flags=nat.CRSOLVE_PLAN_ALG1 | (0 if args.no_e2e else nat.CRSOLVE_PLAN_HOST_STAGING))
+    dx = torch.empty_like(dy)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        crs.crsolve_factor(plan, dA, dB)
+        crs.crsolve_solve(plan, dy, dx)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    info = crs.crsolve_info_get(plan)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(1.0)
+    launches0 = crs.crsolve_launch_count(plan)
+    crs.crsolve_timing_enable(plan, True)
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark(True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sampler.mark(False)
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    recs = crs.crsolve_timing_read(plan)
+    crs.crsolve_timing_enable(plan, False)
+    launches = crs.crsolve_launch_count(plan) - launches0
+    ms, total_units = reduce_over_ranks(ms, N * args.steps, dev)
+    ms_step = ms / args.steps
+    value = total_units / (ms * 1e-3)
+    by_kind = {}
+    for kind, level, units, kms in recs:
+        d = by_kind.setdefault(kind, {"ms": 0.0, "launches": 0})
+        d["ms"] += kms
+        d["launches"] += 1
+    # dominant kernel: k_factor_odd on the split levels (the single-block level
+    # is excluded: it only needs the Cholesky factors)
+    fac_ms = sum(kms for kind, level, units, kms in recs if kind == "factor_odd" and level < L)
+    fac_launches = sum(1 for kind, level, units, kms in recs if kind == "factor_odd" and level < L)
+    fac_flops = args.steps * L * N * flops_factor_per_odd_block(M)
+    peak_tf = FP64_PEAK_GFLOPS / 1e3
+    achieved = fac_flops / (fac_ms * 1e-3) / 1e12 if fac_ms else None
+    step_flops = alg1_flops(N, M, K_RHS)
+
+    # classic reduction on the same system and GPU, for the cost of the split
+    cplan = crs.Plan(N, M, K_RHS)
+    for _ in range(3):
+        crs.crsolve_factor(cplan, dA, dB)
+        crs.crsolve_solve(cplan, dy, dx)
+    torch.cuda.synchronize()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    c0.record(stream)
+    for _ in range(args.steps):
+        crs.crsolve_factor(cplan, dA, dB)
+        crs.crsolve_solve(cplan, dy, dx)
+    c1.record(stream)
+    torch.cuda.synchronize()
+    classic_ms = c0.elapsed_time(c1) / args.steps
+    cplan.close()
+    step()
+    torch.cuda.synchronize()
+
+    with torch.no_grad():
+        Ah = torch.tril(dA, -1)
+        Ah = Ah + Ah.conj().transpose(1, 2) + torch.diag_embed(torch.diagonal(dA, dim1=1, dim2=2).real.to(dA.dtype))
+        r = dy - torch.bmm(Ah, dx)
+        r[1:] -= torch.bmm(dB, dx[:-1])
+        r[:-1] -= torch.bmm(dB.conj().transpose(1, 2), dx[1:])
+        normA = (Ah.abs().sum(2).max() + 2 * dB.abs().sum(2).max()).item()
+        eta = (r.abs().amax() / (normA * dx.abs().amax())).item()
+
+    e2e = None
+    if not args.no_e2e:
+        tA, tB, ty = (torch.from_numpy(a).pin_memory() for a in (A, B, y))
+        tx = torch.empty_like(ty).pin_memory()
+        crs.crsolve_solve_host(plan, tA, tB, ty, tx)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            crs.crsolve_solve_host(plan, tA, tB, ty, tx)
+        el = time.perf_counter() - t0
+        e2e = {"value": N * args.e2e_steps / el * ws, "unit": "block-rows/s",
+               "h2d_bytes_per_step": int(tA.numel() + tB.numel() + ty.numel()) * 16,
+               "d2h_bytes_per_step": int(tx.numel()) * 16 + 8, "steps": args.e2e_steps}
+
+    cpu, sample_err = None, None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        n_sample = 1 << 14
+        sA, sB, sy = synthetic.gen_system(n_sample, M, K_RHS, seed=SEED)
+        sx, _ = oracle.alg1_solve(sA, sB, sy)
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            oracle.alg1_solve(sA, sB, sy)
+            reps += 1
+            el = time.perf_counter() - t0
+            if el >= 10.0:
+                break
+        cpu = {"value": n_sample * reps / el, "unit": "block-rows/s", "cores": oracle.max_threads(),
+               "kind": "oracle",
+               "sample": f"{reps} Algorithm 1 oracle solves of an N=2^14, m={M}, k={K_RHS} system, {el:.1f} s"}
+        xs = crs.solve(*(torch.from_numpy(a).to(dev) for a in (sA, sB, sy)), method="alg1").cpu().numpy()
+        sample_err = float(np.linalg.norm(xs - sx) / np.linalg.norm(sx))
+
+    if rank == 0:
+        line = {
+            "metric": "block-rows/s", "value": value, "unit": "block-rows/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
+            "data": "synthetic",
+            "config": {"workload": workload, "N": N, "m": M, "k": K_RHS, "seed": SEED,
+                       "l2": "inputs larger than L2 (A alone 1 GiB), no flush",
+                       "parallelism": f"{ws} independent system(s), one per GPU"},
+            "roofline": {"bound": "alu", "kernel": f"k_factor_odd<{M}>, split levels 0..{L - 1}",
+                         "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": (achieved / peak_tf) if achieved else None, "traffic": None,
+                         "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived)",
+                         "flops_per_unit": flops_factor_per_odd_block(M), "units": L * N,
+                         "launches_per_step": fac_launches // args.steps},
+            "step_roofline": {"flops_per_step": step_flops, "achieved": step_flops / (ms_step * 1e-3) / 1e12,
+                              "frac": step_flops / (ms_step * 1e-3) / 1e12 / peak_tf},
+            "vs_classic": {"classic_ms_per_step": classic_ms, "ratio": ms_step / classic_ms,
+                           "flop_ratio": step_flops / (N * flops_per_block_row(M, K_RHS))},
+            "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] // args.steps}
+                        for k, v in by_kind.items()},
+            "error": {"residual_eta": eta, "sample_rel_err_vs_oracle": sample_err, "bound": 1e-10},
+            "breakdown": info, "gpu_launches": launches, "clocks": clocks, "e2e": e2e, "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -435,7 +613,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "adjoint", "mixed"])
+    ap.add_argument("--workload", default="plain", choices=["plain", "batched", "adjoint", "mixed", "alg1"])
     ap.add_argument("--nsys", type=int, default=4096, help="systems of the batched workload")
     ap.add_argument("--log2n", type=int, default=20,
                     help="log2 of the block count (smaller cases are for profiling only)")
@@ -448,6 +626,8 @@ def main():
         return run_adjoint(args)
     if args.workload == "mixed":
         return run_mixed(args)
+    if args.workload == "alg1":
+        return run_alg1(args)
 
     import torch
     import paper_1807_00370_gb300 as crs

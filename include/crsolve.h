@@ -69,6 +69,25 @@ enum crsolve_precision {
 /* plan flags */
 #define CRSOLVE_PLAN_HOST_STAGING 1u  /* workspace also holds device copies of A, B, y, x
                                          for crsolve_solve_host */
+#define CRSOLVE_PLAN_ALG1 2u          /* the paper's own method, Algorithm 1 (Sec. 3) */
+
+/*
+ * Plans with CRSOLVE_PLAN_ALG1 run the paper's Algorithm 1 instead of classic
+ * reduction: every level splits each system into its odd half (U, E, u) and
+ * its even half (V, F, v) of eq. Formulas and recurses on both, down to
+ * single m x m blocks solved by Cholesky; there is no back-substitution.
+ * Level l holds 2^l systems of N/2^l blocks, so every level factors all N
+ * diagonal blocks (N log2 N block factorisations in total against N for
+ * classic reduction) and the workspace keeps log2 N + 1 levels of factors.
+ * N must be a power of two (Algorithm 1 assumes it) and precision
+ * CRSOLVE_FP64; otherwise crsolve_plan_create returns CRSOLVE_EUNSUPPORTED.
+ * crsolve_info: level = recursion depth of the first breakdown (log2 N = the
+ * single blocks), orig_block = the smallest failing original block at that
+ * depth, block = its 1-based position among the N blocks of that depth (the
+ * split systems in order, each split putting the odd half first).
+ * crsolve_factor, crsolve_solve, crsolve_backward and crsolve_solve_host work
+ * unchanged on such plans.
+ */
 
 /* Largest block size m and right-hand-side width k the kernels accept. */
 #define CRSOLVE_MAX_M 64
@@ -248,7 +267,9 @@ enum crsolve_kernel_kind {
     CRSOLVE_K_NANFILL = 6,         /* NaN fill of gA / gB after a breakdown */
     CRSOLVE_K_RESIDUAL = 7,        /* mixed precision: FP64 residual y - A x */
     CRSOLVE_K_CONVERT = 8,         /* mixed precision: FP64 <-> FP32 copies */
-    CRSOLVE_K_UPDATE = 9           /* mixed precision: x += d and norms */
+    CRSOLVE_K_UPDATE = 9,          /* mixed precision: x += d and norms */
+    CRSOLVE_K_ALG1_BORDER = 10,    /* Algorithm 1: auxiliary border blocks of the level buffers */
+    CRSOLVE_K_ALG1_MERGE = 11      /* Algorithm 1: merge of the two base solutions */
 };
 
 typedef struct {
@@ -301,7 +322,8 @@ int crsolve_tile_set(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc
 int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads,
                      int32_t *threads_solve);
 
-/* Number of levels of the plan (floor(log2 N) + 1) and the level sizes. */
+/* Number of levels of the plan (floor(log2 N) + 1) and the level sizes; with
+ * CRSOLVE_PLAN_ALG1, log2 N + 1 levels of N blocks each (2^l systems of N/2^l). */
 int crsolve_plan_levels(crsolve_plan p, int32_t *nlev, int64_t *sizes /* [nlev] or NULL */);
 
 /*

@@ -26,6 +26,7 @@ CRSOLVE_EUNSUPPORTED = -6
 CRSOLVE_FP64 = 0
 CRSOLVE_MIXED = 1
 CRSOLVE_PLAN_HOST_STAGING = 1
+CRSOLVE_PLAN_ALG1 = 2
 CRSOLVE_MAX_M = 64
 CRSOLVE_MAX_K = 4096
 
@@ -45,7 +46,8 @@ class CrsolveKernelTime(ctypes.Structure):
 
 
 KERNEL_KINDS = {0: "factor_odd", 1: "factor_fix", 2: "solve_down_odd", 3: "solve_down_fix",
-                4: "solve_up", 5: "adjoint_outer", 6: "nan_fill", 7: "residual", 8: "convert", 9: "update"}
+                4: "solve_up", 5: "adjoint_outer", 6: "nan_fill", 7: "residual", 8: "convert", 9: "update",
+                10: "alg1_border", 11: "alg1_merge"}
 
 SIGNATURES = {
     "crsolve_plan_create": (ctypes.c_int, [_I64, _I32, _I32, _I32, _U32, ctypes.POINTER(_P)]),

@@ -247,10 +247,23 @@ def crsolve_solve_noalloc(A: torch.Tensor, B: torch.Tensor | None, y: torch.Tens
     return x, {"status": info.status, "level": info.level, "block": info.block, "orig_block": info.orig_block}
 
 
-def solve(A: torch.Tensor, B: torch.Tensor | None, y: torch.Tensor, check: bool = True) -> torch.Tensor:
-    """x = A^{-1} y for one system on the tensors' CUDA device."""
+_METHOD_FLAGS = {"classic": 0, "alg1": nat.CRSOLVE_PLAN_ALG1}
+
+
+def _method_flags(method: str) -> int:
+    try:
+        return _METHOD_FLAGS[method]
+    except KeyError:
+        raise ValueError(f"method must be one of {sorted(_METHOD_FLAGS)}") from None
+
+
+def solve(A: torch.Tensor, B: torch.Tensor | None, y: torch.Tensor, check: bool = True,
+          method: str = "classic") -> torch.Tensor:
+    """x = A^{-1} y for one system on the tensors' CUDA device.  method:
+    "classic" (classic cyclic reduction, any N) or "alg1" (the paper's
+    Algorithm 1, both halves reduced, N a power of two)."""
     N, m, _ = A.shape
-    plan = Plan(N, m, y.shape[-1], device=A.device)
+    plan = Plan(N, m, y.shape[-1], flags=_method_flags(method), device=A.device)
     crsolve_factor(plan, A, B)
     x = crsolve_solve(plan, y)
     if check:
@@ -269,13 +282,15 @@ class CRSolveFn(torch.autograd.Function):
     keep_factors=False trades compute for memory: the forward pass frees its
     plan (the per-level factors and reduced systems) and keeps only A, B and
     x; the backward pass re-factors A to get the factors back.  The
-    re-factorisation is deterministic, so the gradients are identical."""
+    re-factorisation is deterministic, so the gradients are identical.
+    method selects the solver as in ``solve``."""
 
     @staticmethod
-    def forward(ctx, A, B, y, keep_factors: bool = True):
+    def forward(ctx, A, B, y, keep_factors: bool = True, method: str = "classic"):
         N, m, _ = A.shape
         A, B, y = A.contiguous(), None if B is None else B.contiguous(), y.contiguous()
-        plan = Plan(N, m, y.shape[-1], device=A.device)
+        ctx.flags = _method_flags(method)
+        plan = Plan(N, m, y.shape[-1], flags=ctx.flags, device=A.device)
         crsolve_factor(plan, A, B)
         x = crsolve_solve(plan, y)
         ctx.has_B = B is not None
@@ -297,8 +312,8 @@ class CRSolveFn(torch.autograd.Function):
         else:
             x, A, B = ctx.saved_tensors
             N, m, _ = A.shape
-            plan = Plan(N, m, x.shape[-1], device=A.device)
+            plan = Plan(N, m, x.shape[-1], flags=ctx.flags, device=A.device)
             crsolve_factor(plan, A, B if ctx.has_B else None)
         gy, gA, gB = crsolve_backward(plan, x, gx.contiguous(), ctx.needs_input_grad[0],
                                       ctx.needs_input_grad[1] and ctx.has_B)
-        return gA, gB, gy if ctx.needs_input_grad[2] else None, None
+        return gA, gB, gy if ctx.needs_input_grad[2] else None, None, None

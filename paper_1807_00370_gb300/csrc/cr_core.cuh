@@ -366,7 +366,7 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
                         d = fmx(-l.x, l.x, d);
                         d = fmx(-l.y, l.y, d);
                     }
-                    if (!(d > R(0))) report_fail(a.status, a.level, 2 * (t0 + b) + 1);
+                    if (!(d > R(0))) report_fail(a.status, a.level, report_index(a, 2 * (t0 + b)));
                     const R iv = rsq(d);
                     sInv[b * MT + c] = iv;
                     Lb[tri(c, c)] = zmk(d * iv, R(0));

@@ -110,7 +110,28 @@ struct LevelArgsT {
     C *x;               // [Nl][m][k]  level solution
     unsigned long long *status;
     int *err;           // nullable: set to 1 if a bounded device-side wait gave up
+    // Breakdown index map (see report_index): 0 for classic reduction; for the
+    // concatenated split systems of Algorithm 1, rep_bits = log2 N and rep_off
+    // the position of this reduction's block 0 in the level's concatenation.
+    int64_t rep_off;
+    int rep_bits;
 };
 using LevelArgs = LevelArgsT<double>;
+
+// 1-based block index that a breakdown of the level block at 0-based position
+// pos0 reports.  Classic reduction: the local index pos0 + 1.  Algorithm 1
+// (rep_bits = L = log2 N): level l holds the 2^l split systems of size N/2^l
+// one after another, each split putting the odd half before the even half, so
+// position p of the concatenation holds original block rotl^l(p) (rotation on
+// L bits); that original index is reported.
+template <class R>
+__device__ __forceinline__ int64_t report_index(const LevelArgsT<R> &a, int64_t pos0) {
+    if (a.rep_bits == 0) return pos0 + 1;
+    const int nb = a.rep_bits, s = a.level % nb;
+    const uint64_t mask = (1ull << nb) - 1;
+    const uint64_t u = (uint64_t)(pos0 + a.rep_off) & mask;
+    const uint64_t r = s ? (((u << s) | (u >> (nb - s))) & mask) : u;
+    return (int64_t)r + 1;
+}
 
 }  // namespace crs

@@ -61,6 +61,12 @@ cudaError_t launch_residual(int64_t N, int m, int k, const z2 *A, const z2 *B, c
 // Adjoint outer products gA, gB from x and gy.
 cudaError_t launch_adjoint_outer(int64_t N, int m, int k, const z2 *x, const z2 *gy, z2 *gA,
                                  z2 *gB, int nsm, cudaStream_t s);
+// Algorithm 1 driver: the fixed border blocks of the two level buffers
+// (A0[0] = A1[0] = I; B0, B1, B1mid = 0 where non-null), and the final merge of
+// the two base reductions' solutions (NaN after a breakdown).
+cudaError_t launch_alg1_border(z2 *A0, z2 *A1, z2 *B0, z2 *B1, z2 *B1mid, int m, cudaStream_t s);
+cudaError_t launch_alg1_merge(z2 *x, const z2 *xb, int64_t N, int64_t mk, const unsigned long long *status,
+                              int nsm, cudaStream_t s);
 // Fill n complex values with NaN if *status records a breakdown.
 cudaError_t launch_nan_if_failed(z2 *x, int64_t n, const unsigned long long *status, int nsm,
                                  cudaStream_t s);

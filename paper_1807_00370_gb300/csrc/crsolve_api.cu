@@ -54,6 +54,15 @@ struct crsolve_plan_s {
     bool fallback = false;                       // FP32 factor broke down: everything in FP64
     int last_iters = 0;
     double last_delta = 0.0, last_rho = 0.0;
+    // Algorithm 1 (CRSOLVE_PLAN_ALG1): levels 0..aL (aL = log2 N, the last
+    // one being the single blocks), two reductions per level: alev[0] reads
+    // the level buffer from block 1 (the concatenation of the split systems),
+    // alev[1] from block 0 (the same, behind the auxiliary block A_0 = I)
+    bool alg1 = false;
+    int aL = 0;
+    std::vector<LevelPlan> alev[2];
+    size_t offA1A[2] = {0, 0}, offA1B[2] = {0, 0}, offA1Y[2] = {0, 0}, offA1R[2] = {0, 0};
+    size_t offA1Xb = 0, offA1Xz = 0;
     // instrumentation
     bool timing = false;
     struct Rec { int kind, level; int64_t units; cudaEvent_t e0, e1; };
@@ -162,7 +171,142 @@ int launch(crsolve_plan_s *p, int kind, int level, int64_t units, cudaStream_t s
     return CRSOLVE_OK;
 }
 
+// ---- Algorithm 1 -----------------------------------------------------------
+//
+// Level l of Algorithm 1 (Sec. 3) holds 2^l split systems of n = N/2^l
+// blocks.  They are stored one after another as one block-tridiagonal system
+// of N blocks, with zero couplings across system boundaries, behind one
+// auxiliary block (A = I, B = 0, y = 0) at buffer position 0.  One level is
+// then two classic reductions of the same buffer:
+//   h = 0: from block 1 (the concatenation); it eliminates the odd blocks of
+//          every split system, and its even system is, block for block, the
+//          concatenation of their even halves (V, F, v of eq. Formulas);
+//   h = 1: from block 0 (the concatenation shifted by one); it eliminates the
+//          auxiliary block and the even blocks, and its even system is the
+//          concatenation of the odd halves (U, E, u).
+// A zero coupling stays exactly zero through a reduction (P = L^{-1} 0), so
+// the split systems stay decoupled.  The next level stores the odd halves at
+// positions 1..N/2 and the even halves at N/2+1..N, with the coupling between
+// them (position N/2 of the B buffer) zero.  Position p of level l therefore
+// holds original block rotl^l(p) (on log2 N bits), and after log2 N levels
+// the single blocks are back in the original order.  The last level (single
+// blocks, every coupling zero) is factored and solved by the same two
+// reductions, whose back-substitution then reduces to x = L^{-H} L^{-1} y.
+crs::LevelArgs alg1_args(const crsolve_plan_s *p, int l, int h) {
+    const LevelPlan &H = p->alev[h][l];
+    crs::LevelArgs a{};
+    a.Nl = H.Nl; a.no = H.no; a.ne = H.ne;
+    a.m = p->m; a.level = l;
+    const int64_t N = p->N, in0 = (h == 0) ? 1 : 0, out0 = (h == 0) ? 1 + N / 2 : 1;
+    const size_t mm = (size_t)p->m * p->m;
+    const int cur = l & 1, nxt = cur ^ 1;
+    char *ws = p->ws;
+    a.A = reinterpret_cast<const z2 *>(ws + p->offA1A[cur]) + in0 * mm;
+    a.B = reinterpret_cast<const z2 *>(ws + p->offA1B[cur]) + in0 * mm;
+    a.An = reinterpret_cast<z2 *>(ws + p->offA1A[nxt]) + out0 * mm;
+    a.Bn = reinterpret_cast<z2 *>(ws + p->offA1B[nxt]) + out0 * mm;
+    a.L = reinterpret_cast<z2 *>(ws + H.offL);
+    a.inv = reinterpret_cast<double *>(ws + H.offInv);
+    a.Z = reinterpret_cast<z2 *>(ws + H.offZ);
+    a.Wbd = reinterpret_cast<z2 *>(ws + p->offWbd);
+    a.r = reinterpret_cast<z2 *>(ws + p->offA1R[h]);
+    a.cbd = reinterpret_cast<z2 *>(ws + p->offCbd);
+    a.status = reinterpret_cast<unsigned long long *>(ws + p->offStatus);
+    a.rep_bits = p->aL;
+    a.rep_off = (h == 0) ? 0 : -1;
+    return a;
+}
+
+int alg1_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
+    const int64_t N = p->N;
+    const size_t mm = (size_t)p->m * p->m, zsz = sizeof(z2);
+    z2 *A0 = reinterpret_cast<z2 *>(p->ws + p->offA1A[0]), *A1 = reinterpret_cast<z2 *>(p->ws + p->offA1A[1]);
+    z2 *B0 = reinterpret_cast<z2 *>(p->ws + p->offA1B[0]), *B1 = reinterpret_cast<z2 *>(p->ws + p->offA1B[1]);
+    if (cudaMemsetAsync(p->ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess ||
+        cudaMemcpyAsync(A0 + mm, A, N * mm * zsz, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        (N > 1 && cudaMemcpyAsync(B0 + mm, B, (N - 1) * mm * zsz, cudaMemcpyDeviceToDevice, s) != cudaSuccess))
+        return CRSOLVE_ECUDA;
+    int rc;
+    if ((rc = launch(p, CRSOLVE_K_ALG1_BORDER, 0, 1, s, [&] {
+             return crs::launch_alg1_border(A0, A1, B0, B1, N > 1 ? B1 + (N / 2) * mm : nullptr, p->m, s);
+         })))
+        return rc;
+    for (int l = 0; l <= p->aL; ++l) {
+        for (int h = 1; h >= 0; --h) {
+            if (h == 1 && N < 2) continue;
+            crs::LevelArgs a = alg1_args(p, l, h);
+            a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
+            if ((rc = launch(p, CRSOLVE_K_FACTOR_ODD, l, a.no, s,
+                             [&] { return crs::launch_factor_odd(p->mt, a, s); })))
+                return rc;
+            if (crs::num_ctas(a.no, a.nb) > 1 &&
+                (rc = launch(p, CRSOLVE_K_FACTOR_FIX, l, crs::num_ctas(a.no, a.nb) - 1, s,
+                             [&] { return crs::launch_factor_fix(a, p->nsm, s); })))
+                return rc;
+        }
+        // buffer 0 held the caller's coupling at position N/2; from level 2 on it
+        // is the (zero) coupling between the odd and the even halves
+        if (l == 0 && p->aL >= 2 && cudaMemsetAsync(B0 + (N / 2) * mm, 0, mm * zsz, s) != cudaSuccess)
+            return CRSOLVE_ECUDA;
+    }
+    p->factored = true;
+    return CRSOLVE_OK;
+}
+
+int alg1_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
+    const int64_t N = p->N;
+    const size_t mk = (size_t)p->m * k, zsz = sizeof(z2);
+    z2 *Y[2] = {reinterpret_cast<z2 *>(p->ws + p->offA1Y[0]), reinterpret_cast<z2 *>(p->ws + p->offA1Y[1])};
+    z2 *Xb = reinterpret_cast<z2 *>(p->ws + p->offA1Xb), *Xz = reinterpret_cast<z2 *>(p->ws + p->offA1Xz);
+    if (cudaMemcpyAsync(Y[0] + mk, y, N * mk * zsz, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
+        cudaMemsetAsync(Y[0], 0, mk * zsz, s) != cudaSuccess || cudaMemsetAsync(Y[1], 0, mk * zsz, s) != cudaSuccess ||
+        cudaMemsetAsync(Xz, 0, (N / 2 + 1) * mk * zsz, s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    int rc;
+    for (int l = 0; l <= p->aL; ++l) {
+        const int cur = l & 1, nxt = cur ^ 1;
+        for (int h = 1; h >= 0; --h) {
+            if (h == 1 && N < 2) continue;
+            crs::LevelArgs a = alg1_args(p, l, h);
+            a.k = k;
+            a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
+            a.kc = crs::solve_kc(p->mt, k, a.no, p->nsm);
+            a.y = Y[cur] + ((h == 0) ? 1 : 0) * mk;
+            a.yn = Y[nxt] + ((h == 0) ? 1 + N / 2 : 1) * mk;
+            if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s,
+                             [&] { return crs::launch_solve_down_odd(p->mt, a, s); })))
+                return rc;
+            if (crs::num_ctas(a.no, a.nb) > 1 &&
+                (rc = launch(p, CRSOLVE_K_SOLVE_DOWN_FIX, l, crs::num_ctas(a.no, a.nb) - 1, s,
+                             [&] { return crs::launch_solve_down_fix(a, p->nsm, s); })))
+                return rc;
+        }
+    }
+    // single blocks: x = L^{-H} r of both reductions (zero even unknowns and
+    // couplings), from block 1 straight into x, the shifted one into Xb
+    for (int h = 0; h < 2; ++h) {
+        if (h == 1 && N < 2) continue;
+        crs::LevelArgs a = alg1_args(p, p->aL, h);
+        a.k = k;
+        a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
+        a.kc = crs::solve_kc(p->mt, k, a.no, p->nsm);
+        a.xn = Xz;
+        a.x = (h == 0) ? x : Xb;
+        if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, p->aL, a.no, s,
+                         [&] { return crs::launch_solve_up(p->mt, a, s); })))
+            return rc;
+    }
+    if (N >= 2 && (rc = launch(p, CRSOLVE_K_ALG1_MERGE, p->aL, N, s, [&] {
+                       return crs::launch_alg1_merge(x, Xb, N, (int64_t)mk,
+                                                     reinterpret_cast<const unsigned long long *>(p->ws + p->offStatus),
+                                                     p->nsm, s);
+                   })))
+        return rc;
+    return CRSOLVE_OK;
+}
+
 int do_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
+    if (p->alg1) return alg1_factor(p, A, B, s);
     if (cudaMemsetAsync(p->ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
         return CRSOLVE_ECUDA;
     int rc;
@@ -182,6 +326,7 @@ int do_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
 }
 
 int do_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
+    if (p->alg1) return alg1_solve(p, k, y, x, s);
     const int nlev = (int)p->lev.size();
     int rc;
     for (int l = 0; l < nlev; ++l) {
@@ -416,7 +561,9 @@ int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, u
     if (N < 1 || m < 1 || kmax < 1) return CRSOLVE_EINVAL;
     if (m > CRSOLVE_MAX_M || kmax > CRSOLVE_MAX_K) return CRSOLVE_EUNSUPPORTED;
     if (precision != CRSOLVE_FP64 && precision != CRSOLVE_MIXED) return CRSOLVE_EUNSUPPORTED;
-    if (flags & ~(uint32_t)CRSOLVE_PLAN_HOST_STAGING) return CRSOLVE_EINVAL;
+    if (flags & ~(uint32_t)(CRSOLVE_PLAN_HOST_STAGING | CRSOLVE_PLAN_ALG1)) return CRSOLVE_EINVAL;
+    const bool alg1 = (flags & CRSOLVE_PLAN_ALG1) != 0;
+    if (alg1 && ((N & (N - 1)) != 0 || precision != CRSOLVE_FP64)) return CRSOLVE_EUNSUPPORTED;
     crsolve_plan_s *p = new (std::nothrow) crsolve_plan_s();
     if (!p) return CRSOLVE_ENOMEM;
     p->N = N; p->m = m; p->kmax = kmax; p->precision = precision; p->flags = flags;
@@ -429,8 +576,36 @@ int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, u
     const size_t zsz = sizeof(crsolve_z), mm = (size_t)m * m, mk = (size_t)m * kmax;
     size_t cur = 0;
     p->offStatus = take(cur, 256);
+    p->alg1 = alg1;
+    if (alg1) {
+        int L = 0;
+        while ((int64_t(1) << L) < N) ++L;
+        p->aL = L;
+        for (int l = 0; l <= L; ++l)
+            for (int h = 0; h < 2; ++h) {
+                if (h == 1 && N < 2) continue;
+                LevelPlan H{};
+                H.Nl = N + h; H.no = (H.Nl + 1) / 2; H.ne = H.Nl / 2;
+                H.offL = take(cur, H.no * mm * zsz);
+                H.offInv = take(cur, H.no * (size_t)m * sizeof(double));
+                H.offZ = take(cur, H.no * 2 * mm * zsz);
+                p->alev[h].push_back(H);
+            }
+        const int64_t noB = N / 2 + 1;
+        for (int b = 0; b < 2; ++b) {
+            p->offA1A[b] = take(cur, (N + 1) * mm * zsz);
+            p->offA1B[b] = take(cur, N * mm * zsz);
+            p->offA1Y[b] = take(cur, (N + 1) * mk * zsz);
+        }
+        p->offA1R[0] = take(cur, ((N + 1) / 2) * mk * zsz);
+        p->offA1R[1] = take(cur, noB * mk * zsz);
+        p->offA1Xb = take(cur, (N + 1) * mk * zsz);
+        p->offA1Xz = take(cur, noB * mk * zsz);
+        p->offWbd = take(cur, noB * mm * zsz);
+        p->offCbd = take(cur, noB * mk * zsz);
+    }
     int64_t Nl = N;
-    while (true) {
+    while (!alg1) {
         LevelPlan L{};
         L.Nl = Nl; L.no = (Nl + 1) / 2; L.ne = Nl / 2;
         L.offL = take(cur, L.no * mm * zsz);
@@ -448,8 +623,10 @@ int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, u
     const int64_t no0 = (N + 1) / 2;
     // CTA-boundary scratch: at most one m x m (factor) and one m x kmax (solve)
     // per CTA of the largest level
-    p->offWbd = take(cur, no0 * mm * zsz);
-    p->offCbd = take(cur, no0 * mk * zsz);
+    if (!alg1) {
+        p->offWbd = take(cur, no0 * mm * zsz);
+        p->offCbd = take(cur, no0 * mk * zsz);
+    }
     if (flags & CRSOLVE_PLAN_HOST_STAGING) {
         p->offSA = take(cur, N * mm * zsz);
         p->offSB = take(cur, (N - 1) * mm * zsz);
@@ -613,8 +790,17 @@ int crsolve_info_get(crsolve_plan p, crsolve_info *out, void *stream) {
         *out = crsolve_info{CRSOLVE_OK, 0, 0, 0};
     } else {
         const int level = (int)(st >> 40);
-        const int64_t block = (int64_t)(st & ((1ull << 40) - 1));
-        *out = crsolve_info{CRSOLVE_NOT_PD, level, block, block << level};
+        const int64_t idx = (int64_t)(st & ((1ull << 40) - 1));
+        if (p->alg1) {
+            // the kernels report the original block; its position at that
+            // level is rotr^level on log2 N bits
+            const int L = p->aL, sh = L ? level % L : 0;
+            const uint64_t mask = L ? ((1ull << L) - 1) : 0, u = (uint64_t)(idx - 1) & mask;
+            const uint64_t pos = sh ? (((u >> sh) | (u << (L - sh))) & mask) : u;
+            *out = crsolve_info{CRSOLVE_NOT_PD, level, (int64_t)pos + 1, idx};
+        } else {
+            *out = crsolve_info{CRSOLVE_NOT_PD, level, idx, idx << level};
+        }
     }
     return CRSOLVE_OK;
 }
@@ -703,6 +889,13 @@ int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t 
 
 int crsolve_plan_levels(crsolve_plan p, int32_t *nlev, int64_t *sizes) {
     if (!p || !nlev) return CRSOLVE_EINVAL;
+    if (p->alg1) {
+        // every level of Algorithm 1 holds all N blocks (2^l systems of N/2^l)
+        *nlev = p->aL + 1;
+        if (sizes)
+            for (int l = 0; l <= p->aL; ++l) sizes[l] = p->N;
+        return CRSOLVE_OK;
+    }
     *nlev = (int32_t)p->lev.size();
     if (sizes)
         for (size_t l = 0; l < p->lev.size(); ++l) sizes[l] = p->lev[l].Nl;

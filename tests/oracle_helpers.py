@@ -37,3 +37,40 @@ def eta_inf(A, B, x, y):
     R = y.reshape(N * m, k) - D @ X
     nA = np.abs(D).sum(axis=1).max()
     return max(np.abs(R[:, c]).max() / (nA * np.abs(X[:, c]).max()) for c in range(k))
+
+
+def dense_schur(D, keep, m):
+    """Schur complement of the dense matrix D onto the block rows `keep`;
+    returns (S, kept scalar rows, eliminated scalar rows)."""
+    rows = np.concatenate([np.arange(b * m, (b + 1) * m) for b in keep])
+    rest = np.setdiff1d(np.arange(D.shape[0]), rows)
+    S = D[np.ix_(rows, rows)]
+    if rest.size:
+        S = S - D[np.ix_(rows, rest)] @ np.linalg.solve(D[np.ix_(rest, rest)], D[np.ix_(rest, rows)])
+    return S, rows, rest
+
+
+def brute_force_first_failure(A, B, margin):
+    """For Algorithm 1 on N = 2^L blocks: the first (depth, 1-based original
+    block) whose diagonal block, in the dense Schur complement of the whole
+    matrix onto its residue class i = s (mod 2^depth), is not positive
+    definite (the split system at that depth that holds those unknowns is
+    exactly that Schur complement).  None if every block passes; ValueError
+    if some block is within `margin` of singular (too close to call)."""
+    N, m, _ = A.shape
+    D = assemble(A, B)
+    L = N.bit_length() - 1
+    for d in range(L + 1):
+        fails = []
+        for s0 in range(1 << d):
+            keep = np.arange(s0, N, 1 << d)
+            S, _, _ = dense_schur(D, keep, m)
+            for j, b in enumerate(keep):
+                lam = np.linalg.eigvalsh(S[j * m:(j + 1) * m, j * m:(j + 1) * m]).min()
+                if abs(lam) < margin:
+                    raise ValueError("too close to call")
+                if lam < 0:
+                    fails.append(int(b) + 1)
+        if fails:
+            return d, min(fails)
+    return None

@@ -53,7 +53,10 @@ def _create(N, m, k, prec=0, flags=0):
     (8, 65, 1, 0, 0, nat.CRSOLVE_EUNSUPPORTED),
     (8, 4, 5000, 0, 0, nat.CRSOLVE_EUNSUPPORTED),
     (8, 4, 1, 7, 0, nat.CRSOLVE_EUNSUPPORTED),
-    (8, 4, 1, 0, 2, nat.CRSOLVE_EINVAL),
+    (8, 4, 1, 0, 4, nat.CRSOLVE_EINVAL),
+    # Algorithm 1 needs N a power of two and FP64
+    (6, 4, 1, 0, nat.CRSOLVE_PLAN_ALG1, nat.CRSOLVE_EUNSUPPORTED),
+    (8, 4, 1, nat.CRSOLVE_MIXED, nat.CRSOLVE_PLAN_ALG1, nat.CRSOLVE_EUNSUPPORTED),
 ])
 def test_plan_argument_errors_are_host_side(N, m, k, prec, flags, code):
     rc, h = _create(N, m, k, prec, flags)

@@ -17,7 +17,8 @@ import pytest
 
 import oracle
 import synthetic
-from tests.oracle_helpers import assemble, dense_solve, eta_inf, herm_from_lower, rel_err
+from tests.oracle_helpers import (assemble, brute_force_first_failure, dense_schur, dense_solve, eta_inf,
+                                  herm_from_lower, rel_err)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -47,16 +48,6 @@ def test_hand_worked_split_n2_m1():
     assert abs(x[0, 0, 0] - g["x1"]) <= 1e-15 and abs(x[1, 0, 0] - g["x2"]) <= 1e-15
 
 
-def _dense_schur(D, keep, m):
-    """Schur complement of the dense matrix D onto the block rows `keep`."""
-    rows = np.concatenate([np.arange(b * m, (b + 1) * m) for b in keep])
-    rest = np.setdiff1d(np.arange(D.shape[0]), rows)
-    S = D[np.ix_(rows, rows)]
-    if rest.size:
-        S = S - D[np.ix_(rows, rest)] @ np.linalg.solve(D[np.ix_(rest, rest)], D[np.ix_(rest, rows)])
-    return S, rows, rest
-
-
 @pytest.mark.parametrize("N", [2, 4, 8, 16])
 @pytest.mark.parametrize("m,k", [(1, 1), (3, 2), (5, 3)])
 def test_split_equals_dense_schur_complements(N, m, k):
@@ -72,7 +63,7 @@ def test_split_equals_dense_schur_complements(N, m, k):
     h = N // 2
     for half, (Dg, Sb, rhs) in {0: ("U", "E", "u"), 1: ("V", "F", "v")}.items():
         keep = np.arange(half, N, 2)
-        S, rows, rest = _dense_schur(D, keep, m)
+        S, rows, rest = dense_schur(D, keep, m)
         Yr = Y[rows] - (D[np.ix_(rows, rest)] @ np.linalg.solve(D[np.ix_(rest, rest)], Y[rest]))
         scale = np.abs(S).max()
         for j in range(h):
@@ -166,30 +157,6 @@ def test_split_systems_are_bitwise_hermitian_and_positive_definite():
     assert depth == 5 and len(todo) == 32
 
 
-def _brute_force_first_failure(A, B, margin):
-    """First (depth, original block) whose diagonal block, in the dense Schur
-    complement onto its residue class, is not positive definite.  Returns
-    None if every block passes; raises if a block is within `margin` of
-    singular (the case is then too close to call)."""
-    N, m, _ = A.shape
-    D = assemble(A, B)
-    L = N.bit_length() - 1
-    for d in range(L + 1):
-        fails = []
-        for s0 in range(1 << d):
-            keep = np.arange(s0, N, 1 << d)
-            S, _, _ = _dense_schur(D, keep, m)
-            for j, b in enumerate(keep):
-                lam = np.linalg.eigvalsh(S[j * m:(j + 1) * m, j * m:(j + 1) * m]).min()
-                if abs(lam) < margin:
-                    raise ValueError("too close to call")
-                if lam < 0:
-                    fails.append(int(b) + 1)
-        if fails:
-            return d, min(fails)
-    return None
-
-
 def test_breakdown_iff_not_positive_definite_and_its_location():
     """Sec. 2 "Determination of Positive Definiteness": the recursion breaks
     down exactly when the matrix is not positive definite, and it does so at
@@ -214,7 +181,7 @@ def test_breakdown_iff_not_positive_definite_and_its_location():
         if abs(lmin) < 1e-6 * lam.max():
             continue
         try:
-            expect = _brute_force_first_failure(A, B, 1e-9 * lam.max())
+            expect = brute_force_first_failure(A, B, 1e-9 * lam.max())
         except ValueError:
             continue
         _, info = oracle.alg1_solve(A, B, y)
