@@ -160,6 +160,11 @@ int crsolve_backward(crsolve_plan p, int32_t k, const crsolve_z *x, const crsolv
  * crsolve_solve_host -- factor and solve with HOST buffers: copies A, B, y
  * from host memory (pinned for full speed) into the plan's staging area,
  * factors, solves, copies x back to host memory and synchronises the stream.
+ * For classic plans with N > 1 the copies run on a second stream owned by the
+ * plan and overlap the level-0 kernels: the level-0 factor starts range by
+ * range as the rows of A and B it reads arrive, y is copied while the coarse
+ * levels are factored, and x is copied back range by range behind the level-0
+ * up sweep.  x is bit-identical to crsolve_factor + crsolve_solve.
  * Needs a plan created with CRSOLVE_PLAN_HOST_STAGING.  Returns CRSOLVE_OK or
  * CRSOLVE_NOT_PD (then x holds NaN), or a negative error.
  */
@@ -296,8 +301,11 @@ int crsolve_timing_read(crsolve_plan p, crsolve_kernel_time *out, int32_t cap, i
  * mode crsolve_factor and crsolve_solve synchronise the stream, and A and B
  * must stay valid and unchanged until the plan is re-factored or destroyed
  * (the residual reads them).  A breakdown in the FP32 levels is re-decided by
- * an FP64 factorisation, and refinement that does not contract falls back to
- * the FP64 path, so the flags are always the FP64 ones.
+ * an FP64 factorisation, so the flags are always the FP64 ones.  Refinement
+ * hands over to the FP64 path (factor + solve) when it does not contract, or
+ * when the steps still needed at the observed contraction rate would cost more
+ * than that path (each step: one FP64 residual and one FP32 correction sweep);
+ * the handover comes after the first or second residual.
  * crsolve_mixed_stats reports the last solve: FP64 residuals computed,
  * delta = |last correction|_inf / |x|_inf, rho = observed contraction per
  * refinement step, and whether the FP64 path was used instead.

@@ -115,6 +115,11 @@ struct LevelArgsT {
     // the position of this reduction's block 0 in the level's concatenation.
     int64_t rep_off;
     int rep_bits;
+    // Chunk range of one launch of the odd-block kernels: chunks c_begin ..
+    // c_begin + c_count - 1 (c_count = 0: every chunk of the level).  A level
+    // may be run as several such launches, e.g. each as soon as the input
+    // rows it reads have arrived from the host.
+    int64_t c_begin, c_count;
 };
 using LevelArgs = LevelArgsT<double>;
 

@@ -9,7 +9,7 @@ namespace crs {
 template <int MT, class R>
 __global__ void __launch_bounds__(256) k_factor_odd(LevelArgsT<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    factor_chunk<MT, R>(a, blockIdx.x, smem_raw);
+    factor_chunk<MT, R>(a, a.c_begin + blockIdx.x, smem_raw);
 }
 
 template <class R>
@@ -20,7 +20,7 @@ __global__ void __launch_bounds__(256) k_factor_fix(LevelArgsT<R> a) {
 template <int MT, class R>
 __global__ void __launch_bounds__(256) k_solve_down_odd(LevelArgsT<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    solve_down_chunk<MT, R>(a, blockIdx.x, blockIdx.y, smem_raw);
+    solve_down_chunk<MT, R>(a, a.c_begin + blockIdx.x, blockIdx.y, smem_raw);
 }
 
 template <class R>
@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(256) k_solve_down_fix(LevelArgsT<R> a) {
 template <int MT, class R>
 __global__ void __launch_bounds__(256) k_solve_up(LevelArgsT<R> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    solve_up_chunk<MT, R>(a, blockIdx.x, blockIdx.y, smem_raw);
+    solve_up_chunk<MT, R>(a, a.c_begin + blockIdx.x, blockIdx.y, smem_raw);
 }
 
 // ------------------------------------------------------------------ adjoint
@@ -227,6 +227,12 @@ int solve_kc32(int mt, int k, int64_t no, int nsm) {
     return spread_kc(tile_shape32(mt).kc_max, k, num_ctas(no, solve_nb32(mt, no, nsm)), nsm);
 }
 
+// CTAs of one launch of an odd-block kernel: the chunk range, else the level.
+template <class R>
+static unsigned odd_grid(const LevelArgsT<R> &a) {
+    return (unsigned)(a.c_count > 0 ? a.c_count : num_ctas(a.no, a.nb));
+}
+
 static unsigned grid_1d(int64_t items, int nsm) {
     int64_t g = (items + 255) / 256;
     const int64_t cap = (int64_t)nsm * 16;
@@ -237,7 +243,7 @@ static unsigned grid_1d(int64_t items, int nsm) {
 
 template <int MT, class R>
 static cudaError_t factor_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
-    const unsigned grid = (unsigned)num_ctas(a.no, a.nb);
+    const unsigned grid = odd_grid(a);
     const int th = sizeof(R) == 4 ? tile_shape32(MT).threads : tile_shape(MT).threads;
     k_factor_odd<MT, R><<<grid, th, factor_smem_bytes(MT, a.nb, sizeof(R)), s>>>(a);
     return cudaGetLastError();
@@ -245,7 +251,7 @@ static cudaError_t factor_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
 
 template <int MT, class R>
 static cudaError_t solve_down_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
-    const dim3 grid((unsigned)num_ctas(a.no, a.nb), (unsigned)((a.k + a.kc - 1) / a.kc));
+    const dim3 grid(odd_grid(a), (unsigned)((a.k + a.kc - 1) / a.kc));
     const int th = sizeof(R) == 4 ? tile_shape32(MT).threads_solve : tile_shape(MT).threads_solve;
     k_solve_down_odd<MT, R><<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
     return cudaGetLastError();
@@ -253,7 +259,7 @@ static cudaError_t solve_down_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
 
 template <int MT, class R>
 static cudaError_t solve_up_mt(const LevelArgsT<R> &a, cudaStream_t s) {
-    const dim3 grid((unsigned)num_ctas(a.no, a.nb), (unsigned)((a.k + a.kc - 1) / a.kc));
+    const dim3 grid(odd_grid(a), (unsigned)((a.k + a.kc - 1) / a.kc));
     const int th = sizeof(R) == 4 ? tile_shape32(MT).threads_solve : tile_shape(MT).threads_solve;
     k_solve_up<MT, R><<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
     return cudaGetLastError();

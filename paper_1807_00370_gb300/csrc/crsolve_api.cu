@@ -6,6 +6,7 @@
 // blocks (the next level).  Every block row of the original system is an odd
 // block at exactly one level, so the factorisation does N block Cholesky
 // factorisations in total.
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <new>
@@ -63,6 +64,9 @@ struct crsolve_plan_s {
     std::vector<LevelPlan> alev[2];
     size_t offA1A[2] = {0, 0}, offA1B[2] = {0, 0}, offA1Y[2] = {0, 0}, offA1R[2] = {0, 0};
     size_t offA1Xb = 0, offA1Xz = 0;
+    // crsolve_solve_host: a copy stream (created on first use) and its events
+    cudaStream_t cstream = nullptr;
+    std::vector<cudaEvent_t> xev;
     // instrumentation
     bool timing = false;
     struct Rec { int kind, level; int64_t units; cudaEvent_t e0, e1; };
@@ -305,12 +309,10 @@ int alg1_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     return CRSOLVE_OK;
 }
 
-int do_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
-    if (p->alg1) return alg1_factor(p, A, B, s);
-    if (cudaMemsetAsync(p->ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
-        return CRSOLVE_ECUDA;
+// Factor levels [l0, nlev): odd-block kernel and CTA-boundary fix-up per level.
+int factor_levels(crsolve_plan_s *p, int l0, const z2 *A, const z2 *B, cudaStream_t s) {
     int rc;
-    for (int l = 0; l < (int)p->lev.size(); ++l) {
+    for (int l = l0; l < (int)p->lev.size(); ++l) {
         crs::LevelArgs a = level_args(p, l, A, B);
         a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
         if ((rc = launch(p, CRSOLVE_K_FACTOR_ODD, l, a.no, s,
@@ -321,19 +323,33 @@ int do_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
                          [&] { return crs::launch_factor_fix(a, p->nsm, s); })))
             return rc;
     }
+    return CRSOLVE_OK;
+}
+
+int do_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
+    if (p->alg1) return alg1_factor(p, A, B, s);
+    if (cudaMemsetAsync(p->ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    int rc;
+    if ((rc = factor_levels(p, 0, A, B, s))) return rc;
     p->factored = true;
     return CRSOLVE_OK;
 }
 
-int do_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
-    if (p->alg1) return alg1_solve(p, k, y, x, s);
+crs::LevelArgs solve_args(const crsolve_plan_s *p, int l, int k) {
+    crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
+    a.k = k;
+    a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
+    a.kc = crs::solve_kc(p->mt, k, a.no, p->nsm);
+    return a;
+}
+
+// Down sweep of every level, then the up sweep of levels nlev-1 .. l_end.
+int solve_sweeps(crsolve_plan_s *p, int k, const z2 *y, z2 *x, int l_end, cudaStream_t s) {
     const int nlev = (int)p->lev.size();
     int rc;
     for (int l = 0; l < nlev; ++l) {
-        crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
-        a.k = k;
-        a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
-        a.kc = crs::solve_kc(p->mt, k, a.no, p->nsm);
+        crs::LevelArgs a = solve_args(p, l, k);
         a.y = (l == 0) ? y : reinterpret_cast<const z2 *>(p->ws + p->lev[l - 1].offYn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s,
                          [&] { return crs::launch_solve_down_odd(p->mt, a, s); })))
@@ -343,16 +359,130 @@ int do_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
                          [&] { return crs::launch_solve_down_fix(a, p->nsm, s); })))
             return rc;
     }
-    for (int l = nlev - 1; l >= 0; --l) {
-        crs::LevelArgs a = level_args(p, l, nullptr, nullptr);
-        a.k = k;
-        a.nb = crs::solve_nb(p->mt, a.no, p->nsm);
-        a.kc = crs::solve_kc(p->mt, k, a.no, p->nsm);
+    for (int l = nlev - 1; l >= l_end; --l) {
+        crs::LevelArgs a = solve_args(p, l, k);
         a.x = (l == 0) ? x : reinterpret_cast<z2 *>(p->ws + p->lev[l - 1].offXn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, l, a.no, s,
                          [&] { return crs::launch_solve_up(p->mt, a, s); })))
             return rc;
     }
+    return CRSOLVE_OK;
+}
+
+int do_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
+    if (p->alg1) return alg1_solve(p, k, y, x, s);
+    return solve_sweeps(p, k, y, x, 0, s);
+}
+
+// ---- host buffers: copies overlapped with the level-0 kernels --------------
+//
+// crsolve_solve_host on a classic FP64 plan.  A level-0 chunk of odd blocks
+// t0 .. t1-1 reads block rows 2 t0 - 1 .. 2 t1 - 1 of A and B and writes rows
+// 2 t0 .. 2 t1 - 1 of x, so level 0 is run as G chunk ranges: on a copy
+// stream the rows of A and B are sent range by range (in row order, so the
+// one row a range needs from its left neighbour has arrived before it), and
+// the factor kernel of range g starts as soon as its rows are on the device;
+// y follows while the coarse levels are factored; after the down sweep and
+// the coarse up sweeps, x of range g goes back to the host while the next
+// range of the level-0 up sweep still runs.  Every kernel does exactly the
+// work of crsolve_factor + crsolve_solve, so x is bit-identical to theirs.
+constexpr int kHostRanges = 8;
+
+cudaEvent_t host_event(crsolve_plan_s *p, size_t i) {
+    while (p->xev.size() <= i) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return nullptr;
+        p->xev.push_back(e);
+    }
+    return p->xev[i];
+}
+
+// Chunk range g of G over n chunks: [n g / G, n (g+1) / G).
+int64_t range_edge(int64_t n, int g, int G) { return n * g / G; }
+
+int solve_host_pipelined(crsolve_plan_s *p, int k, const crsolve_z *A_host, const crsolve_z *B_host,
+                         const crsolve_z *y_host, crsolve_z *x_host, cudaStream_t s) {
+    const int64_t N = p->N;
+    const size_t zsz = sizeof(crsolve_z), mm = (size_t)p->m * p->m, mk = (size_t)p->m * k;
+    z2 *dA = reinterpret_cast<z2 *>(p->ws + p->offSA), *dB = reinterpret_cast<z2 *>(p->ws + p->offSB);
+    z2 *dy = reinterpret_cast<z2 *>(p->ws + p->offSY), *dx = reinterpret_cast<z2 *>(p->ws + p->offSX);
+    if (!p->cstream && cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking) != cudaSuccess) {
+        p->cstream = nullptr;
+        return CRSOLVE_ECUDA;
+    }
+    cudaStream_t cs = p->cstream;
+    size_t ne = 0;
+    // the copy stream starts after everything already queued on s
+    cudaEvent_t e = host_event(p, ne++);
+    if (!e || cudaEventRecord(e, s) != cudaSuccess || cudaStreamWaitEvent(cs, e, 0) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    if (cudaMemsetAsync(p->ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    int rc;
+    // level-0 factor by ranges of chunks, each after its rows of A and B
+    {
+        crs::LevelArgs a = level_args(p, 0, dA, dB);
+        a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
+        const int64_t nc = crs::num_ctas(a.no, a.nb);
+        const int G = (int)(nc < kHostRanges ? nc : kHostRanges);
+        for (int g = 0; g < G; ++g) {
+            const int64_t c0 = range_edge(nc, g, G), c1 = range_edge(nc, g + 1, G);
+            const int64_t r0 = 2 * c0 * a.nb, r1 = (g == G - 1) ? N : 2 * c1 * a.nb;
+            const int64_t b1 = r1 < N - 1 ? r1 : N - 1;
+            if (cudaMemcpyAsync(dA + r0 * mm, A_host + r0 * mm, (r1 - r0) * mm * zsz, cudaMemcpyHostToDevice, cs) !=
+                cudaSuccess)
+                return CRSOLVE_ECUDA;
+            if (b1 > r0 && cudaMemcpyAsync(dB + r0 * mm, B_host + r0 * mm, (b1 - r0) * mm * zsz,
+                                           cudaMemcpyHostToDevice, cs) != cudaSuccess)
+                return CRSOLVE_ECUDA;
+            e = host_event(p, ne++);
+            if (!e || cudaEventRecord(e, cs) != cudaSuccess || cudaStreamWaitEvent(s, e, 0) != cudaSuccess)
+                return CRSOLVE_ECUDA;
+            a.c_begin = c0;
+            a.c_count = c1 - c0;
+            const int64_t units = (c1 * a.nb < a.no ? c1 * a.nb : a.no) - c0 * a.nb;
+            if ((rc = launch(p, CRSOLVE_K_FACTOR_ODD, 0, units, s, [&] { return crs::launch_factor_odd(p->mt, a, s); })))
+                return rc;
+        }
+        a.c_begin = a.c_count = 0;
+        if (nc > 1 && (rc = launch(p, CRSOLVE_K_FACTOR_FIX, 0, nc - 1, s,
+                                   [&] { return crs::launch_factor_fix(a, p->nsm, s); })))
+            return rc;
+    }
+    // y while the coarse levels are factored
+    if (cudaMemcpyAsync(dy, y_host, N * mk * zsz, cudaMemcpyHostToDevice, cs) != cudaSuccess) return CRSOLVE_ECUDA;
+    cudaEvent_t ey = host_event(p, ne++);
+    if (!ey || cudaEventRecord(ey, cs) != cudaSuccess) return CRSOLVE_ECUDA;
+    if ((rc = factor_levels(p, 1, nullptr, nullptr, s))) return rc;
+    p->factored = true;
+    if (cudaStreamWaitEvent(s, ey, 0) != cudaSuccess) return CRSOLVE_ECUDA;
+    if ((rc = solve_sweeps(p, k, dy, dx, 1, s))) return rc;
+    // level-0 up sweep by ranges, each range's x sent back behind it
+    {
+        crs::LevelArgs a = solve_args(p, 0, k);
+        a.x = dx;
+        const int64_t nc = crs::num_ctas(a.no, a.nb);
+        const int G = (int)(nc < kHostRanges ? nc : kHostRanges);
+        for (int g = 0; g < G; ++g) {
+            const int64_t c0 = range_edge(nc, g, G), c1 = range_edge(nc, g + 1, G);
+            const int64_t r0 = 2 * c0 * a.nb, r1 = (g == G - 1) ? N : 2 * c1 * a.nb;
+            a.c_begin = c0;
+            a.c_count = c1 - c0;
+            const int64_t units = (c1 * a.nb < a.no ? c1 * a.nb : a.no) - c0 * a.nb;
+            if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, 0, units, s, [&] { return crs::launch_solve_up(p->mt, a, s); })))
+                return rc;
+            e = host_event(p, ne++);
+            if (!e || cudaEventRecord(e, s) != cudaSuccess || cudaStreamWaitEvent(cs, e, 0) != cudaSuccess)
+                return CRSOLVE_ECUDA;
+            if (cudaMemcpyAsync(x_host + r0 * mk, dx + r0 * mk, (r1 - r0) * mk * zsz, cudaMemcpyDeviceToHost, cs) !=
+                cudaSuccess)
+                return CRSOLVE_ECUDA;
+        }
+    }
+    // s resumes after the last copy
+    e = host_event(p, ne++);
+    if (!e || cudaEventRecord(e, cs) != cudaSuccess || cudaStreamWaitEvent(s, e, 0) != cudaSuccess)
+        return CRSOLVE_ECUDA;
     return CRSOLVE_OK;
 }
 
@@ -498,8 +628,21 @@ int mixed_correction(crsolve_plan_s *p, int k, const z2 *r, cudaStream_t s) {
 // x_{i+1} = x_i + A~^{-1} r_i.  With delta_i = |d_i|_inf / |x_{i+1}|_inf and
 // rho = delta_i / delta_{i-1} (the observed contraction), the error of
 // x_{i+1} is about rho * delta_i; stop when that is below 1e-13 (or delta_i
-// is at FP64 resolution).  No contraction (rho > 0.5 twice) switches to the
-// FP64 path.
+// is at FP64 resolution).  The FP64 path takes over when refinement cannot
+// pay: no contraction (rho > 0.5 twice, or rho >= 1), or more steps predicted
+// at the observed rate (delta shrinking by rho per step) than the FP64
+// factor + solve would cost (mixed_step_cost).
+//
+// Cost of one refinement step relative to an FP64 factor + solve, in FP64
+// flops per block row: the FP64 residual 3 m^2 k complex multiply-adds
+// (24 m^2 k flop); the FP32 correction sweep 40 m^2 k flop, at about 1/8 of
+// its FP64 time on GB300 (FP32 levels 11 ms vs FP64 85 ms per sweep at
+// N = 2^14, m = 64, k = 32); the FP64 path 25.33 m^3 + 40 m^2 k.
+double mixed_step_cost(int m, int k) {
+    const double mm = (double)m * m, step = 24.0 * mm * k + 5.0 * mm * k;
+    return step / (25.33 * mm * m + 40.0 * mm * k);
+}
+
 int mixed_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     char *ws = p->ws;
     const int64_t n = p->N * (int64_t)p->m * k;
@@ -534,12 +677,13 @@ int mixed_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
         if (!(delta == delta)) break;                       // NaN: give up on FP32
         if (it > 0) {
             rho = prev > 0 ? delta / prev : 0.0;
-            if (rho * delta <= 1e-13 || delta <= 4.4e-16) {
-                p->last_delta = delta; p->last_rho = rho;
-                return CRSOLVE_OK;
-            }
+            p->last_delta = delta; p->last_rho = rho;
+            if (rho * delta <= 1e-13 || delta <= 4.4e-16) return CRSOLVE_OK;
             slow = rho > 0.5 ? slow + 1 : 0;
-            if (slow >= 2) break;
+            if (slow >= 2 || !(rho < 1.0)) break;
+            // steps still needed for rho^n * delta <= 1e-13, against the fallback
+            const double need = std::ceil(std::log(1e-13 / (rho * delta)) / std::log(rho));
+            if (need * mixed_step_cost(p->m, k) > 1.0) break;
         }
         prev = delta;
         p->last_delta = delta; p->last_rho = rho;
@@ -763,13 +907,20 @@ int crsolve_solve_host(crsolve_plan p, int32_t k, const crsolve_z *A_host, const
     const size_t zsz = sizeof(crsolve_z), mm = (size_t)p->m * p->m, mk = (size_t)p->m * k;
     z2 *dA = reinterpret_cast<z2 *>(p->ws + p->offSA), *dB = reinterpret_cast<z2 *>(p->ws + p->offSB);
     z2 *dy = reinterpret_cast<z2 *>(p->ws + p->offSY), *dx = reinterpret_cast<z2 *>(p->ws + p->offSX);
-    if (cudaMemcpyAsync(dA, A_host, p->N * mm * zsz, cudaMemcpyHostToDevice, s) != cudaSuccess) return CRSOLVE_ECUDA;
-    if (p->N > 1 && cudaMemcpyAsync(dB, B_host, (p->N - 1) * mm * zsz, cudaMemcpyHostToDevice, s) != cudaSuccess)
-        return CRSOLVE_ECUDA;
-    if (cudaMemcpyAsync(dy, y_host, p->N * mk * zsz, cudaMemcpyHostToDevice, s) != cudaSuccess) return CRSOLVE_ECUDA;
-    if ((rc = do_factor(p, dA, p->N > 1 ? dB : nullptr, s))) return rc;
-    if ((rc = do_solve(p, k, dy, dx, s))) return rc;
-    if (cudaMemcpyAsync(x_host, dx, p->N * mk * zsz, cudaMemcpyDeviceToHost, s) != cudaSuccess) return CRSOLVE_ECUDA;
+    if (!p->alg1 && p->N > 1) {
+        if ((rc = solve_host_pipelined(p, k, A_host, B_host, y_host, x_host, s))) return rc;
+    } else {
+        if (cudaMemcpyAsync(dA, A_host, p->N * mm * zsz, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return CRSOLVE_ECUDA;
+        if (p->N > 1 && cudaMemcpyAsync(dB, B_host, (p->N - 1) * mm * zsz, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return CRSOLVE_ECUDA;
+        if (cudaMemcpyAsync(dy, y_host, p->N * mk * zsz, cudaMemcpyHostToDevice, s) != cudaSuccess)
+            return CRSOLVE_ECUDA;
+        if ((rc = do_factor(p, dA, p->N > 1 ? dB : nullptr, s))) return rc;
+        if ((rc = do_solve(p, k, dy, dx, s))) return rc;
+        if (cudaMemcpyAsync(x_host, dx, p->N * mk * zsz, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+            return CRSOLVE_ECUDA;
+    }
     unsigned long long st = 0;
     if (cudaMemcpyAsync(&st, p->ws + p->offStatus, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return CRSOLVE_ECUDA;
@@ -808,6 +959,8 @@ int crsolve_info_get(crsolve_plan p, crsolve_info *out, void *stream) {
 int crsolve_destroy(crsolve_plan p) {
     if (!p) return CRSOLVE_EINVAL;
     for (cudaEvent_t e : p->pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : p->xev) cudaEventDestroy(e);
+    if (p->cstream) cudaStreamDestroy(p->cstream);
     delete p;
     return CRSOLVE_OK;
 }

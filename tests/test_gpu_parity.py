@@ -164,6 +164,43 @@ def test_solve_host_buffers(cuda_ok):
     assert rel_err(x.numpy(), oracle.cr_solve(A, B, y)[0]) <= TOL
 
 
+@pytest.mark.parametrize("N,m,k", [(1, 4, 1), (2, 8, 4), (3, 5, 2), (17, 8, 4), (333, 16, 3), (20001, 8, 4),
+                                   (4099, 32, 5)])
+def test_solve_host_overlapped_equals_device_path(cuda_ok, N, m, k):
+    """crsolve_solve_host sends A, B range by range and starts the level-0
+    factor of each range as soon as its rows arrive, and returns x range by
+    range behind the level-0 up sweep.  The kernels do the same arithmetic as
+    crsolve_factor + crsolve_solve, so x must be bit-identical to theirs (sizes
+    with one, a few and eight ranges, ragged last ranges; pinned and pageable
+    host buffers)."""
+    A, B, y = synthetic.gen_system(N, m, k, seed=N + 7 * m + k)
+    x_dev, info, _ = run(A, B, y)
+    plan = crs.Plan(N, m, k, flags=1)
+    for pinned in (True, False):
+        tA, tB, ty = (torch.from_numpy(a) for a in (A, B, y))
+        if pinned:
+            tA, tB, ty = (t.pin_memory() for t in (tA, tB, ty))
+        x, rc = crs.crsolve_solve_host(plan, tA, tB if N > 1 else None, ty)
+        assert rc == 0
+        assert np.array_equal(x.numpy(), x_dev), pinned
+    assert rel_err(x_dev, oracle.cr_solve(A, B, y)[0]) <= TOL
+
+
+def test_solve_host_overlapped_breakdown_gives_nan(cuda_ok):
+    N, m = 4000, 8
+    for seed in range(20):
+        A, B, y = synthetic.gen_system(N, m, 2, seed=seed)
+        Ai = synthetic.make_indefinite(A)
+        if np.linalg.eigvalsh(Ai[N // 2 - 1]).min() < 0:
+            break
+    plan = crs.Plan(N, m, 2, flags=1)
+    tA, tB, ty = (torch.from_numpy(a).pin_memory() for a in (Ai, B, y))
+    x, rc = crs.crsolve_solve_host(plan, tA, tB, ty)
+    assert rc == 1
+    assert crs.crsolve_info_get(plan) == oracle.cr_solve(Ai, B, y)[1]
+    assert np.isnan(x.numpy()).all()
+
+
 def test_solve_before_factor_is_an_error(cuda_ok):
     plan = crs.Plan(8, 4, 1)
     y = torch.zeros((8, 4, 1), dtype=torch.complex128, device="cuda")
