@@ -49,8 +49,8 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # ~1.9 DFMA/clk/SM), 152 SMs, 2070 MHz maximum SM clock
 FP64_FMA_PER_CLK_SM, N_SM, SM_MAX_MHZ = 2, 152, 2070.0
 FP64_PEAK_GFLOPS = FP64_FMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ / 1e3
-# ncu: k_factor_odd<8, double>, level 0 of N = 2^18: dram 538.0 MB read + 625.1 MB written for 2^17 odd blocks
-TRAFFIC_PER_ODD_BLOCK = (538.0e6 + 625.1e6) / (1 << 17)
+# ncu: k_factor_odd<8, double>, level 0 of N = 2^18: dram 537.9 MB read + 624.8 MB written for 2^17 odd blocks
+TRAFFIC_PER_ODD_BLOCK = (537.9e6 + 624.8e6) / (1 << 17)
 
 
 def flops_factor_per_odd_block(m: int) -> float:
@@ -365,6 +365,41 @@ MIX_WORKLOAD = ("precision: FP32 fine levels + FP64 coarse levels, FP64 residual
                 "N=2^14, m=64, k=32, complex, kappa in {1e2, 1e4, 1e6}")
 
 
+def residual_eta(dA, dB, dy, dx) -> float:
+    """max-norm backward error ||y - A x|| / (||A|| ||x||) of a device solution
+    (torch ops on the measurement side, not part of the solver)."""
+    import torch
+    with torch.no_grad():
+        Ah = torch.tril(dA, -1)
+        Ah = Ah + Ah.conj().transpose(1, 2) + torch.diag_embed(torch.diagonal(dA, dim1=1, dim2=2).real.to(dA.dtype))
+        r = dy - torch.bmm(Ah, dx)
+        r[1:] -= torch.bmm(dB, dx[:-1])
+        r[:-1] -= torch.bmm(dB.conj().transpose(1, 2), dx[1:])
+        normA = (Ah.abs().sum(2).max() + 2 * dB.abs().sum(2).max()).item()
+        return (r.abs().amax() / (normA * dx.abs().amax())).item()
+
+
+def mixed_oracle_check(table, kap, m, k):
+    """Relative error of the mixed form against the CPU oracle on the N = 2^10
+    system with the same kappa (the oracle solves it in ~0.1 s)."""
+    import torch
+    import oracle
+    import paper_1807_00370_gb300 as crs
+    from paper_1807_00370_gb300 import _native as nat
+    case = table.get("mixed_N2p10_m64_k32")
+    if case is None:
+        return None
+    n = case["N"]
+    A, B, y = synthetic.gen_system(n, m, k, seed=case["seed"], shift=case["shifts"][kap])
+    dA, dB, dy = (torch.from_numpy(a).cuda() for a in (A, B, y))
+    plan = crs.Plan(n, m, k, precision=nat.CRSOLVE_MIXED)
+    crs.crsolve_factor(plan, dA, dB)
+    x = crs.crsolve_solve(plan, dy).cpu().numpy()
+    xo, info = oracle.cr_solve(A, B, y)
+    return {"N": n, "rel_err_vs_oracle": float(np.linalg.norm(x - xo) / np.linalg.norm(xo)),
+            "flags_equal": crs.crsolve_info_get(plan) == info, "refinement": crs.crsolve_mixed_stats(plan)}
+
+
 def run_mixed(args):
     """For each kappa: the mixed form and the plain FP64 path on the same system."""
     import torch
@@ -406,10 +441,14 @@ def run_mixed(args):
             res[name] = {"ms": e0.elapsed_time(e1) / args.steps, "x": x, "kernels_ms": by,
                          "stats": crs.crsolve_mixed_stats(plan) if prec == nat.CRSOLVE_MIXED else None}
         err = float((torch.linalg.norm(res["mixed"]["x"] - res["fp64"]["x"]) / torch.linalg.norm(res["fp64"]["x"])).item())
-        runs.append({"kappa": float(kap), "shift": shifts["shifts"][kap], "mixed_ms": res["mixed"]["ms"],
-                     "fp64_ms": res["fp64"]["ms"], "speedup": res["fp64"]["ms"] / res["mixed"]["ms"],
-                     "rel_err_vs_fp64_path": err, "refinement": res["mixed"]["stats"],
-                     "mixed_kernels_ms": res["mixed"]["kernels_ms"], "fp64_kernels_ms": res["fp64"]["kernels_ms"]})
+        run = {"kappa": float(kap), "shift": shifts["shifts"][kap], "mixed_ms": res["mixed"]["ms"],
+               "fp64_ms": res["fp64"]["ms"], "speedup": res["fp64"]["ms"] / res["mixed"]["ms"],
+               "rel_err_vs_fp64_path": err, "residual_eta_mixed": residual_eta(dA, dB, dy, res["mixed"]["x"]),
+               "refinement": res["mixed"]["stats"],
+               "mixed_kernels_ms": res["mixed"]["kernels_ms"], "fp64_kernels_ms": res["fp64"]["kernels_ms"]}
+        if not args.no_cpu_baseline:
+            run["oracle_check"] = mixed_oracle_check(table, kap, m, k)
+        runs.append(run)
     peak_tf = FP64_PEAK_GFLOPS / 1e3
     best = min(runs, key=lambda r: r["mixed_ms"])
     line = {
@@ -534,14 +573,7 @@ def run_alg1(args):
     step()
     torch.cuda.synchronize()
 
-    with torch.no_grad():
-        Ah = torch.tril(dA, -1)
-        Ah = Ah + Ah.conj().transpose(1, 2) + torch.diag_embed(torch.diagonal(dA, dim1=1, dim2=2).real.to(dA.dtype))
-        r = dy - torch.bmm(Ah, dx)
-        r[1:] -= torch.bmm(dB, dx[:-1])
-        r[:-1] -= torch.bmm(dB.conj().transpose(1, 2), dx[1:])
-        normA = (Ah.abs().sum(2).max() + 2 * dB.abs().sum(2).max()).item()
-        eta = (r.abs().amax() / (normA * dx.abs().amax())).item()
+    eta = residual_eta(dA, dB, dy, dx)
 
     e2e = None
     if not args.no_e2e:
@@ -612,7 +644,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--workload", default="plain", choices=["plain", "batched", "adjoint", "mixed", "alg1"])
     ap.add_argument("--nsys", type=int, default=4096, help="systems of the batched workload")
     ap.add_argument("--log2n", type=int, default=20,
@@ -700,14 +732,7 @@ def main():
     value = total_units / (ms * 1e-3)
 
     # measurement-side residual check (torch ops, not part of the solver)
-    with torch.no_grad():
-        Ah = torch.tril(dA, -1)
-        Ah = Ah + Ah.conj().transpose(1, 2) + torch.diag_embed(torch.diagonal(dA, dim1=1, dim2=2).real.to(dA.dtype))
-        r = dy - torch.bmm(Ah, dx)
-        r[1:] -= torch.bmm(dB, dx[:-1])
-        r[:-1] -= torch.bmm(dB.conj().transpose(1, 2), dx[1:])
-        normA = (Ah.abs().sum(2).max() + 2 * dB.abs().sum(2).max()).item()
-        eta = (r.abs().amax() / (normA * dx.abs().amax())).item()
+    eta = residual_eta(dA, dB, dy, dx)
 
     e2e = None
     if not args.no_e2e:
