@@ -301,6 +301,41 @@ def adjoint_flops_per_row(m: int, k: int) -> float:
     return 8.0 * (m * (m + 1) / 2 + m * m) * 2 * k
 
 
+def adjoint_keep_levels(args, dA, dB, dy, dc, full_bytes, full_ms):
+    """Memory held between the forward and the backward pass against the
+    time of one forward + backward step, for plans that keep the factors of
+    the first `keep` levels only (crsolve_plan_keep_levels): forward = factor +
+    solve, then the scratch (coarse levels, solve buffers) is released; the
+    backward pass binds a new scratch, which re-factors the coarse levels."""
+    import torch
+    import paper_1807_00370_gb300 as crs
+    N, m, k = dy.shape
+    out = [{"keep": "all", "held_bytes": full_bytes, "ms_per_step": full_ms}]
+    stream = torch.cuda.current_stream()
+    for keep in (2, 1, 0):
+        plan = crs.Plan(N, m, k, keep_levels=keep)
+        x = torch.empty_like(dy)
+
+        def step():
+            crs.crsolve_factor(plan, dA, dB)
+            crs.crsolve_solve(plan, dy, x)
+            plan.release_scratch()
+            return crs.crsolve_backward(plan, x, dc)
+
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append({"keep": keep, "held_bytes": plan.workspace_bytes, "scratch_bytes": plan.scratch_bytes,
+                    "ms_per_step": e0.elapsed_time(e1) / args.steps})
+    return out
+
+
 def run_adjoint(args):
     import torch
     import paper_1807_00370_gb300 as crs
@@ -350,6 +385,7 @@ def run_adjoint(args):
                      if adj_ms else None},
         "kernels": {kk: {"ms_per_step": v} for kk, v in by.items()},
         "gpu_launches": crs.crsolve_launch_count(plan) - launches0, "e2e": None, "cpu_baseline": None,
+        "keep_levels": adjoint_keep_levels(args, dA, dB, dy, dc, plan.workspace_bytes, ms_step),
     }
     if not args.no_cpu_baseline:
         sA, sB, sy = synthetic.gen_system(1 << 12, m, k, seed=ADJ_SEED)

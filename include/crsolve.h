@@ -121,6 +121,42 @@ int crsolve_workspace_bytes(crsolve_plan p, size_t *bytes);
 int crsolve_set_workspace(crsolve_plan p, void *dev_ptr, size_t bytes);
 
 /*
+ * crsolve_plan_keep_levels -- trade compute for memory (classic FP64 plans;
+ * call before crsolve_set_workspace).  The plan's memory is split in two:
+ *   workspace  the factors (L, 1/diag L, Z = [P | Q]) of the fine levels
+ *              0 .. keep-1 and the reduced system (A^(keep), B^(keep)) of
+ *              level keep, plus the breakdown status;
+ *   scratch    the factors of the coarse levels keep .. L, the right-hand
+ *              sides and solutions of every level during a solve, and the
+ *              CTA-boundary buffers (crsolve_scratch_bytes, crsolve_set_scratch).
+ * Level l has ceil(N_l / 2) odd blocks, so the workspace holds about
+ * 1 - 2^-keep of the factor storage, and rebuilding the coarse levels costs
+ * about 2^-keep of a factorisation.  Factor, solve, backward and solve_host
+ * calls need the scratch bound; between calls it may be unbound
+ * (crsolve_set_scratch(p, NULL, 0)) and its memory reused.  Binding scratch
+ * (any pointer, even the same one) marks the coarse factors as lost: the next
+ * crsolve_solve or crsolve_backward first re-factors levels keep .. L from the
+ * stored level-keep system (the recursion of Sec. 2 "Formulation of the
+ * Method" restarted at level keep), which is deterministic, so results are
+ * bit-identical to an unsplit plan's.  keep = 0 keeps no factors: the
+ * re-factorisation starts from the A and B given to crsolve_factor, which must
+ * then stay valid and unchanged (after crsolve_solve_host, whose staged A and B
+ * live in the scratch, that gives CRSOLVE_ENOTFACTORED).  keep = -1 (the
+ * default) keeps everything in the workspace and uses no scratch.
+ * Returns CRSOLVE_EINVAL (keep < -1, or workspace or scratch already bound) or
+ * CRSOLVE_EUNSUPPORTED (Algorithm 1 or mixed-precision plans).
+ */
+int crsolve_plan_keep_levels(crsolve_plan p, int32_t keep);
+
+/* Bytes of scratch a plan split by crsolve_plan_keep_levels needs (0 otherwise). */
+int crsolve_scratch_bytes(crsolve_plan p, size_t *bytes);
+
+/* Bind caller-owned device memory (256-byte aligned, >= crsolve_scratch_bytes)
+ * as the scratch of a split plan, or unbind it with dev_ptr = NULL.  Returns
+ * CRSOLVE_EINVAL on an unsplit plan, CRSOLVE_ENOMEM if bytes is too small. */
+int crsolve_set_scratch(crsolve_plan p, void *dev_ptr, size_t bytes);
+
+/*
  * crsolve_factor -- the reduction sweep of Sec. 2 on device data.
  *   A [N][m][m], B [N-1][m][m] (B may be NULL iff N == 1).  For every level it
  *   factors the odd diagonal blocks (Cholesky with breakdown test), forms

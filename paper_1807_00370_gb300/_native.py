@@ -53,6 +53,9 @@ SIGNATURES = {
     "crsolve_plan_create": (ctypes.c_int, [_I64, _I32, _I32, _I32, _U32, ctypes.POINTER(_P)]),
     "crsolve_workspace_bytes": (ctypes.c_int, [_P, ctypes.POINTER(_SZ)]),
     "crsolve_set_workspace": (ctypes.c_int, [_P, _P, _SZ]),
+    "crsolve_plan_keep_levels": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "crsolve_scratch_bytes": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "crsolve_set_scratch": (ctypes.c_int, [_P, _P, _SZ]),
     "crsolve_factor": (ctypes.c_int, [_P, _P, _P, _P]),
     "crsolve_solve": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "crsolve_backward": (ctypes.c_int, [_P, _I32, _P, _P, _P, _P, _P, _P]),

@@ -56,10 +56,17 @@ def _need(t, shape, name, device=None, cpu=False):
 
 class Plan:
     """One system shape (N blocks of m x m, right-hand sides up to kmax wide)
-    with its device workspace (a torch uint8 tensor owned by this object)."""
+    with its device workspace (a torch uint8 tensor owned by this object).
+
+    keep_levels (classic FP64 plans) splits the memory as
+    crsolve_plan_keep_levels does: ``workspace`` keeps the factors of levels
+    < keep_levels and the level-keep_levels reduced system; ``scratch`` holds
+    the coarse levels and the solve buffers.  release_scratch() frees the
+    scratch between calls; the next call binds a new one and the solver
+    re-factors the coarse levels first (bit-identical results)."""
 
     def __init__(self, N: int, m: int, kmax: int, precision: int = nat.CRSOLVE_FP64,
-                 flags: int = 0, device=None):
+                 flags: int = 0, device=None, keep_levels: int | None = None):
         lib = nat.load()
         if not torch.cuda.is_available():
             raise RuntimeError("crsolve needs a CUDA device")
@@ -70,16 +77,42 @@ class Plan:
         with torch.cuda.device(self.device):
             nat.check(lib.crsolve_plan_create(self.N, self.m, self.kmax, self.precision, self.flags,
                                               ctypes.byref(self._h)), "crsolve_plan_create")
+            self.keep_levels = None if keep_levels is None else int(keep_levels)
+            if self.keep_levels is not None:
+                nat.check(lib.crsolve_plan_keep_levels(self._h, self.keep_levels), "crsolve_plan_keep_levels")
             nbytes = ctypes.c_size_t()
             nat.check(lib.crsolve_workspace_bytes(self._h, ctypes.byref(nbytes)), "crsolve_workspace_bytes")
             self.workspace_bytes = int(nbytes.value)
             self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
             nat.check(lib.crsolve_set_workspace(self._h, _vp(self.workspace), self.workspace.numel()),
                       "crsolve_set_workspace")
+            self.scratch, self.scratch_bytes = None, 0
+            if self.keep_levels is not None:
+                nat.check(lib.crsolve_scratch_bytes(self._h, ctypes.byref(nbytes)), "crsolve_scratch_bytes")
+                self.scratch_bytes = int(nbytes.value)
+                self.ensure_scratch()
 
     @property
     def handle(self):
         return self._h
+
+    def ensure_scratch(self) -> None:
+        """Bind a scratch buffer if this split plan has none (the next solve
+        then re-factors the coarse levels)."""
+        if self.keep_levels is None or self.scratch is not None:
+            return
+        with torch.cuda.device(self.device):
+            self.scratch = torch.empty(max(self.scratch_bytes, 256), dtype=torch.uint8, device=self.device)
+            nat.check(nat.load().crsolve_set_scratch(self._h, _vp(self.scratch), self.scratch.numel()),
+                      "crsolve_set_scratch")
+
+    def release_scratch(self) -> None:
+        """Unbind and free the scratch of a split plan (call on the stream that
+        used it); the workspace alone stays held."""
+        if self.keep_levels is None or self.scratch is None:
+            return
+        nat.check(nat.load().crsolve_set_scratch(self._h, None, 0), "crsolve_set_scratch")
+        self.scratch = None
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:
@@ -102,6 +135,7 @@ def crsolve_factor(plan: Plan, A: torch.Tensor, B: torch.Tensor | None, stream=N
     _need(A, (N, m, m), "A", plan.device)
     if N > 1:
         _need(B, (N - 1, m, m), "B", plan.device)
+    plan.ensure_scratch()
     with torch.cuda.device(plan.device):
         nat.check(nat.load().crsolve_factor(plan.handle, _vp(A), _vp(B) if N > 1 else None, _stream(stream)),
                   "crsolve_factor")
@@ -114,6 +148,7 @@ def crsolve_solve(plan: Plan, y: torch.Tensor, x: torch.Tensor | None = None, st
     if x is None:
         x = torch.empty_like(y)
     _need(x, (N, m, k), "x", plan.device)
+    plan.ensure_scratch()
     with torch.cuda.device(plan.device):
         nat.check(nat.load().crsolve_solve(plan.handle, k, _vp(y), _vp(x), _stream(stream)), "crsolve_solve")
     return x
@@ -128,6 +163,7 @@ def crsolve_backward(plan: Plan, x: torch.Tensor, gx: torch.Tensor, want_gA: boo
     gy = torch.empty_like(gx)
     gA = torch.empty((N, m, m), dtype=torch.complex128, device=plan.device) if want_gA else None
     gB = torch.empty((N - 1, m, m), dtype=torch.complex128, device=plan.device) if (want_gB and N > 1) else None
+    plan.ensure_scratch()
     with torch.cuda.device(plan.device):
         nat.check(nat.load().crsolve_backward(plan.handle, k, _vp(x), _vp(gx), _vp(gy), _vp(gA), _vp(gB),
                                               _stream(stream)), "crsolve_backward")
@@ -154,6 +190,7 @@ def crsolve_solve_host(plan: Plan, A: torch.Tensor, B: torch.Tensor | None, y: t
     if x is None:
         x = torch.empty_like(y, pin_memory=y.is_pinned())
     _need(x, (N, m, k), "x", cpu=True)
+    plan.ensure_scratch()
     with torch.cuda.device(plan.device):
         rc = nat.check(nat.load().crsolve_solve_host(plan.handle, k, _vp(A), _vp(B) if N > 1 else None,
                                                      _vp(y), _vp(x), _stream(stream)), "crsolve_solve_host")
@@ -279,35 +316,61 @@ class CRSolveFn(torch.autograd.Function):
     outer products).  A_j is treated as Hermitian: its gradient is projected
     onto Hermitian matrices.
 
-    keep_factors=False trades compute for memory: the forward pass frees its
-    plan (the per-level factors and reduced systems) and keeps only A, B and
-    x; the backward pass re-factors A to get the factors back.  The
-    re-factorisation is deterministic, so the gradients are identical.
+    keep_factors trades compute for memory between the forward and the
+    backward pass:
+      True   keep the factors of every level (no recomputation);
+      l >= 1 (classic method) keep the factors of the fine levels 0 .. l-1
+             and the level-l reduced system, about 1 - 2^-l of the factor
+             memory; the backward pass re-factors the coarse levels l .. L
+             (about 2^-l of the factorisation);
+      False  keep only A, B and x; the backward pass re-factors everything.
+    The re-factorisation is deterministic, so the gradients are identical.
     method selects the solver as in ``solve``."""
 
     @staticmethod
-    def forward(ctx, A, B, y, keep_factors: bool = True, method: str = "classic"):
+    def forward(ctx, A, B, y, keep_factors=True, method: str = "classic"):
         N, m, _ = A.shape
         A, B, y = A.contiguous(), None if B is None else B.contiguous(), y.contiguous()
         ctx.flags = _method_flags(method)
-        plan = Plan(N, m, y.shape[-1], flags=ctx.flags, device=A.device)
+        if keep_factors is True:
+            keep = None
+        elif keep_factors is False:
+            keep = 0
+        else:
+            keep = int(keep_factors)
+            if keep < 0:
+                raise ValueError("keep_factors must be True, False or a level count >= 0")
+        if keep is not None and ctx.flags & nat.CRSOLVE_PLAN_ALG1 and keep > 0:
+            raise ValueError("keep_factors = l > 0 needs the classic method")
+        split = keep is not None and not ctx.flags & nat.CRSOLVE_PLAN_ALG1
+        plan = Plan(N, m, y.shape[-1], flags=ctx.flags, device=A.device, keep_levels=keep if split else None)
         crsolve_factor(plan, A, B)
         x = crsolve_solve(plan, y)
         ctx.has_B = B is not None
-        ctx.keep = bool(keep_factors)
-        if ctx.keep:
+        ctx.keep = keep
+        if keep is None:
             ctx.plan = plan
             ctx.save_for_backward(x)
+        elif split:
+            # the coarse levels go with the scratch; keep = 0 re-factors from
+            # A and B, which the plan reads again in the backward pass
+            plan.release_scratch()
+            ctx.plan = plan
+            ctx.save_for_backward(x, A, B if B is not None else A.new_empty(0))
         else:
             plan.close()
             del plan
+            ctx.plan = None
             ctx.save_for_backward(x, A, B if B is not None else A.new_empty(0))
         return x
 
     @staticmethod
     def backward(ctx, gx):
-        if ctx.keep:
+        if ctx.keep is None:
             (x,) = ctx.saved_tensors
+            plan = ctx.plan
+        elif ctx.plan is not None:
+            x = ctx.saved_tensors[0]
             plan = ctx.plan
         else:
             x, A, B = ctx.saved_tensors

@@ -32,6 +32,15 @@ struct LevelPlan {
 constexpr int64_t kMixedCoarse = 2;
 constexpr int kMixedMaxIter = 40;
 
+// Workspace offsets with this bit set address the plan's scratch buffer
+// (plans split by crsolve_plan_keep_levels); the others the workspace.
+constexpr size_t kScr = size_t(1) << 62;
+
+struct WsMap {
+    char *ws, *scr;
+    char *operator+(size_t off) const { return (off & kScr) ? scr + (off & ~kScr) : ws + off; }
+};
+
 }  // namespace
 
 struct crsolve_plan_s {
@@ -44,6 +53,16 @@ struct crsolve_plan_s {
     size_t total = 0;
     char *ws = nullptr;
     size_t ws_bytes = 0;
+    // keep_levels split (keep >= 0): factors of levels < keep and the level-keep
+    // system in the workspace; coarser factors, solve buffers and CTA-boundary
+    // scratch in the scratch buffer, whose coarse factors are rebuilt from the
+    // level-keep system after the scratch has been (re)bound
+    int keep = -1;
+    char *scr = nullptr;
+    size_t scr_total = 0;
+    bool coarse_valid = false;
+    const z2 *lvl0A = nullptr, *lvl0B = nullptr;   // the caller's A, B (re-factor from level 0)
+    WsMap map() const { return WsMap{ws, scr}; }
     bool factored = false;
     bool prepared = false;
     // mixed precision
@@ -91,7 +110,7 @@ crs::LevelArgs level_args(const crsolve_plan_s *p, int l, const z2 *A0, const z2
     crs::LevelArgs a{};
     a.Nl = L.Nl; a.no = L.no; a.ne = L.ne;
     a.m = p->m; a.level = l;
-    char *ws = p->ws;
+    const WsMap ws = p->map();
     a.A = (l == 0) ? A0 : reinterpret_cast<const z2 *>(ws + p->lev[l - 1].offAn);
     a.B = (l == 0) ? B0 : reinterpret_cast<const z2 *>(ws + p->lev[l - 1].offBn);
     a.L = reinterpret_cast<z2 *>(ws + L.offL);
@@ -113,7 +132,7 @@ crs::LevelArgsT<float> level_args32(const crsolve_plan_s *p, int l) {
     crs::LevelArgsT<float> a{};
     a.Nl = L.Nl; a.no = L.no; a.ne = L.ne;
     a.m = p->m; a.level = l;
-    char *ws = p->ws;
+    const WsMap ws = p->map();
     using C = crs::c2;
     a.A = reinterpret_cast<const C *>(ws + (l == 0 ? p->offA32 : p->lev32[l - 1].offAn));
     a.B = reinterpret_cast<const C *>(ws + (l == 0 ? p->offB32 : p->lev32[l - 1].offBn));
@@ -204,7 +223,7 @@ crs::LevelArgs alg1_args(const crsolve_plan_s *p, int l, int h) {
     const int64_t N = p->N, in0 = (h == 0) ? 1 : 0, out0 = (h == 0) ? 1 + N / 2 : 1;
     const size_t mm = (size_t)p->m * p->m;
     const int cur = l & 1, nxt = cur ^ 1;
-    char *ws = p->ws;
+    const WsMap ws = p->map();
     a.A = reinterpret_cast<const z2 *>(ws + p->offA1A[cur]) + in0 * mm;
     a.B = reinterpret_cast<const z2 *>(ws + p->offA1B[cur]) + in0 * mm;
     a.An = reinterpret_cast<z2 *>(ws + p->offA1A[nxt]) + out0 * mm;
@@ -224,9 +243,9 @@ crs::LevelArgs alg1_args(const crsolve_plan_s *p, int l, int h) {
 int alg1_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
     const int64_t N = p->N;
     const size_t mm = (size_t)p->m * p->m, zsz = sizeof(z2);
-    z2 *A0 = reinterpret_cast<z2 *>(p->ws + p->offA1A[0]), *A1 = reinterpret_cast<z2 *>(p->ws + p->offA1A[1]);
-    z2 *B0 = reinterpret_cast<z2 *>(p->ws + p->offA1B[0]), *B1 = reinterpret_cast<z2 *>(p->ws + p->offA1B[1]);
-    if (cudaMemsetAsync(p->ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess ||
+    z2 *A0 = reinterpret_cast<z2 *>(p->map() + p->offA1A[0]), *A1 = reinterpret_cast<z2 *>(p->map() + p->offA1A[1]);
+    z2 *B0 = reinterpret_cast<z2 *>(p->map() + p->offA1B[0]), *B1 = reinterpret_cast<z2 *>(p->map() + p->offA1B[1]);
+    if (cudaMemsetAsync(p->map() + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess ||
         cudaMemcpyAsync(A0 + mm, A, N * mm * zsz, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
         (N > 1 && cudaMemcpyAsync(B0 + mm, B, (N - 1) * mm * zsz, cudaMemcpyDeviceToDevice, s) != cudaSuccess))
         return CRSOLVE_ECUDA;
@@ -260,8 +279,8 @@ int alg1_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
 int alg1_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     const int64_t N = p->N;
     const size_t mk = (size_t)p->m * k, zsz = sizeof(z2);
-    z2 *Y[2] = {reinterpret_cast<z2 *>(p->ws + p->offA1Y[0]), reinterpret_cast<z2 *>(p->ws + p->offA1Y[1])};
-    z2 *Xb = reinterpret_cast<z2 *>(p->ws + p->offA1Xb), *Xz = reinterpret_cast<z2 *>(p->ws + p->offA1Xz);
+    z2 *Y[2] = {reinterpret_cast<z2 *>(p->map() + p->offA1Y[0]), reinterpret_cast<z2 *>(p->map() + p->offA1Y[1])};
+    z2 *Xb = reinterpret_cast<z2 *>(p->map() + p->offA1Xb), *Xz = reinterpret_cast<z2 *>(p->map() + p->offA1Xz);
     if (cudaMemcpyAsync(Y[0] + mk, y, N * mk * zsz, cudaMemcpyDeviceToDevice, s) != cudaSuccess ||
         cudaMemsetAsync(Y[0], 0, mk * zsz, s) != cudaSuccess || cudaMemsetAsync(Y[1], 0, mk * zsz, s) != cudaSuccess ||
         cudaMemsetAsync(Xz, 0, (N / 2 + 1) * mk * zsz, s) != cudaSuccess)
@@ -302,7 +321,7 @@ int alg1_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     }
     if (N >= 2 && (rc = launch(p, CRSOLVE_K_ALG1_MERGE, p->aL, N, s, [&] {
                        return crs::launch_alg1_merge(x, Xb, N, (int64_t)mk,
-                                                     reinterpret_cast<const unsigned long long *>(p->ws + p->offStatus),
+                                                     reinterpret_cast<const unsigned long long *>(p->map() + p->offStatus),
                                                      p->nsm, s);
                    })))
         return rc;
@@ -328,7 +347,7 @@ int factor_levels(crsolve_plan_s *p, int l0, const z2 *A, const z2 *B, cudaStrea
 
 int do_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
     if (p->alg1) return alg1_factor(p, A, B, s);
-    if (cudaMemsetAsync(p->ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
+    if (cudaMemsetAsync(p->map() + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
         return CRSOLVE_ECUDA;
     int rc;
     if ((rc = factor_levels(p, 0, A, B, s))) return rc;
@@ -350,7 +369,7 @@ int solve_sweeps(crsolve_plan_s *p, int k, const z2 *y, z2 *x, int l_end, cudaSt
     int rc;
     for (int l = 0; l < nlev; ++l) {
         crs::LevelArgs a = solve_args(p, l, k);
-        a.y = (l == 0) ? y : reinterpret_cast<const z2 *>(p->ws + p->lev[l - 1].offYn);
+        a.y = (l == 0) ? y : reinterpret_cast<const z2 *>(p->map() + p->lev[l - 1].offYn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s,
                          [&] { return crs::launch_solve_down_odd(p->mt, a, s); })))
             return rc;
@@ -361,7 +380,7 @@ int solve_sweeps(crsolve_plan_s *p, int k, const z2 *y, z2 *x, int l_end, cudaSt
     }
     for (int l = nlev - 1; l >= l_end; --l) {
         crs::LevelArgs a = solve_args(p, l, k);
-        a.x = (l == 0) ? x : reinterpret_cast<z2 *>(p->ws + p->lev[l - 1].offXn);
+        a.x = (l == 0) ? x : reinterpret_cast<z2 *>(p->map() + p->lev[l - 1].offXn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, l, a.no, s,
                          [&] { return crs::launch_solve_up(p->mt, a, s); })))
             return rc;
@@ -372,6 +391,20 @@ int solve_sweeps(crsolve_plan_s *p, int k, const z2 *y, z2 *x, int l_end, cudaSt
 int do_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     if (p->alg1) return alg1_solve(p, k, y, x, s);
     return solve_sweeps(p, k, y, x, 0, s);
+}
+
+// Plans split by crsolve_plan_keep_levels: after the scratch has been (re)bound
+// the factors of levels keep .. L are rebuilt from the level-keep system kept
+// in the workspace (for keep = 0: the caller's A, B), the recursion of Sec. 2
+// restarted at level keep.  Deterministic, so they equal the lost ones.
+int ensure_coarse(crsolve_plan_s *p, cudaStream_t s) {
+    if (p->keep < 0 || p->coarse_valid) return CRSOLVE_OK;
+    if (!p->scr) return CRSOLVE_ENOMEM;
+    if (p->keep == 0 && !p->lvl0A) return CRSOLVE_ENOTFACTORED;
+    int rc;
+    if ((rc = factor_levels(p, p->keep, p->lvl0A, p->lvl0B, s))) return rc;
+    p->coarse_valid = true;
+    return CRSOLVE_OK;
 }
 
 // ---- host buffers: copies overlapped with the level-0 kernels --------------
@@ -404,8 +437,8 @@ int solve_host_pipelined(crsolve_plan_s *p, int k, const crsolve_z *A_host, cons
                          const crsolve_z *y_host, crsolve_z *x_host, cudaStream_t s) {
     const int64_t N = p->N;
     const size_t zsz = sizeof(crsolve_z), mm = (size_t)p->m * p->m, mk = (size_t)p->m * k;
-    z2 *dA = reinterpret_cast<z2 *>(p->ws + p->offSA), *dB = reinterpret_cast<z2 *>(p->ws + p->offSB);
-    z2 *dy = reinterpret_cast<z2 *>(p->ws + p->offSY), *dx = reinterpret_cast<z2 *>(p->ws + p->offSX);
+    z2 *dA = reinterpret_cast<z2 *>(p->map() + p->offSA), *dB = reinterpret_cast<z2 *>(p->map() + p->offSB);
+    z2 *dy = reinterpret_cast<z2 *>(p->map() + p->offSY), *dx = reinterpret_cast<z2 *>(p->map() + p->offSX);
     if (!p->cstream && cudaStreamCreateWithFlags(&p->cstream, cudaStreamNonBlocking) != cudaSuccess) {
         p->cstream = nullptr;
         return CRSOLVE_ECUDA;
@@ -416,7 +449,7 @@ int solve_host_pipelined(crsolve_plan_s *p, int k, const crsolve_z *A_host, cons
     cudaEvent_t e = host_event(p, ne++);
     if (!e || cudaEventRecord(e, s) != cudaSuccess || cudaStreamWaitEvent(cs, e, 0) != cudaSuccess)
         return CRSOLVE_ECUDA;
-    if (cudaMemsetAsync(p->ws + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
+    if (cudaMemsetAsync(p->map() + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
         return CRSOLVE_ECUDA;
     int rc;
     // level-0 factor by ranges of chunks, each after its rows of A and B
@@ -493,7 +526,7 @@ int solve_host_pipelined(crsolve_plan_s *p, int k, const crsolve_z *A_host, cons
 // factorisation, so that the reported flags are always the FP64 ones.
 int mixed_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
     const size_t mm = (size_t)p->m * p->m;
-    char *ws = p->ws;
+    const WsMap ws = p->map();
     p->A64 = reinterpret_cast<const crsolve_z *>(A);
     p->B64 = reinterpret_cast<const crsolve_z *>(B);
     p->fallback = false;
@@ -560,7 +593,7 @@ int mixed_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
 // One correction solve d = A~^{-1} r with the mixed factorisation: r (FP64)
 // -> FP32, FP32 down sweep, FP64 coarse levels, FP32 up sweep -> d (FP32).
 int mixed_correction(crsolve_plan_s *p, int k, const z2 *r, cudaStream_t s) {
-    char *ws = p->ws;
+    const WsMap ws = p->map();
     const int64_t mk = (int64_t)p->m * k;
     const int nlev = (int)p->lev.size();
     int rc;
@@ -644,7 +677,7 @@ double mixed_step_cost(int m, int k) {
 }
 
 int mixed_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
-    char *ws = p->ws;
+    const WsMap ws = p->map();
     const int64_t n = p->N * (int64_t)p->m * k;
     unsigned long long *norms = reinterpret_cast<unsigned long long *>(ws + p->offNorms);
     z2 *r = reinterpret_cast<z2 *>(ws + p->offR64);
@@ -694,33 +727,25 @@ int mixed_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     return do_solve(p, k, y, x, s);
 }
 
-}  // namespace
-
-extern "C" {
-
-int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, uint32_t flags,
-                        crsolve_plan *out_plan) {
-    if (!out_plan) return CRSOLVE_EINVAL;
-    *out_plan = nullptr;
-    if (N < 1 || m < 1 || kmax < 1) return CRSOLVE_EINVAL;
-    if (m > CRSOLVE_MAX_M || kmax > CRSOLVE_MAX_K) return CRSOLVE_EUNSUPPORTED;
-    if (precision != CRSOLVE_FP64 && precision != CRSOLVE_MIXED) return CRSOLVE_EUNSUPPORTED;
-    if (flags & ~(uint32_t)(CRSOLVE_PLAN_HOST_STAGING | CRSOLVE_PLAN_ALG1)) return CRSOLVE_EINVAL;
-    const bool alg1 = (flags & CRSOLVE_PLAN_ALG1) != 0;
-    if (alg1 && ((N & (N - 1)) != 0 || precision != CRSOLVE_FP64)) return CRSOLVE_EUNSUPPORTED;
-    crsolve_plan_s *p = new (std::nothrow) crsolve_plan_s();
-    if (!p) return CRSOLVE_ENOMEM;
-    p->N = N; p->m = m; p->kmax = kmax; p->precision = precision; p->flags = flags;
-    p->mt = crs::pick_mt(m);
-    if (cudaGetDevice(&p->device) != cudaSuccess ||
-        cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
-        delete p;
-        return CRSOLVE_ECUDA;
-    }
-    const size_t zsz = sizeof(crsolve_z), mm = (size_t)m * m, mk = (size_t)m * kmax;
-    size_t cur = 0;
+// Workspace layout of a plan (offsets; see WsMap for the two regions).
+void layout(crsolve_plan_s *p) {
+    const int64_t N = p->N;
+    const int m = p->m;
+    const bool alg1 = p->alg1;
+    const uint32_t flags = p->flags;
+    const int precision = p->precision;
+    const size_t zsz = sizeof(crsolve_z), mm = (size_t)m * m, mk = (size_t)m * p->kmax;
+    size_t cur = 0, scur = 0;
+    // region of the keep_levels split: tp = workspace, ts = scratch (the
+    // workspace too when the plan is not split)
+    const bool split = p->keep >= 0;
+    auto tp = [&](size_t bytes) { return take(cur, bytes); };
+    auto ts = [&](size_t bytes) { return split ? (take(scur, bytes) | kScr) : take(cur, bytes); };
+    p->lev.clear();
+    p->lev32.clear();
+    p->alev[0].clear();
+    p->alev[1].clear();
     p->offStatus = take(cur, 256);
-    p->alg1 = alg1;
     if (alg1) {
         int L = 0;
         while ((int64_t(1) << L) < N) ++L;
@@ -752,14 +777,17 @@ int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, u
     while (!alg1) {
         LevelPlan L{};
         L.Nl = Nl; L.no = (Nl + 1) / 2; L.ne = Nl / 2;
-        L.offL = take(cur, L.no * mm * zsz);
-        L.offInv = take(cur, L.no * (size_t)m * sizeof(double));
-        L.offZ = take(cur, L.no * 2 * mm * zsz);
-        L.offR = take(cur, L.no * mk * zsz);
-        L.offAn = take(cur, L.ne * mm * zsz);
-        L.offBn = take(cur, (L.ne > 1 ? L.ne - 1 : 0) * mm * zsz);
-        L.offYn = take(cur, L.ne * mk * zsz);
-        L.offXn = take(cur, L.ne * mk * zsz);
+        // factors of levels < keep (and the level-keep system) persist
+        const bool keep_l = !split || (int)p->lev.size() < p->keep;
+        auto tf = [&](size_t bytes) { return keep_l ? tp(bytes) : ts(bytes); };
+        L.offL = tf(L.no * mm * zsz);
+        L.offInv = tf(L.no * (size_t)m * sizeof(double));
+        L.offZ = tf(L.no * 2 * mm * zsz);
+        L.offR = ts(L.no * mk * zsz);
+        L.offAn = tf(L.ne * mm * zsz);
+        L.offBn = tf((L.ne > 1 ? L.ne - 1 : 0) * mm * zsz);
+        L.offYn = ts(L.ne * mk * zsz);
+        L.offXn = ts(L.ne * mk * zsz);
         p->lev.push_back(L);
         if (Nl == 1) break;
         Nl /= 2;
@@ -768,14 +796,14 @@ int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, u
     // CTA-boundary scratch: at most one m x m (factor) and one m x kmax (solve)
     // per CTA of the largest level
     if (!alg1) {
-        p->offWbd = take(cur, no0 * mm * zsz);
-        p->offCbd = take(cur, no0 * mk * zsz);
+        p->offWbd = ts(no0 * mm * zsz);
+        p->offCbd = ts(no0 * mk * zsz);
     }
     if (flags & CRSOLVE_PLAN_HOST_STAGING) {
-        p->offSA = take(cur, N * mm * zsz);
-        p->offSB = take(cur, (N - 1) * mm * zsz);
-        p->offSY = take(cur, N * mk * zsz);
-        p->offSX = take(cur, N * mk * zsz);
+        p->offSA = ts(N * mm * zsz);
+        p->offSB = ts((N - 1) * mm * zsz);
+        p->offSY = ts(N * mk * zsz);
+        p->offSX = ts(N * mk * zsz);
     }
     if (precision == CRSOLVE_MIXED) {
         // FP32 levels: all levels with more than kMixedCoarse blocks (at least one)
@@ -809,7 +837,60 @@ int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, u
         p->offErr = take(cur, 16);
     }
     p->total = cur;
+    p->scr_total = scur;
+}
+
+}  // namespace
+
+extern "C" {
+
+int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, uint32_t flags,
+                        crsolve_plan *out_plan) {
+    if (!out_plan) return CRSOLVE_EINVAL;
+    *out_plan = nullptr;
+    if (N < 1 || m < 1 || kmax < 1) return CRSOLVE_EINVAL;
+    if (m > CRSOLVE_MAX_M || kmax > CRSOLVE_MAX_K) return CRSOLVE_EUNSUPPORTED;
+    if (precision != CRSOLVE_FP64 && precision != CRSOLVE_MIXED) return CRSOLVE_EUNSUPPORTED;
+    if (flags & ~(uint32_t)(CRSOLVE_PLAN_HOST_STAGING | CRSOLVE_PLAN_ALG1)) return CRSOLVE_EINVAL;
+    const bool alg1 = (flags & CRSOLVE_PLAN_ALG1) != 0;
+    if (alg1 && ((N & (N - 1)) != 0 || precision != CRSOLVE_FP64)) return CRSOLVE_EUNSUPPORTED;
+    crsolve_plan_s *p = new (std::nothrow) crsolve_plan_s();
+    if (!p) return CRSOLVE_ENOMEM;
+    p->N = N; p->m = m; p->kmax = kmax; p->precision = precision; p->flags = flags;
+    p->mt = crs::pick_mt(m);
+    if (cudaGetDevice(&p->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess) {
+        delete p;
+        return CRSOLVE_ECUDA;
+    }
+    p->alg1 = alg1;
+    layout(p);
     *out_plan = p;
+    return CRSOLVE_OK;
+}
+
+int crsolve_plan_keep_levels(crsolve_plan p, int32_t keep) {
+    if (!p || keep < -1 || p->ws || p->scr) return CRSOLVE_EINVAL;
+    if (keep >= 0 && (p->alg1 || p->precision != CRSOLVE_FP64)) return CRSOLVE_EUNSUPPORTED;
+    p->keep = keep;
+    layout(p);
+    p->factored = false;
+    p->coarse_valid = false;
+    return CRSOLVE_OK;
+}
+
+int crsolve_scratch_bytes(crsolve_plan p, size_t *bytes) {
+    if (!p || !bytes) return CRSOLVE_EINVAL;
+    *bytes = p->scr_total;
+    return CRSOLVE_OK;
+}
+
+int crsolve_set_scratch(crsolve_plan p, void *dev_ptr, size_t bytes) {
+    if (!p || p->keep < 0) return CRSOLVE_EINVAL;
+    if (dev_ptr && ((uintptr_t)dev_ptr & 255u)) return CRSOLVE_EINVAL;
+    if (dev_ptr && bytes < p->scr_total) return CRSOLVE_ENOMEM;
+    p->scr = static_cast<char *>(dev_ptr);
+    p->coarse_valid = false;
     return CRSOLVE_OK;
 }
 
@@ -831,22 +912,28 @@ int crsolve_set_workspace(crsolve_plan p, void *dev_ptr, size_t bytes) {
 int crsolve_factor(crsolve_plan p, const crsolve_z *A, const crsolve_z *B, void *stream) {
     if (!p || !A || (p->N > 1 && !B)) return CRSOLVE_EINVAL;
     if (!aligned16(A) || (B && !aligned16(B))) return CRSOLVE_EINVAL;
-    if (!p->ws) return CRSOLVE_ENOMEM;
+    if (!p->ws || (p->keep >= 0 && !p->scr)) return CRSOLVE_ENOMEM;
     int rc = check_device(p);
     if (rc) return rc;
     if ((rc = ensure_prepared(p))) return rc;
     if (p->precision == CRSOLVE_MIXED && p->lT > 0)
         return mixed_factor(p, reinterpret_cast<const z2 *>(A), reinterpret_cast<const z2 *>(B),
                             static_cast<cudaStream_t>(stream));
-    return do_factor(p, reinterpret_cast<const z2 *>(A), reinterpret_cast<const z2 *>(B),
-                     static_cast<cudaStream_t>(stream));
+    p->coarse_valid = false;
+    if ((rc = do_factor(p, reinterpret_cast<const z2 *>(A), reinterpret_cast<const z2 *>(B),
+                        static_cast<cudaStream_t>(stream))))
+        return rc;
+    p->coarse_valid = true;
+    p->lvl0A = reinterpret_cast<const z2 *>(A);
+    p->lvl0B = reinterpret_cast<const z2 *>(B);
+    return CRSOLVE_OK;
 }
 
 int crsolve_solve(crsolve_plan p, int32_t k, const crsolve_z *y, crsolve_z *x, void *stream) {
     if (!p || !y || !x || k < 1) return CRSOLVE_EINVAL;
     if (k > p->kmax) return CRSOLVE_EUNSUPPORTED;
     if (!aligned16(y) || !aligned16(x) || (const void *)y == (const void *)x) return CRSOLVE_EINVAL;
-    if (!p->ws) return CRSOLVE_ENOMEM;
+    if (!p->ws || (p->keep >= 0 && !p->scr)) return CRSOLVE_ENOMEM;
     if (!p->factored) return CRSOLVE_ENOTFACTORED;
     int rc = check_device(p);
     if (rc) return rc;
@@ -854,6 +941,7 @@ int crsolve_solve(crsolve_plan p, int32_t k, const crsolve_z *y, crsolve_z *x, v
     if (p->precision == CRSOLVE_MIXED && p->lT > 0 && !p->fallback)
         return mixed_solve(p, k, reinterpret_cast<const z2 *>(y), reinterpret_cast<z2 *>(x),
                            static_cast<cudaStream_t>(stream));
+    if ((rc = ensure_coarse(p, static_cast<cudaStream_t>(stream)))) return rc;
     return do_solve(p, k, reinterpret_cast<const z2 *>(y), reinterpret_cast<z2 *>(x),
                     static_cast<cudaStream_t>(stream));
 }
@@ -867,12 +955,13 @@ int crsolve_backward(crsolve_plan p, int32_t k, const crsolve_z *x, const crsolv
         return CRSOLVE_EINVAL;
     if ((const void *)gx == (const void *)gy) return CRSOLVE_EINVAL;
     if (p->N == 1) gB = nullptr;
-    if (!p->ws) return CRSOLVE_ENOMEM;
+    if (!p->ws || (p->keep >= 0 && !p->scr)) return CRSOLVE_ENOMEM;
     if (!p->factored) return CRSOLVE_ENOTFACTORED;
     int rc = check_device(p);
     if (rc) return rc;
     if ((rc = ensure_prepared(p))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if ((rc = ensure_coarse(p, s))) return rc;
     if ((rc = do_solve(p, k, reinterpret_cast<const z2 *>(gx), reinterpret_cast<z2 *>(gy), s))) return rc;
     if (!gA && !gB) return CRSOLVE_OK;
     if ((rc = launch(p, CRSOLVE_K_ADJOINT, 0, p->N, s, [&] {
@@ -881,7 +970,7 @@ int crsolve_backward(crsolve_plan p, int32_t k, const crsolve_z *x, const crsolv
                                               reinterpret_cast<z2 *>(gB), p->nsm, s);
          })))
         return rc;
-    const unsigned long long *st = reinterpret_cast<const unsigned long long *>(p->ws + p->offStatus);
+    const unsigned long long *st = reinterpret_cast<const unsigned long long *>(p->map() + p->offStatus);
     const int64_t mm = (int64_t)p->m * p->m;
     if (gA && (rc = launch(p, CRSOLVE_K_NANFILL, 0, p->N, s, [&] {
                    return crs::launch_nan_if_failed(reinterpret_cast<z2 *>(gA), p->N * mm, st, p->nsm, s);
@@ -899,14 +988,18 @@ int crsolve_solve_host(crsolve_plan p, int32_t k, const crsolve_z *A_host, const
     if (!p || !A_host || !y_host || !x_host || (p->N > 1 && !B_host) || k < 1) return CRSOLVE_EINVAL;
     if (!(p->flags & CRSOLVE_PLAN_HOST_STAGING)) return CRSOLVE_EINVAL;
     if (k > p->kmax) return CRSOLVE_EUNSUPPORTED;
-    if (!p->ws) return CRSOLVE_ENOMEM;
+    if (!p->ws || (p->keep >= 0 && !p->scr)) return CRSOLVE_ENOMEM;
     int rc = check_device(p);
     if (rc) return rc;
     if ((rc = ensure_prepared(p))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // the level-0 system is staged in the scratch region: a split plan can
+    // rebuild its coarse levels from level keep >= 1 later, not from level 0
+    p->coarse_valid = true;
+    p->lvl0A = p->lvl0B = nullptr;
     const size_t zsz = sizeof(crsolve_z), mm = (size_t)p->m * p->m, mk = (size_t)p->m * k;
-    z2 *dA = reinterpret_cast<z2 *>(p->ws + p->offSA), *dB = reinterpret_cast<z2 *>(p->ws + p->offSB);
-    z2 *dy = reinterpret_cast<z2 *>(p->ws + p->offSY), *dx = reinterpret_cast<z2 *>(p->ws + p->offSX);
+    z2 *dA = reinterpret_cast<z2 *>(p->map() + p->offSA), *dB = reinterpret_cast<z2 *>(p->map() + p->offSB);
+    z2 *dy = reinterpret_cast<z2 *>(p->map() + p->offSY), *dx = reinterpret_cast<z2 *>(p->map() + p->offSX);
     if (!p->alg1 && p->N > 1) {
         if ((rc = solve_host_pipelined(p, k, A_host, B_host, y_host, x_host, s))) return rc;
     } else {
@@ -922,7 +1015,7 @@ int crsolve_solve_host(crsolve_plan p, int32_t k, const crsolve_z *A_host, const
             return CRSOLVE_ECUDA;
     }
     unsigned long long st = 0;
-    if (cudaMemcpyAsync(&st, p->ws + p->offStatus, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (cudaMemcpyAsync(&st, p->map() + p->offStatus, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return CRSOLVE_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return CRSOLVE_ECUDA;
     return st == CRS_NO_FAIL ? CRSOLVE_OK : CRSOLVE_NOT_PD;
@@ -934,7 +1027,7 @@ int crsolve_info_get(crsolve_plan p, crsolve_info *out, void *stream) {
     if (!p->factored) return CRSOLVE_ENOTFACTORED;
     unsigned long long st = 0;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if (cudaMemcpyAsync(&st, p->ws + p->offStatus, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    if (cudaMemcpyAsync(&st, p->map() + p->offStatus, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess)
         return CRSOLVE_ECUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return CRSOLVE_ECUDA;
     if (st == CRS_NO_FAIL) {
@@ -1058,8 +1151,8 @@ int crsolve_plan_levels(crsolve_plan p, int32_t *nlev, int64_t *sizes) {
 int crsolve_debug_level_system(crsolve_plan p, int32_t level, const crsolve_z **A_l, const crsolve_z **B_l) {
     if (!p || !A_l || !B_l || level < 1 || level >= (int32_t)p->lev.size()) return CRSOLVE_EINVAL;
     if (!p->ws) return CRSOLVE_ENOMEM;
-    *A_l = reinterpret_cast<const crsolve_z *>(p->ws + p->lev[level - 1].offAn);
-    *B_l = reinterpret_cast<const crsolve_z *>(p->ws + p->lev[level - 1].offBn);
+    *A_l = reinterpret_cast<const crsolve_z *>(p->map() + p->lev[level - 1].offAn);
+    *B_l = reinterpret_cast<const crsolve_z *>(p->map() + p->lev[level - 1].offBn);
     return CRSOLVE_OK;
 }
 
