@@ -200,7 +200,9 @@ int crsolve_backward(crsolve_plan p, int32_t k, const crsolve_z *x, const crsolv
  * plan and overlap the level-0 kernels: the level-0 factor starts range by
  * range as the rows of A and B it reads arrive, y is copied while the coarse
  * levels are factored, and x is copied back range by range behind the level-0
- * up sweep.  x is bit-identical to crsolve_factor + crsolve_solve.
+ * up sweep.  x is bit-identical to crsolve_factor + crsolve_solve.  The
+ * factorisation is FP64 for every plan: on a CRSOLVE_MIXED plan, later
+ * crsolve_solve calls use it (FP64) until the next crsolve_factor.
  * Needs a plan created with CRSOLVE_PLAN_HOST_STAGING.  Returns CRSOLVE_OK or
  * CRSOLVE_NOT_PD (then x holds NaN), or a negative error.
  */

@@ -997,6 +997,9 @@ int crsolve_solve_host(crsolve_plan p, int32_t k, const crsolve_z *A_host, const
     // rebuild its coarse levels from level keep >= 1 later, not from level 0
     p->coarse_valid = true;
     p->lvl0A = p->lvl0B = nullptr;
+    // the host path factors in FP64: later crsolve_solve calls on a mixed
+    // plan must use these factors, not FP32 ones from an earlier crsolve_factor
+    if (p->precision == CRSOLVE_MIXED) p->fallback = true;
     const size_t zsz = sizeof(crsolve_z), mm = (size_t)p->m * p->m, mk = (size_t)p->m * k;
     z2 *dA = reinterpret_cast<z2 *>(p->map() + p->offSA), *dB = reinterpret_cast<z2 *>(p->map() + p->offSB);
     z2 *dy = reinterpret_cast<z2 *>(p->map() + p->offSY), *dx = reinterpret_cast<z2 *>(p->map() + p->offSX);

@@ -130,3 +130,47 @@ def test_autograd_keep_levels_gives_identical_gradients(cuda_ok, keep):
         grads.append((tA.grad, tB.grad, ty.grad))
     for a, b in zip(*grads):
         assert torch.equal(a, b)
+
+
+def test_split_plan_host_buffers(cuda_ok):
+    """crsolve_solve_host on a split plan stages A, B, y and x in the scratch;
+    x equals the device path.  With keep >= 1 a later device solve after a new
+    scratch rebuilds the coarse levels from the kept level-keep system; with
+    keep = 0 the staged level-0 system is gone with the scratch, so that solve
+    is refused (CRSOLVE_ENOTFACTORED) instead of reading lost data."""
+    N, m, k = 3000, 8, 4
+    A, B, y = synthetic.gen_system(N, m, k, seed=21)
+    dA, dB, dy = to_dev(A, B, y)
+    ref = crs.Plan(N, m, k)
+    crs.crsolve_factor(ref, dA, dB)
+    x_ref = crs.crsolve_solve(ref, dy)
+    tA, tB, ty = (torch.from_numpy(a).pin_memory() for a in (A, B, y))
+    for keep in (0, 1, 3):
+        plan = crs.Plan(N, m, k, flags=nat.CRSOLVE_PLAN_HOST_STAGING, keep_levels=keep)
+        x, rc = crs.crsolve_solve_host(plan, tA, tB, ty)
+        assert rc == 0 and torch.equal(x, x_ref.cpu()), keep
+        poison = _rebind_elsewhere(plan)
+        if keep == 0:
+            with pytest.raises(nat.CrsolveError):
+                crs.crsolve_solve(plan, dy)
+        else:
+            assert torch.equal(crs.crsolve_solve(plan, dy), x_ref), keep
+        del poison
+
+
+def test_mixed_plan_after_host_solve_uses_its_fp64_factors(cuda_ok):
+    """A mixed plan factored by crsolve_factor on one system and then used by
+    crsolve_solve_host on another: a later crsolve_solve must solve the second
+    system (the host path's FP64 factors), not refine with the first one's."""
+    N, m, k = 500, 8, 2
+    A1, B1, y1 = synthetic.gen_system(N, m, k, seed=31)
+    A2, B2, y2 = synthetic.gen_system(N, m, k, seed=32)
+    d1 = to_dev(A1, B1, y1)
+    plan = crs.Plan(N, m, k, precision=nat.CRSOLVE_MIXED, flags=nat.CRSOLVE_PLAN_HOST_STAGING)
+    crs.crsolve_factor(plan, d1[0], d1[1])
+    x2h, rc = crs.crsolve_solve_host(plan, *(torch.from_numpy(a).pin_memory() for a in (A2, B2, y2)))
+    assert rc == 0
+    xo2, _ = oracle.cr_solve(A2, B2, y2)
+    assert rel_err(x2h.numpy(), xo2) <= 1e-12
+    (dy2,) = to_dev(y2)
+    assert rel_err(crs.crsolve_solve(plan, dy2), xo2) <= 1e-12
