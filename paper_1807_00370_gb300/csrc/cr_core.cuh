@@ -115,15 +115,38 @@ __device__ __forceinline__ void trsm_lower_cta(const C *sL, const R *sInv, C *ba
     const int NT = blockDim.x, tid = threadIdx.x;
     for (int rb = 0; rb < m; rb += BS) {
         const int re = min(rb + BS, m);
+        const int nbr = re - rb;
         for (int e = tid; e < nbh * ncols; e += NT) {
             const int b = e / ncols, col = e - b * ncols;
             const C *Lb = sL + b * TRI;
             const R *ivb = sInv + b * MT;
             C *z = base + b * bstride + col;
-            for (int r = rb; r < re; ++r) {
-                C acc = z[r * ld];
-                for (int s = rb; s < r; ++s) zmsub(acc, Lb[tri(r, s)], z[s * ld]);
-                z[r * ld] = zscale(acc, ivb[r]);
+            if constexpr (sizeof(R) == 4) {
+                // FP32 (latency-bound): the column's rows rb .. re-1 in
+                // registers, so the chain waits on FMAs, not on shared memory
+                C zr[BS];
+#pragma unroll
+                for (int i = 0; i < BS; ++i)
+                    if (i < nbr) zr[i] = z[(rb + i) * ld];
+#pragma unroll
+                for (int i = 0; i < BS; ++i) {
+                    if (i < nbr) {
+                        const C *Lr = Lb + tri(rb + i, rb);
+                        C acc = zr[i];
+#pragma unroll
+                        for (int j = 0; j < i; ++j) zmsub(acc, Lr[j], zr[j]);
+                        zr[i] = zscale(acc, ivb[rb + i]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < BS; ++i)
+                    if (i < nbr) z[(rb + i) * ld] = zr[i];
+            } else {
+                for (int r = rb; r < re; ++r) {
+                    C acc = z[r * ld];
+                    for (int s = rb; s < r; ++s) zmsub(acc, Lb[tri(r, s)], z[s * ld]);
+                    z[r * ld] = zscale(acc, ivb[r]);
+                }
             }
         }
         __syncthreads();
@@ -153,15 +176,36 @@ __device__ __forceinline__ void trsm_lower_h_cta(const C *sL, const R *sInv, C *
     const int NT = blockDim.x, tid = threadIdx.x;
     for (int re = m; re > 0; re -= BS) {
         const int rb = max(re - BS, 0);
+        const int nbr = re - rb;
         for (int e = tid; e < nbh * ncols; e += NT) {
             const int b = e / ncols, col = e - b * ncols;
             const C *Lb = sL + b * TRI;
             const R *ivb = sInv + b * MT;
             C *z = base + b * bstride + col;
-            for (int r = re - 1; r >= rb; --r) {
-                C acc = z[r * ld];
-                for (int s = r + 1; s < re; ++s) zmsub_ca(acc, Lb[tri(s, r)], z[s * ld]);
-                z[r * ld] = zscale(acc, ivb[r]);
+            if constexpr (sizeof(R) == 4) {
+                C zr[BS];
+#pragma unroll
+                for (int i = 0; i < BS; ++i)
+                    if (i < nbr) zr[i] = z[(rb + i) * ld];
+#pragma unroll
+                for (int i = BS - 1; i >= 0; --i) {
+                    if (i < nbr) {
+                        C acc = zr[i];
+#pragma unroll
+                        for (int j = i + 1; j < BS; ++j)
+                            if (j < nbr) zmsub_ca(acc, Lb[tri(rb + j, rb + i)], zr[j]);
+                        zr[i] = zscale(acc, ivb[rb + i]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < BS; ++i)
+                    if (i < nbr) z[(rb + i) * ld] = zr[i];
+            } else {
+                for (int r = re - 1; r >= rb; --r) {
+                    C acc = z[r * ld];
+                    for (int s = r + 1; s < re; ++s) zmsub_ca(acc, Lb[tri(s, r)], z[s * ld]);
+                    z[r * ld] = zscale(acc, ivb[r]);
+                }
             }
         }
         __syncthreads();
@@ -326,19 +370,62 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
 
     // stage the lower triangles of A_2t and A_2t+1, B_{2t-1} (P part) and
     // B_{2t}^H (Q part)
-    for (int e = tid; e < nbh * mm; e += NT) {
-        const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        const int64_t t = t0 + b, pos = 2 * t;
-        if (r >= c) {
-            sL[b * TRI + tri(r, c)] = a.A[pos * mm + rem];
-            if (t < a.ne) {
-                C v = a.A[(pos + 1) * mm + rem];
-                if (r == c) v.y = R(0);
-                sV[b * TRI + tri(r, c)] = v;
+    if constexpr (MT >= 32 && sizeof(R) == 4) {
+        // FP32 large tiles (one or two CTAs per SM, latency-bound): the loads
+        // of U iterations go out together
+        // (into registers) before any store, so their latencies overlap
+        constexpr int U = 8;
+        const int n = nbh * mm;
+        for (int e0 = tid; e0 < n; e0 += U * NT) {
+            C va[U], vv[U], vp[U], vq[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * NT;
+                va[u] = vv[u] = vp[u] = vq[u] = zmk(R(0), R(0));
+                if (e < n) {
+                    const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
+                    const int64_t t = t0 + b, pos = 2 * t;
+                    if (r >= c) {
+                        va[u] = __ldg(a.A + pos * mm + rem);
+                        if (t < a.ne) vv[u] = __ldg(a.A + (pos + 1) * mm + rem);
+                    }
+                    if (pos >= 1) vp[u] = __ldg(a.B + (pos - 1) * mm + rem);
+                    if (pos + 1 < a.Nl) vq[u] = __ldg(a.B + pos * mm + rem);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int e = e0 + u * NT;
+                if (e < n) {
+                    const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
+                    if (r >= c) {
+                        sL[b * TRI + tri(r, c)] = va[u];
+                        if (t0 + b < a.ne) {
+                            C v = vv[u];
+                            if (r == c) v.y = R(0);
+                            sV[b * TRI + tri(r, c)] = v;
+                        }
+                    }
+                    sZ[(b * MT + r) * LDZ + c] = vp[u];
+                    sZ[(b * MT + c) * LDZ + m + r] = zconj(vq[u]);
+                }
             }
         }
-        sZ[(b * MT + r) * LDZ + c] = (pos >= 1) ? a.B[(pos - 1) * mm + rem] : zmk(R(0), R(0));
-        sZ[(b * MT + c) * LDZ + m + r] = (pos + 1 < a.Nl) ? zconj(a.B[pos * mm + rem]) : zmk(R(0), R(0));
+    } else {
+        for (int e = tid; e < nbh * mm; e += NT) {
+            const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
+            const int64_t t = t0 + b, pos = 2 * t;
+            if (r >= c) {
+                sL[b * TRI + tri(r, c)] = a.A[pos * mm + rem];
+                if (t < a.ne) {
+                    C v = a.A[(pos + 1) * mm + rem];
+                    if (r == c) v.y = R(0);
+                    sV[b * TRI + tri(r, c)] = v;
+                }
+            }
+            sZ[(b * MT + r) * LDZ + c] = (pos >= 1) ? a.B[(pos - 1) * mm + rem] : zmk(R(0), R(0));
+            sZ[(b * MT + c) * LDZ + m + r] = (pos + 1 < a.Nl) ? zconj(a.B[pos * mm + rem]) : zmk(R(0), R(0));
+        }
     }
     __syncthreads();
 
@@ -361,10 +448,22 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
                     const int b = e;
                     C *Lb = sL + b * TRI;
                     R d = Lb[tri(c, c)].x;
-                    for (int s = kb; s < c; ++s) {
-                        const C l = Lb[tri(c, s)];
-                        d = fmx(-l.x, l.x, d);
-                        d = fmx(-l.y, l.y, d);
+                    if constexpr (MT >= 32 && sizeof(R) == 4) {
+                        // fixed trip count: the loads are issued ahead of the FMA chain
+                        const C *Lc = Lb + tri(c, kb);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (kb + j < c) {
+                                const C l = Lc[j];
+                                d = fmx(-l.x, l.x, d);
+                                d = fmx(-l.y, l.y, d);
+                            }
+                    } else {
+                        for (int s = kb; s < c; ++s) {
+                            const C l = Lb[tri(c, s)];
+                            d = fmx(-l.x, l.x, d);
+                            d = fmx(-l.y, l.y, d);
+                        }
                     }
                     if (!(d > R(0))) report_fail(a.status, a.level, report_index(a, 2 * (t0 + b)));
                     const R iv = rsq(d);
@@ -374,7 +473,14 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
                     const int e2 = e - dpad, b = e2 / below, r = c + 1 + (e2 - b * below);
                     C *Lb = sL + b * TRI;
                     C u = Lb[tri(r, c)];
-                    for (int s = kb; s < c; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(c, s)]);
+                    if constexpr (MT >= 32 && sizeof(R) == 4) {
+                        const C *Lr = Lb + tri(r, kb), *Lc = Lb + tri(c, kb);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (kb + j < c) zmsub_cb(u, Lr[j], Lc[j]);
+                    } else {
+                        for (int s = kb; s < c; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(c, s)]);
+                    }
                     Lb[tri(r, c)] = u;
                 }
             }
@@ -394,7 +500,14 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
                 const int r = ke + rr, q = ke + qq;
                 C *Lb = sL + b * TRI;
                 C u = Lb[tri(r, q)];
-                for (int s = kb; s < ke; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(q, s)]);
+                if constexpr (sizeof(R) == 4) {
+                    const C *Lr = Lb + tri(r, kb), *Lq = Lb + tri(q, kb);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (kb + j < ke) zmsub_cb(u, Lr[j], Lq[j]);
+                } else {
+                    for (int s = kb; s < ke; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(q, s)]);
+                }
                 Lb[tri(r, q)] = u;
             }
             __syncthreads();
