@@ -356,14 +356,20 @@ def run_adjoint(args):
     for _ in range(max(args.warmup, 3)):
         step()
     torch.cuda.synchronize()
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(1.0)
     launches0 = crs.crsolve_launch_count(plan)
     crs.crsolve_timing_enable(plan, True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sampler.mark(True)
     e0.record(stream)
     for _ in range(args.steps):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    sampler.mark(False)
+    clocks = sampler.stop()
     recs = crs.crsolve_timing_read(plan)
     crs.crsolve_timing_enable(plan, False)
     ms_step = e0.elapsed_time(e1) / args.steps
@@ -384,7 +390,8 @@ def run_adjoint(args):
                      "adjoint_outer_frac": (N * adjoint_flops_per_row(m, k) / (adj_ms * 1e-3) / 1e12 / peak_tf)
                      if adj_ms else None},
         "kernels": {kk: {"ms_per_step": v} for kk, v in by.items()},
-        "gpu_launches": crs.crsolve_launch_count(plan) - launches0, "e2e": None, "cpu_baseline": None,
+        "gpu_launches": crs.crsolve_launch_count(plan) - launches0, "clocks": clocks, "e2e": None,
+        "cpu_baseline": None,
         "keep_levels": adjoint_keep_levels(args, dA, dB, dy, dc, plan.workspace_bytes, ms_step),
     }
     if not args.no_cpu_baseline:
@@ -451,6 +458,10 @@ def run_mixed(args):
     shifts = table.get(name, {"shifts": {"1e+02": 1.0, "1e+04": 1.0, "1e+06": 1.0}})
     stream = torch.cuda.current_stream()
     runs = []
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(1.0)
+    sampler.mark(True)
     for kap in ("1e+02", "1e+04", "1e+06"):
         A, B, y = synthetic.gen_system(N, m, k, seed=MIX_SEED, shift=shifts["shifts"][kap])
         dA, dB, dy = (torch.from_numpy(a).cuda() for a in (A, B, y))
@@ -485,8 +496,9 @@ def run_mixed(args):
         if not args.no_cpu_baseline:
             run["oracle_check"] = mixed_oracle_check(table, kap, m, k)
         runs.append(run)
+    sampler.mark(False)
+    clocks = sampler.stop()
     peak_tf = FP64_PEAK_GFLOPS / 1e3
-    best = min(runs, key=lambda r: r["mixed_ms"])
     line = {
         "metric": "block-rows/s", "value": N / (runs[0]["mixed_ms"] * 1e-3), "unit": "block-rows/s", "n_gpus": 1,
         "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": runs[0]["mixed_ms"],
@@ -495,7 +507,7 @@ def run_mixed(args):
                                         "value_is": "kappa ~ 1e2"},
         "runs": runs,
         "fp64_path_frac_of_peak": N * flops_per_block_row(m, k) / (runs[0]["fp64_ms"] * 1e-3) / 1e12 / peak_tf,
-        "e2e": None, "cpu_baseline": None,
+        "clocks": clocks, "e2e": None, "cpu_baseline": None,
     }
     if not args.no_cpu_baseline:
         small = table.get("mixed_N2p10_m64_k32", {"shifts": {"1e+02": 1.0}})["shifts"]["1e+02"]

@@ -34,7 +34,7 @@ def _mixed(A, B, y):
 
 
 @pytest.mark.parametrize("N,m,k", [(1, 4, 1), (2, 3, 2), (65, 4, 1), (300, 8, 4), (1000, 16, 8), (257, 64, 32),
-                                   (4097, 5, 3)])
+                                   (4097, 5, 3), (129, 32, 16), (77, 40, 3), (200, 57, 20)])
 def test_mixed_matches_oracle(cuda_ok, N, m, k):
     A, B, y = synthetic.gen_system(N, m, k, seed=N * m + k)
     x, info, st = _mixed(A, B, y)
