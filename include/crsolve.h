@@ -197,10 +197,10 @@ int crsolve_backward(crsolve_plan p, int32_t k, const crsolve_z *x, const crsolv
  * from host memory (pinned for full speed) into the plan's staging area,
  * factors, solves, copies x back to host memory and synchronises the stream.
  * For classic plans with N > 1 the copies run on a second stream owned by the
- * plan and overlap the level-0 kernels: the level-0 factor starts range by
- * range as the rows of A and B it reads arrive, y is copied while the coarse
- * levels are factored, and x is copied back range by range behind the level-0
- * up sweep.  x is bit-identical to crsolve_factor + crsolve_solve.  The
+ * plan and overlap the kernels: the level-0 factor starts range by range as
+ * the rows of A and B it reads arrive, followed after each range by the
+ * chunks of levels 1-3 whose rows are complete; y is copied while the rest is
+ * factored, and x is copied back range by range behind the level-0 up sweep.  x is bit-identical to crsolve_factor + crsolve_solve.  The
  * factorisation is FP64 for every plan: on a CRSOLVE_MIXED plan, later
  * crsolve_solve calls use it (FP64) until the next crsolve_factor.
  * Needs a plan created with CRSOLVE_PLAN_HOST_STAGING.  Returns CRSOLVE_OK or

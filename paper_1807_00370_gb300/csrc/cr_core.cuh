@@ -637,15 +637,20 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
 
 // Even block j = c * nb - 1 on the boundary between chunk c-1 and chunk c of
 // a factor level: subtract P^H P of odd block c * nb, left by chunk c in
-// Wbd[c].  Items e = first, first + stride, ... of (chunks - 1) * m(m+1)/2.
+// Wbd[c].  Items e = first, first + stride, ... of (boundaries) * m(m+1)/2;
+// the boundaries are c = 1 .. chunks-1, or with c_count > 0 the range
+// c_begin .. c_begin + c_count - 1 (chunks c-1 and c must both be done).
 template <class R>
 __device__ __forceinline__ void factor_fix_items(const LevelArgsT<R> &a, int64_t first, int64_t stride) {
     using C = cplx_t<R>;
     const int m = a.m, mm = m * m, nl = m * (m + 1) / 2;
-    const int64_t ncta = crs_num_ctas(a.no, a.nb), total = (ncta - 1) * nl;
+    // boundaries c_first .. c_first + nbd - 1 (c_count = 0: all, 1 .. ncta - 1)
+    const int64_t ncta = crs_num_ctas(a.no, a.nb);
+    const int64_t c_first = a.c_count > 0 ? a.c_begin : 1, nbd = a.c_count > 0 ? a.c_count : ncta - 1;
+    const int64_t total = nbd * nl;
     for (int64_t e = first; e < total; e += stride) {
-        const int64_t c = 1 + e / nl;
-        const int f = (int)(e - (c - 1) * nl);
+        const int64_t c = c_first + e / nl;
+        const int f = (int)(e - (c - c_first) * nl);
         const int p = tri_row(f), q = f - p * (p + 1) / 2;
         const int64_t j = c * a.nb - 1;
         C v = zsub(a.An[j * mm + p * m + q], a.Wbd[c * mm + p * m + q]);

@@ -118,7 +118,8 @@ struct LevelArgsT {
     // Chunk range of one launch of the odd-block kernels: chunks c_begin ..
     // c_begin + c_count - 1 (c_count = 0: every chunk of the level).  A level
     // may be run as several such launches, e.g. each as soon as the input
-    // rows it reads have arrived from the host.
+    // rows it reads are complete.  For the factor fix-up kernel the same
+    // fields give the range of chunk boundaries (c_count = 0: 1 .. chunks-1).
     int64_t c_begin, c_count;
 };
 using LevelArgs = LevelArgsT<double>;

@@ -277,9 +277,9 @@ static cudaError_t solve_up_mt(const LevelArgsT<R> &a, cudaStream_t s) {
 
 template <class R>
 static cudaError_t factor_fix_r(const LevelArgsT<R> &a, int nsm, cudaStream_t s) {
-    const int64_t ncta = num_ctas(a.no, a.nb);
-    if (ncta < 2) return cudaSuccess;
-    k_factor_fix<R><<<grid_1d((ncta - 1) * (a.m * (a.m + 1) / 2), nsm), 256, 0, s>>>(a);
+    const int64_t nbd = a.c_count > 0 ? a.c_count : num_ctas(a.no, a.nb) - 1;
+    if (nbd < 1) return cudaSuccess;
+    k_factor_fix<R><<<grid_1d(nbd * (a.m * (a.m + 1) / 2), nsm), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -6,6 +6,7 @@
 // blocks (the next level).  Every block row of the original system is an odd
 // block at exactly one level, so the factorisation does N block Cholesky
 // factorisations in total.
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -420,6 +421,7 @@ int ensure_coarse(crsolve_plan_s *p, cudaStream_t s) {
 // range of the level-0 up sweep still runs.  Every kernel does exactly the
 // work of crsolve_factor + crsolve_solve, so x is bit-identical to theirs.
 constexpr int kHostRanges = 8;
+constexpr int kWaveLevels = 3;   // levels 1 .. 3 follow level 0 as a wavefront
 
 cudaEvent_t host_event(crsolve_plan_s *p, size_t i) {
     while (p->xev.size() <= i) {
@@ -452,15 +454,73 @@ int solve_host_pipelined(crsolve_plan_s *p, int k, const crsolve_z *A_host, cons
     if (cudaMemsetAsync(p->map() + p->offStatus, 0xFF, sizeof(unsigned long long), s) != cudaSuccess)
         return CRSOLVE_ECUDA;
     int rc;
-    // level-0 factor by ranges of chunks, each after its rows of A and B
+    // Factor with a wavefront: level 0 by ranges of chunks, each after its
+    // rows of A and B; after each range, the chunks of levels 1 ..
+    // kWaveLevels whose rows are complete, so the GPU keeps working while the
+    // copies run.  A level-l chunk c reads rows 2 c nb .. 2 (c+1) nb - 1 of the
+    // level-l system; after chunks 0 .. d-1 of level l and the boundaries
+    // between them, rows 0 .. d nb - 2 of level l+1 are complete.  Each wave
+    // level writes its CTA-boundary blocks to a region of its own, so chunks
+    // of interleaved levels never share one; the later levels run after all
+    // of them and reuse the first region.
+    const int nlev = (int)p->lev.size();
+    struct Wave { crs::LevelArgs a; int64_t nc, done, fixed, rows; };
+    std::vector<Wave> w(nlev);
     {
-        crs::LevelArgs a = level_args(p, 0, dA, dB);
-        a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
-        const int64_t nc = crs::num_ctas(a.no, a.nb);
+        z2 *wbd = reinterpret_cast<z2 *>(p->map() + p->offWbd);
+        const int64_t cap = (N + 1) / 2;   // chunks the boundary region holds
+        int64_t used = 0;
+        for (int l = 0; l < nlev; ++l) {
+            Wave &W = w[l];
+            W.a = level_args(p, l, dA, dB);
+            W.a.nb = crs::factor_nb(p->mt, W.a.no, p->nsm);
+            W.nc = crs::num_ctas(W.a.no, W.a.nb);
+            W.done = 0;
+            W.fixed = 1;
+            W.rows = 0;
+            if (l <= kWaveLevels && used + W.nc <= cap) {
+                W.a.Wbd = wbd + used * (int64_t)mm;
+                used += W.nc;
+            } else {
+                W.a.Wbd = wbd;
+            }
+        }
+    }
+    int wave = 0;   // deepest wave level whose boundary region is its own
+    for (int l = 1; l <= kWaveLevels && l < nlev; ++l)
+        if (w[l].a.Wbd != w[0].a.Wbd || w[l].nc == 0) wave = l; else break;
+    // launch the ready chunks of level l (at least min_new unless all are
+    // ready) and the boundaries between done chunks
+    auto advance = [&](int l, int64_t min_new) -> int {
+        Wave &W = w[l];
+        const int64_t ready = W.rows >= W.a.Nl ? W.nc : std::min(W.nc, W.rows / (2 * (int64_t)W.a.nb));
+        if (ready < W.nc && ready - W.done < min_new) return CRSOLVE_OK;
+        int r;
+        if (ready > W.done) {
+            W.a.c_begin = W.done;
+            W.a.c_count = ready - W.done;
+            const int64_t units = std::min(ready * W.a.nb, W.a.no) - W.done * W.a.nb;
+            if ((r = launch(p, CRSOLVE_K_FACTOR_ODD, l, units, s, [&] { return crs::launch_factor_odd(p->mt, W.a, s); })))
+                return r;
+            W.done = ready;
+        }
+        if (W.done > W.fixed) {
+            W.a.c_begin = W.fixed;
+            W.a.c_count = W.done - W.fixed;
+            if ((r = launch(p, CRSOLVE_K_FACTOR_FIX, l, W.done - W.fixed, s,
+                            [&] { return crs::launch_factor_fix(W.a, p->nsm, s); })))
+                return r;
+            W.fixed = W.done;
+        }
+        if (l + 1 < nlev) w[l + 1].rows = W.done == W.nc ? w[l + 1].a.Nl : W.done * W.a.nb - 1;
+        return CRSOLVE_OK;
+    };
+    {
+        const int64_t nc = w[0].nc, nb0 = w[0].a.nb;
         const int G = (int)(nc < kHostRanges ? nc : kHostRanges);
         for (int g = 0; g < G; ++g) {
             const int64_t c0 = range_edge(nc, g, G), c1 = range_edge(nc, g + 1, G);
-            const int64_t r0 = 2 * c0 * a.nb, r1 = (g == G - 1) ? N : 2 * c1 * a.nb;
+            const int64_t r0 = 2 * c0 * nb0, r1 = (g == G - 1) ? N : 2 * c1 * nb0;
             const int64_t b1 = r1 < N - 1 ? r1 : N - 1;
             if (cudaMemcpyAsync(dA + r0 * mm, A_host + r0 * mm, (r1 - r0) * mm * zsz, cudaMemcpyHostToDevice, cs) !=
                 cudaSuccess)
@@ -471,22 +531,18 @@ int solve_host_pipelined(crsolve_plan_s *p, int k, const crsolve_z *A_host, cons
             e = host_event(p, ne++);
             if (!e || cudaEventRecord(e, cs) != cudaSuccess || cudaStreamWaitEvent(s, e, 0) != cudaSuccess)
                 return CRSOLVE_ECUDA;
-            a.c_begin = c0;
-            a.c_count = c1 - c0;
-            const int64_t units = (c1 * a.nb < a.no ? c1 * a.nb : a.no) - c0 * a.nb;
-            if ((rc = launch(p, CRSOLVE_K_FACTOR_ODD, 0, units, s, [&] { return crs::launch_factor_odd(p->mt, a, s); })))
-                return rc;
+            w[0].rows = r1;
+            if ((rc = advance(0, 1))) return rc;
+            for (int l = 1; l <= wave; ++l)
+                if ((rc = advance(l, std::max<int64_t>(1, w[l].nc / kHostRanges)))) return rc;
         }
-        a.c_begin = a.c_count = 0;
-        if (nc > 1 && (rc = launch(p, CRSOLVE_K_FACTOR_FIX, 0, nc - 1, s,
-                                   [&] { return crs::launch_factor_fix(a, p->nsm, s); })))
-            return rc;
     }
-    // y while the coarse levels are factored
+    // y while the rest is factored
     if (cudaMemcpyAsync(dy, y_host, N * mk * zsz, cudaMemcpyHostToDevice, cs) != cudaSuccess) return CRSOLVE_ECUDA;
     cudaEvent_t ey = host_event(p, ne++);
     if (!ey || cudaEventRecord(ey, cs) != cudaSuccess) return CRSOLVE_ECUDA;
-    if ((rc = factor_levels(p, 1, nullptr, nullptr, s))) return rc;
+    for (int l = 0; l < nlev; ++l)
+        if ((rc = advance(l, 0))) return rc;
     p->factored = true;
     if (cudaStreamWaitEvent(s, ey, 0) != cudaSuccess) return CRSOLVE_ECUDA;
     if ((rc = solve_sweeps(p, k, dy, dx, 1, s))) return rc;
