@@ -684,6 +684,57 @@ def run_alg1(args):
         torch.distributed.destroy_process_group()
 
 
+def plain_variant_runs(args, plan, dev):
+    """The other two runs of the plain workload at N = 2^20, m = 8, k = 4: the
+    diagonal shift that makes kappa ~ 1e6 (tests/golden/kappa_shifts.json),
+    and A_{N/2} - 3I (indefinite).  Each: factor + solve time (CUDA events),
+    and the check against the CPU oracle on the whole system (relative error
+    and the a-priori estimate kappa * eta; the breakdown flag and location)."""
+    import torch
+    import oracle
+    import paper_1807_00370_gb300 as crs
+    table = json.load(open(os.path.join(ROOT, "tests", "golden", "kappa_shifts.json")))
+    case = table["plain_N2p20_m8_k4"]
+    out = []
+    stream = torch.cuda.current_stream()
+    for name in ("kappa~1e6", "indefinite A_{N/2} - 3I"):
+        if name.startswith("kappa"):
+            A, B, y = synthetic.gen_system(N_BLOCKS, M, K_RHS, seed=case["seed"], shift=case["shifts"]["1e+06"])
+        else:
+            A, B, y = synthetic.gen_system(N_BLOCKS, M, K_RHS, seed=SEED)
+            A = synthetic.make_indefinite(A)
+        dA, dB, dy = (torch.from_numpy(a).to(dev) for a in (A, B, y))
+        dx = torch.empty_like(dy)
+        for _ in range(2):
+            crs.crsolve_factor(plan, dA, dB)
+            crs.crsolve_solve(plan, dy, dx)
+        torch.cuda.synchronize()
+        steps = 10
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            crs.crsolve_factor(plan, dA, dB)
+            crs.crsolve_solve(plan, dy, dx)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        info = crs.crsolve_info_get(plan)
+        xo, io = oracle.cr_solve(A, B, y)
+        run = {"run": name, "ms_per_step": ms, "value": N_BLOCKS / (ms * 1e-3), "breakdown": info,
+               "breakdown_equals_oracle": info == io}
+        if info["status"] == 0:
+            x = dx.cpu().numpy()
+            eta = residual_eta(dA, dB, dy, dx)
+            run.update({"rel_err_vs_oracle": float(np.linalg.norm(x - xo) / np.linalg.norm(xo)),
+                        "residual_eta": eta, "kappa_estimate": 1e6, "a_priori_kappa_eta": 1e6 * eta,
+                        "bound": 1e-10})
+        else:
+            run["x_all_nan"] = bool(torch.isnan(dx).all().item())
+        out.append(run)
+        del dA, dB, dy, dx
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -797,6 +848,9 @@ def main():
 
     cpu = None
     sample_err = None
+    variants = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and N_BLOCKS == 1 << 20:
+        variants = plain_variant_runs(args, plan, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, cores, desc, (sA, sB, sy, sx) = cpu_oracle_sample()
         cpu = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle", "sample": desc}
@@ -828,6 +882,7 @@ def main():
             "kernels": {k: {"ms_per_step": v["ms"] / args.steps, "launches_per_step": v["launches"] // args.steps}
                         for k, v in by_kind.items()},
             "error": {"residual_eta": eta, "sample_rel_err_vs_oracle": sample_err, "bound": 1e-10},
+            "variants": variants,
             "breakdown": info,
             "gpu_launches": launches,
             "clocks": clocks,
