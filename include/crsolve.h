@@ -36,6 +36,11 @@
  *   - Device memory: the library allocates none for the plan.  The caller
  *     asks for the workspace size, allocates it (e.g. a torch tensor) and
  *     binds it; the plan owns its contents until crsolve_destroy.
+ *   - CUDA graphs: crsolve_factor and crsolve_solve of a CRSOLVE_FP64 plan
+ *     only enqueue kernels and memsets on the stream and can be captured;
+ *     make the plan's first factor call outside the capture (it sets kernel
+ *     attributes).  Mixed-precision plans synchronise and cannot be captured.
+ *   - Tracing: every call and every reduction level is an NVTX range.
  */
 #ifndef CRSOLVE_H
 #define CRSOLVE_H

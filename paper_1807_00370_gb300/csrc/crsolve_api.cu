@@ -9,9 +9,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "crsolve.h"
 #include "cr_launch.h"
@@ -97,6 +100,20 @@ struct crsolve_plan_s {
 };
 
 namespace {
+
+// NVTX range for the lifetime of the object (tracing with Nsight tools;
+// near-free when no tool is attached).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    NvtxRange(const char *what, int level) {
+        char buf[48];
+        snprintf(buf, sizeof buf, "%s level %d", what, level);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
 
 size_t take(size_t &cursor, size_t bytes) {
     const size_t off = cursor;
@@ -333,6 +350,7 @@ int alg1_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
 int factor_levels(crsolve_plan_s *p, int l0, const z2 *A, const z2 *B, cudaStream_t s) {
     int rc;
     for (int l = l0; l < (int)p->lev.size(); ++l) {
+        NvtxRange nv("factor", l);
         crs::LevelArgs a = level_args(p, l, A, B);
         a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
         if ((rc = launch(p, CRSOLVE_K_FACTOR_ODD, l, a.no, s,
@@ -369,6 +387,7 @@ int solve_sweeps(crsolve_plan_s *p, int k, const z2 *y, z2 *x, int l_end, cudaSt
     const int nlev = (int)p->lev.size();
     int rc;
     for (int l = 0; l < nlev; ++l) {
+        NvtxRange nv("solve down", l);
         crs::LevelArgs a = solve_args(p, l, k);
         a.y = (l == 0) ? y : reinterpret_cast<const z2 *>(p->map() + p->lev[l - 1].offYn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s,
@@ -380,6 +399,7 @@ int solve_sweeps(crsolve_plan_s *p, int k, const z2 *y, z2 *x, int l_end, cudaSt
             return rc;
     }
     for (int l = nlev - 1; l >= l_end; --l) {
+        NvtxRange nv("solve up", l);
         crs::LevelArgs a = solve_args(p, l, k);
         a.x = (l == 0) ? x : reinterpret_cast<z2 *>(p->map() + p->lev[l - 1].offXn);
         if ((rc = launch(p, CRSOLVE_K_SOLVE_UP, l, a.no, s,
@@ -966,6 +986,7 @@ int crsolve_set_workspace(crsolve_plan p, void *dev_ptr, size_t bytes) {
 }
 
 int crsolve_factor(crsolve_plan p, const crsolve_z *A, const crsolve_z *B, void *stream) {
+    NvtxRange nv("crsolve_factor");
     if (!p || !A || (p->N > 1 && !B)) return CRSOLVE_EINVAL;
     if (!aligned16(A) || (B && !aligned16(B))) return CRSOLVE_EINVAL;
     if (!p->ws || (p->keep >= 0 && !p->scr)) return CRSOLVE_ENOMEM;
@@ -986,6 +1007,7 @@ int crsolve_factor(crsolve_plan p, const crsolve_z *A, const crsolve_z *B, void 
 }
 
 int crsolve_solve(crsolve_plan p, int32_t k, const crsolve_z *y, crsolve_z *x, void *stream) {
+    NvtxRange nv("crsolve_solve");
     if (!p || !y || !x || k < 1) return CRSOLVE_EINVAL;
     if (k > p->kmax) return CRSOLVE_EUNSUPPORTED;
     if (!aligned16(y) || !aligned16(x) || (const void *)y == (const void *)x) return CRSOLVE_EINVAL;
@@ -1004,6 +1026,7 @@ int crsolve_solve(crsolve_plan p, int32_t k, const crsolve_z *y, crsolve_z *x, v
 
 int crsolve_backward(crsolve_plan p, int32_t k, const crsolve_z *x, const crsolve_z *gx, crsolve_z *gy,
                      crsolve_z *gA, crsolve_z *gB, void *stream) {
+    NvtxRange nv("crsolve_backward");
     if (!p || !x || !gx || !gy || k < 1) return CRSOLVE_EINVAL;
     if (k > p->kmax) return CRSOLVE_EUNSUPPORTED;
     if (!aligned16(x) || !aligned16(gx) || !aligned16(gy) || (gA && !aligned16(gA)) ||
@@ -1041,6 +1064,7 @@ int crsolve_backward(crsolve_plan p, int32_t k, const crsolve_z *x, const crsolv
 
 int crsolve_solve_host(crsolve_plan p, int32_t k, const crsolve_z *A_host, const crsolve_z *B_host,
                        const crsolve_z *y_host, crsolve_z *x_host, void *stream) {
+    NvtxRange nv("crsolve_solve_host");
     if (!p || !A_host || !y_host || !x_host || (p->N > 1 && !B_host) || k < 1) return CRSOLVE_EINVAL;
     if (!(p->flags & CRSOLVE_PLAN_HOST_STAGING)) return CRSOLVE_EINVAL;
     if (k > p->kmax) return CRSOLVE_EUNSUPPORTED;
