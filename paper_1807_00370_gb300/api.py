@@ -295,11 +295,22 @@ def _method_flags(method: str) -> int:
 
 
 def solve(A: torch.Tensor, B: torch.Tensor | None, y: torch.Tensor, check: bool = True,
-          method: str = "classic") -> torch.Tensor:
-    """x = A^{-1} y for one system on the tensors' CUDA device.  method:
+          method: str = "classic", device=None) -> torch.Tensor:
+    """x = A^{-1} y for one system.  CUDA tensors are solved on their device;
+    host tensors go through crsolve_solve_host on `device` (default: the
+    current CUDA device), whose copies overlap the kernels, and x comes back
+    as a host tensor (pin the inputs for full copy speed).  method:
     "classic" (classic cyclic reduction, any N) or "alg1" (the paper's
     Algorithm 1, both halves reduced, N a power of two)."""
     N, m, _ = A.shape
+    if A.device.type == "cpu":
+        A, y = A.contiguous(), y.contiguous()
+        B = None if B is None else B.contiguous()
+        plan = Plan(N, m, y.shape[-1], flags=_method_flags(method) | nat.CRSOLVE_PLAN_HOST_STAGING, device=device)
+        x, rc = crsolve_solve_host(plan, A, B, y)
+        if check and rc != 0:
+            raise NotPositiveDefinite(crsolve_info_get(plan))
+        return x
     plan = Plan(N, m, y.shape[-1], flags=_method_flags(method), device=A.device)
     crsolve_factor(plan, A, B)
     x = crsolve_solve(plan, y)

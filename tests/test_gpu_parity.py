@@ -186,6 +186,19 @@ def test_solve_host_overlapped_equals_device_path(cuda_ok, N, m, k):
     assert rel_err(x_dev, oracle.cr_solve(A, B, y)[0]) <= TOL
 
 
+def test_solve_accepts_host_tensors(cuda_ok):
+    """crs.solve with CPU tensors runs the host-buffer path and returns x on
+    the host, equal to the device path; a breakdown raises NotPositiveDefinite."""
+    A, B, y = synthetic.gen_system(777, 8, 3, seed=77)
+    x = crs.solve(*(torch.from_numpy(a) for a in (A, B, y)))
+    assert x.device.type == "cpu"
+    x_dev, _, _ = run(A, B, y)
+    assert np.array_equal(x.numpy(), x_dev)
+    Ai = synthetic.make_indefinite(A, amount=1e3)
+    with pytest.raises(crs.NotPositiveDefinite):
+        crs.solve(*(torch.from_numpy(a) for a in (Ai, B, y)))
+
+
 def test_solve_host_overlapped_breakdown_gives_nan(cuda_ok):
     N, m = 4000, 8
     for seed in range(20):
