@@ -31,15 +31,21 @@ __device__ __forceinline__ float qnan(float) { return __int_as_float(0x7fc00000)
 
 __device__ __forceinline__ z2 zmk(double re, double im) { return make_double2(re, im); }
 __device__ __forceinline__ c2 zmk(float re, float im) { return make_float2(re, im); }
-template <class C> __device__ __forceinline__ C zconj(C a) { C r = a; r.y = -a.y; return r; }
 template <class C> __device__ __forceinline__ C zsub(C a, C b) { C r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
 template <class C, class R> __device__ __forceinline__ C zscale(C a, R s) { C r; r.x = a.x * s; r.y = a.y * s; return r; }
-// negation by flipping sign bits (integer pipe, no floating-point instruction)
+// Negation by flipping the sign bit on the integer pipe.  The XOR is written
+// in PTX so that the compiler cannot turn it back into a floating-point
+// negation, which it would issue as a DADD on the FP64 pipe, the pipe that
+// bounds the FP64 kernels.  Exact, so results are unchanged.
 __device__ __forceinline__ double dneg_bits(double v) {
-    return __longlong_as_double(__double_as_longlong(v) ^ (long long)0x8000000000000000ull);
+    int hi = __double2hiint(v);
+    const int lo = __double2loint(v);
+    asm("xor.b32 %0, %0, 0x80000000;" : "+r"(hi));
+    return __hiloint2double(hi, lo);
 }
 __device__ __forceinline__ float dneg_bits(float v) { return __int_as_float(__float_as_int(v) ^ (int)0x80000000u); }
 template <class C> __device__ __forceinline__ C zneg(C a) { C r; r.x = dneg_bits(a.x); r.y = dneg_bits(a.y); return r; }
+template <class C> __device__ __forceinline__ C zconj(C a) { C r = a; r.y = dneg_bits(a.y); return r; }
 
 // acc -= a * b
 template <class C> __device__ __forceinline__ void zmsub(C &acc, C a, C b) {
