@@ -572,16 +572,21 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
             const int64_t t = t0 + b;
             if (p < m ? (t == 0) : (2 * t + 1 >= a.Nl)) continue;
             const C *Zb = sZ + b * MT * LDZ + p;
-            R d = R(0);
+            // the Q^H Q diagonal is accumulated straight into V (products
+            // negated by a sign-bit XOR), the P^H P one from zero
+            const bool intoV = p >= m;
+            R *dst = intoV ? &sV[b * TRI + tri(p - m, p - m)].x : nullptr;
+            R d = intoV ? *dst : R(0);
+            const unsigned sg = intoV ? 0x80000000u : 0u;
 #pragma unroll
             for (int s = 0; s < MT; ++s)
                 if (s < m) {
                     const C v = Zb[s * LDZ];
-                    d = fmx(v.x, v.x, d);
-                    d = fmx(v.y, v.y, d);
+                    d = fmx(flip_if(v.x, sg), v.x, d);
+                    d = fmx(flip_if(v.y, sg), v.y, d);
                 }
-            if (p < m) sW[b * TRI + tri(p, p)] = zmk(d, R(0));
-            else sV[b * TRI + tri(p - m, p - m)].x -= d;
+            if (intoV) *dst = d;
+            else sW[b * TRI + tri(p, p)] = zmk(d, R(0));
         } else if (e >= dpadh) {
             const int e2 = e - dpadh, b = e2 / noff, g = e2 - b * noff;
             const int p = tri_row(g) + 1, q = g - p * (p - 1) / 2;   // p > q
@@ -590,17 +595,24 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
             const int kind = (p < m) ? 0 : (q >= m ? 1 : 2);  // P^H P, Q^H Q, Q^H P
             if (kind == 0 ? !hasL : (kind == 1 ? !hasR : !(hasL && hasR))) continue;
             const C *Zb = sZ + b * MT * LDZ;
-            C acc = zmk(R(0), R(0));
+            // Q^H Q is accumulated straight into V and Q^H P into -F, their
+            // products negated by a sign-bit XOR (no FP64 instruction, no
+            // divergence between the kinds); P^H P from zero
+            C *dst = kind == 1 ? &sV[b * TRI + tri(p - m, q - m)] : nullptr;
+            C acc = dst ? *dst : zmk(R(0), R(0));
+            const unsigned sg = kind == 0 ? 0u : 0x80000000u;
 #pragma unroll
             for (int s = 0; s < MT; ++s)
-                if (s < m) zmac_ca(acc, Zb[s * LDZ + p], Zb[s * LDZ + q]);
+                if (s < m) {
+                    const C zp = Zb[s * LDZ + p];
+                    zmac_ca(acc, zmk(flip_if(zp.x, sg), flip_if(zp.y, sg)), Zb[s * LDZ + q]);
+                }
             if (kind == 0) {
                 sW[b * TRI + tri(p, q)] = acc;
             } else if (kind == 1) {
-                C &v = sV[b * TRI + tri(p - m, q - m)];
-                v = zsub(v, acc);
+                *dst = acc;
             } else {
-                a.Bn[(t - 1) * mm + (p - m) * m + q] = zneg(acc);
+                a.Bn[(t - 1) * mm + (p - m) * m + q] = acc;
             }
         }
     }

@@ -44,6 +44,15 @@ __device__ __forceinline__ double dneg_bits(double v) {
     return __hiloint2double(hi, lo);
 }
 __device__ __forceinline__ float dneg_bits(float v) { return __int_as_float(__float_as_int(v) ^ (int)0x80000000u); }
+// Sign flipped when sgn = 0x80000000, unchanged when sgn = 0 (a runtime
+// choice without a branch or a floating-point instruction).
+__device__ __forceinline__ double flip_if(double v, unsigned sgn) {
+    int hi = __double2hiint(v);
+    const int lo = __double2loint(v);
+    asm("xor.b32 %0, %0, %1;" : "+r"(hi) : "r"(sgn));
+    return __hiloint2double(hi, lo);
+}
+__device__ __forceinline__ float flip_if(float v, unsigned sgn) { return __int_as_float(__float_as_int(v) ^ (int)sgn); }
 template <class C> __device__ __forceinline__ C zneg(C a) { C r; r.x = dneg_bits(a.x); r.y = dneg_bits(a.y); return r; }
 template <class C> __device__ __forceinline__ C zconj(C a) { C r = a; r.y = dneg_bits(a.y); return r; }
 
