@@ -50,6 +50,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FP64_FMA_PER_CLK_SM, N_SM, SM_MAX_MHZ = 2, 152, 2070.0
 FP64_PEAK_GFLOPS = FP64_FMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ / 1e3
 # ncu: k_factor_odd<8, double>, level 0 of N = 2^18: dram 537.9 MB read + 624.6 MB written for 2^17 odd blocks
+# (the current build of the kernel)
 TRAFFIC_PER_ODD_BLOCK = (537.9e6 + 624.6e6) / (1 << 17)
 
 
