@@ -782,16 +782,18 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t
             if (p < m ? (t == 0) : (2 * t + 1 >= a.Nl)) continue;
             const C *Rb = sR + b * MT * kc + c;
             const C *Zt = a.Z + t * (int64_t)(m * m2) + p;
-            C acc = zmk(R(0), R(0));
+            // Q^H r is accumulated straight into v, its products negated by a
+            // sign-bit XOR; P^H r from zero
+            C *dst = (p < m) ? &sW[(b * MT + p) * kc + c] : &sV[(b * MT + p - m) * kc + c];
+            C acc = (p < m) ? zmk(R(0), R(0)) : *dst;
+            const unsigned sg = (p < m) ? 0u : 0x80000000u;
 #pragma unroll
             for (int s = 0; s < MT; ++s)
-                if (s < m) zmac_ca(acc, __ldg(Zt + s * m2), Rb[s * kc]);
-            if (p < m) {
-                sW[(b * MT + p) * kc + c] = acc;
-            } else {
-                C &v = sV[(b * MT + p - m) * kc + c];
-                v = zsub(v, acc);
-            }
+                if (s < m) {
+                    const C z = __ldg(Zt + s * m2);
+                    zmac_ca(acc, zmk(flip_if(z.x, sg), flip_if(z.y, sg)), Rb[s * kc]);
+                }
+            *dst = acc;
         }
     }
     __syncthreads();
