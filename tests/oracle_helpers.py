@@ -74,3 +74,48 @@ def brute_force_first_failure(A, B, margin):
         if fails:
             return d, min(fails)
     return None
+
+
+def brute_force_first_failure_classic(A, B, margin):
+    """For classic cyclic reduction on any N: the first (level, 1-based local
+    odd block) whose diagonal block is not positive definite, found without
+    any reduction step.  The level-l system of classic reduction is the dense
+    Schur complement of the whole matrix onto the original blocks
+    2^l, 2*2^l, ..., N_l*2^l (1-based), so the odd block i of level l is
+    diagonal block i of that Schur complement.  At the first level with a
+    failure every failing odd block is listed; the smallest is returned as
+    (level, block, [all failing blocks]).  None if every block passes;
+    ValueError if some block is within `margin` of singular."""
+    N, m, _ = A.shape
+    D = assemble(A, B)
+    level, Nl = 0, N
+    while True:
+        keep = np.arange(1 << level, N + 1, 1 << level) - 1
+        assert len(keep) == Nl
+        S, _, _ = dense_schur(D, keep, m)
+        fails = []
+        for i in range(1, Nl + 1, 2):
+            j = i - 1
+            lam = np.linalg.eigvalsh(S[j * m:(j + 1) * m, j * m:(j + 1) * m]).min()
+            if abs(lam) < margin:
+                raise ValueError("too close to call")
+            if lam < 0:
+                fails.append(i)
+        if fails:
+            return level, min(fails), fails
+        if Nl == 1:
+            return None
+        Nl //= 2
+        level += 1
+
+
+def shift_blocks(A, blocks, excess=0.5):
+    """A copy of A with the Hermitian diagonal blocks at the given 1-based
+    original indices shifted by -(lambda_min + excess) I, so that each of them
+    is indefinite with lambda_min = -excess."""
+    A = A.copy()
+    m = A.shape[1]
+    for b in blocks:
+        lam = np.linalg.eigvalsh(herm_from_lower(A[b - 1])).min()
+        A[b - 1] -= (lam + excess) * np.eye(m)
+    return A

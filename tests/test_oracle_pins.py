@@ -11,7 +11,8 @@ import pytest
 
 import oracle
 import synthetic
-from tests.oracle_helpers import assemble, dense_solve, eta_inf, herm_from_lower, rel_err
+from tests.oracle_helpers import (assemble, brute_force_first_failure_classic, dense_solve, eta_inf,
+                                  herm_from_lower, rel_err, shift_blocks)
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -237,6 +238,59 @@ def test_predicted_breakdown_location(p, m):
             break
     _, info = oracle.cr_solve(Ai, B, y)
     assert info == {"status": 1, "level": p - 1, "block": 1, "orig_block": N // 2}
+
+
+@pytest.mark.parametrize("N,m,blocks,expect", [
+    (16, 3, [11, 5, 3], (0, 3)),     # three odd blocks of level 0 fail: the smallest is reported
+    (32, 2, [20, 12], (2, 3)),       # originals 4*5 and 4*3: even at levels 0 and 1, odd blocks 5, 3 of level 2
+    (37, 4, [37, 9, 25], (0, 9)),    # odd N, the last block (left neighbour only) among the failures
+    (24, 3, [24, 8], (3, 1)),        # level 3 has 3 blocks (originals 8, 16, 24): blocks 1 and 3 fail
+    (32, 2, [12, 27], (0, 27)),      # the first level decides before the index: 27 fails at level 0, 12 at 2
+])
+def test_breakdown_tie_break_smallest_block_of_first_level(N, m, blocks, expect):
+    """Sec. 2 "Determination of Positive Definiteness": a breakdown means the
+    matrix is not positive definite.  Reading for the location when several
+    odd blocks of one level fail: the first level with a failure, then the
+    smallest 1-based local block there.  The expected location is set by
+    construction (each shifted block is indefinite on its own, and its
+    reduced block is that block minus positive semidefinite Schur terms) and
+    confirmed by brute force on the dense matrix (every failing odd block of
+    the first failing level, from Schur complements, no reduction step)."""
+    A, B, y = synthetic.gen_system(N, m, 1, seed=N + 7 * m)
+    A = shift_blocks(A, blocks)
+    level, block, fails = brute_force_first_failure_classic(A, B, margin=1e-6)
+    assert (level, block) == expect
+    assert len(fails) >= 2 or N == 32 and blocks == [12, 27]
+    x, info = oracle.cr_solve(A, B, y)
+    assert info == {"status": 1, "level": level, "block": block, "orig_block": block << level}
+    assert np.isnan(x).all()
+
+
+def test_breakdown_tie_break_random_multi_failures():
+    """Random tiny systems with several shifted diagonal blocks: the oracle's
+    (level, block) equals the brute-force first failure, and at least a few
+    dozen cases have two or more failing odd blocks at that level."""
+    rng = np.random.default_rng(2024)
+    multi = 0
+    for trial in range(240):
+        N = int(rng.integers(2, 33))
+        m = int(rng.integers(1, 5))
+        A, B, y = synthetic.gen_system(N, m, 1, seed=7000 + trial, shift=0.3)
+        A = A.copy()
+        for b in rng.choice(np.arange(N), size=min(int(rng.integers(2, 7)), N), replace=False):
+            A[b] -= float(rng.uniform(0.5, 4.0)) * np.eye(m)
+        try:
+            bf = brute_force_first_failure_classic(A, B, margin=1e-6)
+        except ValueError:
+            continue
+        _, info = oracle.cr_solve(A, B, y)
+        if bf is None:
+            assert info["status"] == 0, (trial, info)
+            continue
+        level, block, fails = bf
+        assert info == {"status": 1, "level": level, "block": block, "orig_block": block << level}, (trial, bf)
+        multi += len(fails) >= 2
+    assert multi >= 30, multi
 
 
 def test_nan_input_reports_breakdown():
