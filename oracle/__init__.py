@@ -49,9 +49,12 @@ class OracleInfo(ctypes.Structure):
 def build(force: bool = False) -> str:
     """Compile cr_oracle.c into _build/libcr_oracle.so (gcc, OpenMP)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(os.path.abspath(__file__)))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".{os.getpid()}.tmp"
-        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off", "-fcx-limited-range",
+        # C99 complex semantics (no -fcx-limited-range): finite products are
+        # the plain formula either way; non-finite ones keep Annex G rules
+        cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-ffp-contract=off",
                "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
