@@ -15,11 +15,17 @@ Prints one JSON line (rank 0).  Extra keys:
   cpu_baseline  the CPU oracle on the host cores on a bounded sample
   clocks        nvidia-smi samples taken during the timed region
 
---workload selects another form: batched (4096 uneven systems in one
-persistent launch), adjoint (factor + solve + crsolve_backward), mixed (FP32
-levels with FP64 refinement at kappa 1e2/1e4/1e6) or alg1 (the paper's
-Algorithm 1 on the plain workload's system, with classic reduction timed
-beside it).  --impl reference times the CPU oracle alone (the reference arm).
+  extra         (one GPU, rank 0; --no-extras skips it) the other forms on the
+                same GPU in the same run, each with its speedup and its error
+                against the CPU oracle: batched (4096 uneven systems in one
+                persistent launch vs the plain path called per system), mixed
+                (FP32 levels + FP64 refinement vs the FP64 path at kappa
+                1e2/1e4/1e6) and adjoint (factor + solve + crsolve_backward)
+
+--workload selects another form as the main line: batched, adjoint, mixed or
+alg1 (the paper's Algorithm 1 on the plain workload's system, with classic
+reduction timed beside it).  --impl reference times the CPU oracle alone on
+the plain workload's full system (the reference arm).
 Under torchrun (N > 1) every rank solves its own independent system (weak
 scaling; the only collectives are the timing barrier and max).
 """
@@ -49,9 +55,39 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # ~1.9 DFMA/clk/SM), 152 SMs, 2070 MHz maximum SM clock
 FP64_FMA_PER_CLK_SM, N_SM, SM_MAX_MHZ = 2, 152, 2070.0
 FP64_PEAK_GFLOPS = FP64_FMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ / 1e3
-# ncu: k_factor_odd<8, double>, level 0 of N = 2^18: dram 537.9 MB read + 624.6 MB written for 2^17 odd blocks
-# (the current build of the kernel)
-TRAFFIC_PER_ODD_BLOCK = (537.9e6 + 624.6e6) / (1 << 17)
+# DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum
+# + dram__bytes_write.sum of k_factor_odd<8, double>, level 0 of N = 2^18, 2^17
+# odd blocks), valid only while the kernel sources are the ones captured: the
+# SHA-256 of the files below at capture time.  Otherwise the line reports null.
+TRAFFIC_CAPTURE = {"bytes_per_odd_block": (537.9e6 + 624.6e6) / (1 << 17),
+                   "sources": ("paper_1807_00370_gb300/csrc/cr_core.cuh", "paper_1807_00370_gb300/csrc/cr_device.cuh",
+                               "paper_1807_00370_gb300/csrc/cr_levels.cu"),
+                   "sha256": None}
+
+
+def captured_traffic_per_odd_block():
+    """The captured bytes per odd block if the kernel sources still hash to the
+    captured ones, else None."""
+    import hashlib
+    if not TRAFFIC_CAPTURE["sha256"]:
+        return None
+    h = hashlib.sha256()
+    for rel in TRAFFIC_CAPTURE["sources"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return TRAFFIC_CAPTURE["bytes_per_odd_block"] if h.hexdigest() == TRAFFIC_CAPTURE["sha256"] else None
+
+
+def fp64_probe():
+    """Measured FP64 FMA rate of this GPU (crsolve_peak_probe): TFLOP/s, FMA
+    lanes per SM per clock, and the SM clock the probe ran at."""
+    import paper_1807_00370_gb300 as crs
+    try:
+        r = crs.crsolve_peak_probe("fp64")
+    except Exception as e:  # noqa: BLE001 - reported, not fatal
+        return {"failed": str(e)}
+    return {"tflops": r["gflops"] / 1e3, "fma_per_clk_sm": r["fma_per_clk_sm"], "sm_mhz": r["sm_mhz"],
+            "tflops_at_max_clock": 2.0 * r["fma_per_clk_sm"] * N_SM * SM_MAX_MHZ / 1e6}
 
 
 def flops_factor_per_odd_block(m: int) -> float:
@@ -170,6 +206,29 @@ def cpu_oracle_sample(seconds: float = 12.0, n_sample: int = 1 << 17):
     return value, cores, desc, (A, B, y, x)
 
 
+def cpu_oracle_single_thread(seconds: float = 5.0, n_sample: int = 1 << 14):
+    """The same oracle on one host core (OpenMP set to one thread), on a
+    smaller sample of the same workload."""
+    import oracle
+    A, B, y = synthetic.gen_system(n_sample, M, K_RHS, seed=SEED)
+    cores = oracle.max_threads()
+    oracle.set_threads(1)
+    try:
+        oracle.cr_solve(A, B, y)
+        reps, t0 = 0, time.perf_counter()
+        while True:
+            oracle.cr_solve(A, B, y)
+            reps += 1
+            el = time.perf_counter() - t0
+            if el >= seconds:
+                break
+    finally:
+        oracle.set_threads(cores)
+    return {"value": n_sample * reps / el, "unit": "block-rows/s", "cores": 1, "kind": "oracle",
+            "sample": f"{reps} single-thread oracle solves of an N=2^{n_sample.bit_length() - 1} system, "
+                      f"m={M}, k={K_RHS}, {el:.1f} s"}
+
+
 def oracle_rate(systems, seconds: float = 10.0, backward: bool = False):
     """The CPU oracle as it stands, on the host cores, over a list of
     (A, B, y[, c]) systems, repeated for about `seconds`; block-rows/s."""
@@ -193,39 +252,66 @@ def run_reference(args):
     if rank != 0:
         return
     import oracle
-    n_sample = 1 << 16
-    A, B, y = synthetic.gen_system(n_sample, M, K_RHS, seed=SEED)
+    n = 1 << args.log2n
+    A, B, y = synthetic.gen_system(n, M, K_RHS, seed=SEED)
     for _ in range(args.warmup):
         oracle.cr_solve(A, B, y)
     t0 = time.perf_counter()
     for _ in range(args.steps):
         oracle.cr_solve(A, B, y)
     el = time.perf_counter() - t0
-    value = n_sample * args.steps / el
+    value = n * args.steps / el
     cores = oracle.max_threads()
+    workload = WORKLOAD.replace("N=2^20", f"N=2^{args.log2n}")
     line = {"impl": "reference", "metric": "block-rows/s", "value": value, "unit": "block-rows/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"N=2^16 blocks per step (bounded sample of the workload)"},
+            "config": {"workload": workload, "N": n, "m": M, "k": K_RHS, "seed": SEED},
             "cpu_baseline": {"value": value, "unit": "block-rows/s", "cores": cores, "kind": "oracle",
-                             "sample": f"{args.steps} oracle solves of an N=2^16, m={M}, k={K_RHS} system"},
+                             "sample": f"{args.steps} oracle solves (factor+solve) of the whole N=2^{args.log2n}, "
+                                       f"m={M}, k={K_RHS} system, {el:.1f} s"},
             "e2e": {"value": value, "unit": "block-rows/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
+
+# steps of the batched / mixed / adjoint measurements inside the default run
+# (the adjoint step is short and takes four times as many)
+EXTRA_STEPS, EXTRA_WARMUP = 3, 1
 
 BATCH_SEED = 3003
 BATCH_WORKLOAD = ("batched CR: 4096 independent HPD block-tridiagonal systems in one persistent launch, "
                   "N ~ U[16, 4096], m in {4, 8, 16, 32}, k ~ U[1, 16], complex128")
 
 
-def run_batched(args):
+def batched_residual_eta(b, A, B, y, x) -> float:
+    """Worst max-norm backward error over every system of a batch (torch ops
+    on the measurement side)."""
+    import torch
+    worst = 0.0
+    with torch.no_grad():
+        for i in range(len(b.Ns)):
+            a, bb, xi = b.system_view(i, A, B, x)
+            yi = b.system_view(i, A, B, y)[2]
+            Ah = torch.tril(a, -1)
+            Ah = Ah + Ah.conj().transpose(1, 2) + torch.diag_embed(torch.diagonal(a, dim1=1, dim2=2).real.to(a.dtype))
+            r = yi - torch.bmm(Ah, xi)
+            if len(bb):
+                r[1:] -= torch.bmm(bb, xi[:-1])
+                r[:-1] -= torch.bmm(bb.conj().transpose(1, 2), xi[1:])
+            nA = (Ah.abs().sum(2).max() + 2 * (bb.abs().sum(2).max() if len(bb) else 0)).item()
+            worst = max(worst, (r.abs().amax() / (nA * xi.abs().amax())).item())
+    return worst
+
+
+def measure_batched(steps: int, warmup: int, nsys: int = 4096, with_oracle: bool = True,
+                    cpu_seconds: float = 10.0) -> dict:
     """4096 uneven systems (seed 3003): one persistent launch replayed as a CUDA
-    graph, against the plain single-system path called per system."""
+    graph with autotuned tiles, against the plain single-system path called
+    per system on the same GPU; sampled systems against the oracle and every
+    system by its residual."""
     import torch
     import paper_1807_00370_gb300 as crs
-    torch.cuda.set_device(0)
-    nsys = args.nsys
     Ns, ms, ks = synthetic.gen_batch_shapes(4096, seed=BATCH_SEED)
     Ns, ms, ks = Ns[:nsys], ms[:nsys], ks[:nsys]
     A, B, y = synthetic.gen_batch_device(Ns, ms, ks, seed=BATCH_SEED)
@@ -236,22 +322,16 @@ def run_batched(args):
     rows = int(Ns.sum())
     flops = float((Ns * (25.33 * ms.astype(float) ** 3 + 40.0 * ms.astype(float) ** 2 * ks)).sum())
     stream = torch.cuda.current_stream()
-    for _ in range(max(args.warmup, 1)):
+    for _ in range(max(warmup, 1)):
         crs.crsolve_batch_graph_launch(b, A, B, y, x)
     torch.cuda.synchronize()
-    sampler = ClockSampler(0)
-    sampler.start()
-    time.sleep(1.0)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler.mark(True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for _ in range(steps):
         crs.crsolve_batch_graph_launch(b, A, B, y, x)
     e1.record(stream)
     torch.cuda.synchronize()
-    sampler.mark(False)
-    clocks = sampler.stop()
-    ms_step = e0.elapsed_time(e1) / args.steps
+    ms_step = e0.elapsed_time(e1) / steps
     infos = crs.crsolve_batch_info(b)
     # the plain path: one plan per system, all on the same stream
     xp = torch.empty_like(y)
@@ -266,10 +346,9 @@ def run_batched(args):
     ms_plain = e0.elapsed_time(e1)
     same = bool(torch.equal(x, xp))
     peak_tf = FP64_PEAK_GFLOPS / 1e3
-    line = {
-        "metric": "block-rows/s", "value": rows / (ms_step * 1e-3), "unit": "block-rows/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+    out = {
+        "metric": "block-rows/s", "value": rows / (ms_step * 1e-3), "unit": "block-rows/s",
+        "ms_per_step": ms_step, "steps": steps, "warmup": max(warmup, 1),
         "config": {"workload": BATCH_WORKLOAD, "systems": len(Ns), "block_rows": rows, "seed": BATCH_SEED,
                    "slots": b.nslots, "l2": "inputs larger than L2, no flush",
                    "tiles": {str(k): v for k, v in b.tiles.items()}, "autotune_s": t_tune},
@@ -279,16 +358,55 @@ def run_batched(args):
         "speedup_vs_plain": {"plain_ms": ms_plain, "batched_ms": ms_step, "speedup": ms_plain / ms_step,
                              "bitwise_equal": same},
         "breakdown_count": sum(1 for r in infos if r["status"]),
-        "gpu_launches": args.steps, "clocks": clocks, "e2e": None, "cpu_baseline": None,
+        "gpu_launches": steps,
     }
-    if not args.no_cpu_baseline:
+    err = {"residual_eta_worst": batched_residual_eta(b, A, B, y, x), "bound": 1e-10}
+    if with_oracle:
+        import oracle
         rng = np.random.default_rng(0)
-        pick = rng.choice(len(Ns), 32, replace=False)
-        sample = [tuple(t.cpu().numpy() for t in b.system_view(int(i), A, B, y)) for i in pick]
-        v, cores, reps, el = oracle_rate(sample)
-        line["cpu_baseline"] = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{reps} passes over 32 randomly chosen systems of the batch "
-                                          f"({sum(s[0].shape[0] for s in sample)} block rows), {el:.1f} s"}
+        pick = []
+        for cls in (4, 8, 16, 32):
+            idx = np.flatnonzero(ms == cls)
+            if len(idx):
+                pick += [int(i) for i in rng.choice(idx, min(2, len(idx)), replace=False)]
+        worst, flags = 0.0, True
+        for i in pick:
+            a, bb, yy = (t.cpu().numpy() for t in b.system_view(i, A, B, y))
+            xo, io = oracle.cr_solve(a, bb, yy)
+            xi = b.system_view(i, A, B, x)[2].cpu().numpy()
+            worst = max(worst, float(np.linalg.norm(xi - xo) / np.linalg.norm(xo)))
+            flags = flags and infos[i] == io
+        err.update({"rel_err_vs_oracle_max": worst, "flags_equal": flags,
+                    "oracle_systems": [f"#{i} N={Ns[i]} m={ms[i]} k={ks[i]}" for i in pick]})
+        sample = [tuple(t.cpu().numpy() for t in b.system_view(int(i), A, B, y))
+                  for i in rng.choice(len(Ns), 32, replace=False)]
+        v, cores, reps, el = oracle_rate(sample, seconds=cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{reps} passes over 32 randomly chosen systems of the batch "
+                                         f"({sum(s_[0].shape[0] for s_ in sample)} block rows), {el:.1f} s"}
+    out["error"] = err
+    b.close()
+    del A, B, y, x, xp
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_batched(args):
+    import torch
+    torch.cuda.set_device(0)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(1.0)
+    sampler.mark(True)
+    res = measure_batched(args.steps, args.warmup, args.nsys, with_oracle=not args.no_cpu_baseline)
+    sampler.mark(False)
+    line = {"metric": res["metric"], "value": res["value"], "unit": res["unit"], "n_gpus": 1,
+            "steps": res["steps"], "warmup": res["warmup"], "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
+            "data": "synthetic"}
+    line.update({k: v for k, v in res.items() if k not in line and k != "metric"})
+    line.update({"clocks": sampler.stop(), "e2e": None})
+    line.setdefault("cpu_baseline", None)
     print(json.dumps(line), flush=True)
 
 
@@ -337,10 +455,12 @@ def adjoint_keep_levels(args, dA, dB, dy, dc, full_bytes, full_ms):
     return out
 
 
-def run_adjoint(args):
+def measure_adjoint(steps: int, warmup: int, with_oracle: bool = True, keep_levels: bool = True,
+                    cpu_seconds: float = 10.0) -> dict:
+    """Forward + backward (factor, solve, crsolve_backward) at N = 2^16, m = 16,
+    k = 8; gradients against the oracle's adjoint on the whole system."""
     import torch
     import paper_1807_00370_gb300 as crs
-    torch.cuda.set_device(0)
     N, m, k = ADJ_N, ADJ_M, ADJ_K
     A, B, y = synthetic.gen_system(N, m, k, seed=ADJ_SEED)
     c = synthetic.gen_cotangent(N, m, k, seed=ADJ_SEED)
@@ -354,36 +474,29 @@ def run_adjoint(args):
         crs.crsolve_solve(plan, dy, x)
         return crs.crsolve_backward(plan, x, dc)
 
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 3)):
         step()
     torch.cuda.synchronize()
-    sampler = ClockSampler(0)
-    sampler.start()
-    time.sleep(1.0)
     launches0 = crs.crsolve_launch_count(plan)
     crs.crsolve_timing_enable(plan, True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    sampler.mark(True)
     e0.record(stream)
-    for _ in range(args.steps):
-        step()
+    for _ in range(steps):
+        grads = step()
     e1.record(stream)
     torch.cuda.synchronize()
-    sampler.mark(False)
-    clocks = sampler.stop()
     recs = crs.crsolve_timing_read(plan)
     crs.crsolve_timing_enable(plan, False)
-    ms_step = e0.elapsed_time(e1) / args.steps
-    adj_ms = sum(r[3] for r in recs if r[0] == "adjoint_outer") / args.steps
+    ms_step = e0.elapsed_time(e1) / steps
+    adj_ms = sum(r[3] for r in recs if r[0] == "adjoint_outer") / steps
     flops = N * (flops_per_block_row(m, k) + flops_solve_per_odd_block(m, k) + adjoint_flops_per_row(m, k))
     peak_tf = FP64_PEAK_GFLOPS / 1e3
     by = {}
     for kind, _, _, kms in recs:
-        by[kind] = by.get(kind, 0.0) + kms / args.steps
-    line = {
-        "metric": "block-rows/s", "value": N / (ms_step * 1e-3), "unit": "block-rows/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)", "data": "synthetic",
+        by[kind] = by.get(kind, 0.0) + kms / steps
+    out = {
+        "metric": "block-rows/s", "value": N / (ms_step * 1e-3), "unit": "block-rows/s",
+        "ms_per_step": ms_step, "steps": steps, "warmup": max(warmup, 3),
         "config": {"workload": ADJ_WORKLOAD, "N": N, "m": m, "k": k, "seed": ADJ_SEED},
         "roofline": {"bound": "alu", "kernel": "whole forward + backward step",
                      "achieved": flops / (ms_step * 1e-3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
@@ -391,16 +504,52 @@ def run_adjoint(args):
                      "adjoint_outer_frac": (N * adjoint_flops_per_row(m, k) / (adj_ms * 1e-3) / 1e12 / peak_tf)
                      if adj_ms else None},
         "kernels": {kk: {"ms_per_step": v} for kk, v in by.items()},
-        "gpu_launches": crs.crsolve_launch_count(plan) - launches0, "clocks": clocks, "e2e": None,
-        "cpu_baseline": None,
-        "keep_levels": adjoint_keep_levels(args, dA, dB, dy, dc, plan.workspace_bytes, ms_step),
+        "gpu_launches": crs.crsolve_launch_count(plan) - launches0,
     }
-    if not args.no_cpu_baseline:
+    if with_oracle:
+        import oracle
+        xo, io = oracle.cr_solve(A, B, y)
+        gyo, gAo, gBo, st = oracle.cr_backward(A, B, xo, c)
+        gy, gA, gB = (g.cpu().numpy() for g in grads)
+
+        def rel(a, b):
+            return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+        out["error"] = {"x": rel(x.cpu().numpy(), xo), "gy": rel(gy, gyo), "gA": rel(gA, gAo), "gB": rel(gB, gBo),
+                        "flags_equal": crs.crsolve_info_get(plan) == io, "bound": 1e-10,
+                        "reference": "oracle solve + adjoint on the whole system"}
         sA, sB, sy = synthetic.gen_system(1 << 12, m, k, seed=ADJ_SEED)
         sc = synthetic.gen_cotangent(1 << 12, m, k, seed=ADJ_SEED)
-        v, cores, reps, el = oracle_rate([(sA, sB, sy, sc)], backward=True)
-        line["cpu_baseline"] = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{reps} oracle solve + backward of an N=2^12, m={m}, k={k} system, {el:.1f} s"}
+        v, cores, reps, el = oracle_rate([(sA, sB, sy, sc)], seconds=cpu_seconds, backward=True)
+        out["cpu_baseline"] = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{reps} oracle solve + backward of an N=2^12, m={m}, k={k} system, {el:.1f} s"}
+    if keep_levels:
+        class _A:
+            pass
+        a = _A()
+        a.steps = steps
+        out["keep_levels"] = adjoint_keep_levels(a, dA, dB, dy, dc, plan.workspace_bytes, ms_step)
+    plan.close()
+    del dA, dB, dy, dc, x
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_adjoint(args):
+    import torch
+    torch.cuda.set_device(0)
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(1.0)
+    sampler.mark(True)
+    res = measure_adjoint(args.steps, args.warmup, with_oracle=not args.no_cpu_baseline)
+    sampler.mark(False)
+    line = {"metric": res["metric"], "value": res["value"], "unit": res["unit"], "n_gpus": 1,
+            "steps": res["steps"], "warmup": res["warmup"], "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
+            "data": "synthetic"}
+    line.update({k: v for k, v in res.items() if k not in line and k != "metric"})
+    line.update({"clocks": sampler.stop(), "e2e": None})
+    line.setdefault("cpu_baseline", None)
     print(json.dumps(line), flush=True)
 
 
@@ -423,98 +572,116 @@ def residual_eta(dA, dB, dy, dx) -> float:
         return (r.abs().amax() / (normA * dx.abs().amax())).item()
 
 
-def mixed_oracle_check(table, kap, m, k):
-    """Relative error of the mixed form against the CPU oracle on the N = 2^10
-    system with the same kappa (the oracle solves it in ~0.1 s)."""
-    import torch
-    import oracle
-    import paper_1807_00370_gb300 as crs
-    from paper_1807_00370_gb300 import _native as nat
-    case = table.get("mixed_N2p10_m64_k32")
-    if case is None:
-        return None
-    n = case["N"]
-    A, B, y = synthetic.gen_system(n, m, k, seed=case["seed"], shift=case["shifts"][kap])
-    dA, dB, dy = (torch.from_numpy(a).cuda() for a in (A, B, y))
-    plan = crs.Plan(n, m, k, precision=nat.CRSOLVE_MIXED)
-    crs.crsolve_factor(plan, dA, dB)
-    x = crs.crsolve_solve(plan, dy).cpu().numpy()
-    xo, info = oracle.cr_solve(A, B, y)
-    return {"N": n, "rel_err_vs_oracle": float(np.linalg.norm(x - xo) / np.linalg.norm(xo)),
-            "flags_equal": crs.crsolve_info_get(plan) == info, "refinement": crs.crsolve_mixed_stats(plan)}
-
-
-def run_mixed(args):
-    """For each kappa: the mixed form and the plain FP64 path on the same system."""
+def measure_mixed(steps: int, warmup: int, log2n: int = 14, with_oracle: bool = True, cpu_seconds: float = 10.0):
+    """For each kappa: the mixed form and the plain FP64 path on the same
+    system and GPU; the mixed solution against the oracle on the whole
+    system."""
     import torch
     import paper_1807_00370_gb300 as crs
     from paper_1807_00370_gb300 import _native as nat
-    torch.cuda.set_device(0)
-    N, m, k = MIX_N, MIX_M, MIX_K
-    name = "mixed_N2p14_m64_k32"
-    if args.log2n != 20 and args.log2n != 14:          # smaller cases are for profiling only
-        N = 1 << args.log2n
-        name = f"mixed_N2p{args.log2n}_m64_k32"
+    N, m, k = 1 << log2n, MIX_M, MIX_K
+    name = f"mixed_N2p{log2n}_m64_k32"
     table = json.load(open(os.path.join(ROOT, "tests", "golden", "kappa_shifts.json")))
     shifts = table.get(name, {"shifts": {"1e+02": 1.0, "1e+04": 1.0, "1e+06": 1.0}})
     stream = torch.cuda.current_stream()
     runs = []
-    sampler = ClockSampler(0)
-    sampler.start()
-    time.sleep(1.0)
-    sampler.mark(True)
     for kap in ("1e+02", "1e+04", "1e+06"):
         A, B, y = synthetic.gen_system(N, m, k, seed=MIX_SEED, shift=shifts["shifts"][kap])
         dA, dB, dy = (torch.from_numpy(a).cuda() for a in (A, B, y))
         res = {}
-        for name, prec in (("mixed", nat.CRSOLVE_MIXED), ("fp64", nat.CRSOLVE_FP64)):
+        for pname, prec in (("mixed", nat.CRSOLVE_MIXED), ("fp64", nat.CRSOLVE_FP64)):
             plan = crs.Plan(N, m, k, precision=prec)
             x = torch.empty_like(dy)
-            for _ in range(max(args.warmup, 1)):
+            for _ in range(max(warmup, 1)):
                 crs.crsolve_factor(plan, dA, dB)
                 crs.crsolve_solve(plan, dy, x)
             torch.cuda.synchronize()
             crs.crsolve_timing_enable(plan, True)
+            launches0 = crs.crsolve_launch_count(plan)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            for _ in range(args.steps):
+            for _ in range(steps):
                 crs.crsolve_factor(plan, dA, dB)
                 crs.crsolve_solve(plan, dy, x)
             e1.record(stream)
             torch.cuda.synchronize()
             by = {}
             for kind, _, _, kms in crs.crsolve_timing_read(plan):
-                by[kind] = round(by.get(kind, 0.0) + kms / args.steps, 3)
+                by[kind] = round(by.get(kind, 0.0) + kms / steps, 3)
             crs.crsolve_timing_enable(plan, False)
-            res[name] = {"ms": e0.elapsed_time(e1) / args.steps, "x": x, "kernels_ms": by,
-                         "stats": crs.crsolve_mixed_stats(plan) if prec == nat.CRSOLVE_MIXED else None}
+            res[pname] = {"ms": e0.elapsed_time(e1) / steps, "x": x, "kernels_ms": by,
+                          "launches": (crs.crsolve_launch_count(plan) - launches0) // steps,
+                          "info": crs.crsolve_info_get(plan),
+                          "stats": crs.crsolve_mixed_stats(plan) if prec == nat.CRSOLVE_MIXED else None}
+            plan.close()
         err = float((torch.linalg.norm(res["mixed"]["x"] - res["fp64"]["x"]) / torch.linalg.norm(res["fp64"]["x"])).item())
         run = {"kappa": float(kap), "shift": shifts["shifts"][kap], "mixed_ms": res["mixed"]["ms"],
                "fp64_ms": res["fp64"]["ms"], "speedup": res["fp64"]["ms"] / res["mixed"]["ms"],
                "rel_err_vs_fp64_path": err, "residual_eta_mixed": residual_eta(dA, dB, dy, res["mixed"]["x"]),
-               "refinement": res["mixed"]["stats"],
+               "refinement": res["mixed"]["stats"], "launches_per_step": res["mixed"]["launches"],
                "mixed_kernels_ms": res["mixed"]["kernels_ms"], "fp64_kernels_ms": res["fp64"]["kernels_ms"]}
-        if not args.no_cpu_baseline:
-            run["oracle_check"] = mixed_oracle_check(table, kap, m, k)
+        if kap == "1e+02":
+            # the refinement's FP64-accurate residual: tensor-core splitting against the FP64 pipe
+            rt = {}
+            for meth in ("split", "fp64"):
+                rr = crs.crsolve_residual(dA, dB, res["mixed"]["x"], dy, method=meth)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(5):
+                    crs.crsolve_residual(dA, dB, res["mixed"]["x"], dy, method=meth, r=rr)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                rt[meth] = {"ms": e0.elapsed_time(e1) / 5, "r": rr}
+            run["residual_ms"] = {"split": rt["split"]["ms"], "fp64": rt["fp64"]["ms"],
+                                  "speedup": rt["fp64"]["ms"] / rt["split"]["ms"],
+                                  "max_abs_diff": float((rt["split"]["r"] - rt["fp64"]["r"]).abs().max().item()),
+                                  "max_abs_residual": float(rt["fp64"]["r"].abs().max().item())}
+            del rt
+        if with_oracle:
+            import oracle
+            xo, io = oracle.cr_solve(A, B, y)
+            xm = res["mixed"]["x"].cpu().numpy()
+            run["rel_err_vs_oracle"] = float(np.linalg.norm(xm - xo) / np.linalg.norm(xo))
+            run["flags_equal_oracle"] = res["mixed"]["info"] == io
+            run["bound"] = 1e-10
         runs.append(run)
-    sampler.mark(False)
-    clocks = sampler.stop()
+        del dA, dB, dy, res
+        torch.cuda.empty_cache()
     peak_tf = FP64_PEAK_GFLOPS / 1e3
-    line = {
-        "metric": "block-rows/s", "value": N / (runs[0]["mixed_ms"] * 1e-3), "unit": "block-rows/s", "n_gpus": 1,
-        "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": runs[0]["mixed_ms"],
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 fine levels / c128",
-        "data": "synthetic", "config": {"workload": MIX_WORKLOAD, "N": N, "m": m, "k": k, "seed": MIX_SEED,
-                                        "value_is": "kappa ~ 1e2"},
-        "runs": runs,
-        "fp64_path_frac_of_peak": N * flops_per_block_row(m, k) / (runs[0]["fp64_ms"] * 1e-3) / 1e12 / peak_tf,
-        "clocks": clocks, "e2e": None, "cpu_baseline": None,
-    }
-    if not args.no_cpu_baseline:
+    out = {"metric": "block-rows/s", "value": N / (runs[0]["mixed_ms"] * 1e-3), "unit": "block-rows/s",
+           "ms_per_step": runs[0]["mixed_ms"], "steps": steps, "warmup": max(warmup, 1),
+           "config": {"workload": MIX_WORKLOAD.replace("N=2^14", f"N=2^{log2n}"), "N": N, "m": m, "k": k,
+                      "seed": MIX_SEED, "value_is": "kappa ~ 1e2"},
+           "speedup_vs_fp64": {r["kappa"]: r["speedup"] for r in runs},
+           "runs": runs,
+           "fp64_path_frac_of_peak": N * flops_per_block_row(m, k) / (runs[0]["fp64_ms"] * 1e-3) / 1e12 / peak_tf}
+    if with_oracle:
         small = table.get("mixed_N2p10_m64_k32", {"shifts": {"1e+02": 1.0}})["shifts"]["1e+02"]
-        v, cores, reps, el = oracle_rate([synthetic.gen_system(1 << 10, m, k, seed=MIX_SEED, shift=small)])
-        line["cpu_baseline"] = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle",
-                                "sample": f"{reps} oracle solves of an N=2^10, m={m}, k={k}, kappa~1e2 system, {el:.1f} s"}
+        v, cores, reps, el = oracle_rate([synthetic.gen_system(1 << 10, m, k, seed=MIX_SEED, shift=small)],
+                                         seconds=cpu_seconds)
+        out["cpu_baseline"] = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle",
+                               "sample": f"{reps} oracle solves of an N=2^10, m={m}, k={k}, kappa~1e2 system, {el:.1f} s"}
+    return out
+
+
+def run_mixed(args):
+    import torch
+    torch.cuda.set_device(0)
+    log2n = 14 if args.log2n in (14, 20) else args.log2n      # smaller cases are for profiling only
+    sampler = ClockSampler(0)
+    sampler.start()
+    time.sleep(1.0)
+    sampler.mark(True)
+    res = measure_mixed(args.steps, args.warmup, log2n, with_oracle=not args.no_cpu_baseline)
+    sampler.mark(False)
+    line = {"metric": res["metric"], "value": res["value"], "unit": res["unit"], "n_gpus": 1,
+            "steps": res["steps"], "warmup": res["warmup"], "ms_per_step": res["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64 fine levels / c128",
+            "data": "synthetic"}
+    line.update({k: v for k, v in res.items() if k not in line and k != "metric"})
+    line.update({"clocks": sampler.stop(), "e2e": None})
+    line.setdefault("cpu_baseline", None)
     print(json.dumps(line), flush=True)
 
 
@@ -745,6 +912,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched, mixed and adjoint measurements of the default run")
     ap.add_argument("--workload", default="plain", choices=["plain", "batched", "adjoint", "mixed", "alg1"])
     ap.add_argument("--nsys", type=int, default=4096, help="systems of the batched workload")
     ap.add_argument("--log2n", type=int, default=20,
@@ -833,6 +1002,7 @@ def main():
 
     # measurement-side residual check (torch ops, not part of the solver)
     eta = residual_eta(dA, dB, dy, dx)
+    traffic_blk = captured_traffic_per_odd_block()
 
     e2e = None
     if not args.no_e2e:
@@ -850,14 +1020,41 @@ def main():
     cpu = None
     sample_err = None
     variants = None
+    probe = fp64_probe()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and N_BLOCKS == 1 << 20:
         variants = plain_variant_runs(args, plan, dev)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         v, cores, desc, (sA, sB, sy, sx) = cpu_oracle_sample()
-        cpu = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle", "sample": desc}
+        cpu = {"value": v, "unit": "block-rows/s", "cores": cores, "kind": "oracle", "sample": desc,
+               "single_thread": cpu_oracle_single_thread()}
         # the GPU on the same sample, for the error at which the rate is quoted
         xs = crs.solve(*(torch.from_numpy(a).to(dev) for a in (sA, sB, sy))).cpu().numpy()
         sample_err = float(np.linalg.norm(xs - sx) / np.linalg.norm(sx))
+
+    extra = None
+    if rank == 0 and ws == 1 and not args.no_extras and N_BLOCKS == 1 << 20:
+        # the other forms on the same GPU, after the plain workload's buffers are released
+        plan.close()
+        del dA, dB, dy, dx
+        torch.cuda.empty_cache()
+        extra = {}
+        xs_ = dict(batched=lambda: measure_batched(EXTRA_STEPS, EXTRA_WARMUP, with_oracle=not args.no_cpu_baseline,
+                                                   cpu_seconds=5.0),
+                   mixed=lambda: measure_mixed(EXTRA_STEPS, EXTRA_WARMUP, with_oracle=not args.no_cpu_baseline,
+                                               cpu_seconds=5.0),
+                   adjoint=lambda: measure_adjoint(EXTRA_STEPS * 4, EXTRA_WARMUP, with_oracle=not args.no_cpu_baseline,
+                                                   cpu_seconds=5.0))
+        sampler2 = ClockSampler(dev.index)
+        sampler2.start()
+        time.sleep(0.5)
+        sampler2.mark(True)
+        for name, fn in xs_.items():
+            try:
+                extra[name] = fn()
+            except Exception as e:  # noqa: BLE001 - recorded in the line; the main number stands
+                extra[name] = {"failed": f"{type(e).__name__}: {e}"}
+        sampler2.mark(False)
+        extra["clocks"] = sampler2.stop()
 
     if rank == 0:
         line = {
@@ -871,11 +1068,12 @@ def main():
             "roofline": {"bound": "alu", "kernel": "k_factor_odd<8>, all levels",
                          "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                          "frac": (achieved / peak_tf) if achieved else None,
-                         "traffic": TRAFFIC_PER_ODD_BLOCK * (fac["units"] / max(fac["launches"], 1)),
-                         "traffic_note": "dram read+write per launch, scaled by odd blocks from the ncu capture of "
-                                         "level 0 at N=2^18 (1163 MB for 2^17 odd blocks; "
-                                         "profiles/k_factor_odd_m8_N2p18_level0.md)",
+                         "traffic": (traffic_blk * (fac["units"] / max(fac["launches"], 1))) if traffic_blk else None,
+                         "traffic_note": "dram read+write per launch: the ncu capture of level 0 at N=2^18 scaled "
+                                         "by odd blocks; null when the kernel sources differ from the captured ones",
                          "peak_source": "FP64 pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived)",
+                         "peak_probe": probe,
+                         "frac_of_probe": (achieved / probe["tflops"]) if achieved and "tflops" in probe else None,
                          "flops_per_unit": flops_factor_per_odd_block(M), "units": fac["units"] // args.steps,
                          "launches_per_step": fac["launches"] // args.steps},
             "step_roofline": {"flops_per_step": step_flops, "achieved": step_flops / (ms_step * 1e-3) / 1e12,
@@ -889,6 +1087,7 @@ def main():
             "clocks": clocks,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "extra": extra,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:

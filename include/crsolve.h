@@ -75,6 +75,8 @@ enum crsolve_precision {
 #define CRSOLVE_PLAN_HOST_STAGING 1u  /* workspace also holds device copies of A, B, y, x
                                          for crsolve_solve_host */
 #define CRSOLVE_PLAN_ALG1 2u          /* the paper's own method, Algorithm 1 (Sec. 3) */
+#define CRSOLVE_PLAN_FP64_RESIDUAL 4u /* mixed precision: residuals and products on the FP64
+                                         pipe even where the tensor-core splitting applies */
 
 /*
  * Plans with CRSOLVE_PLAN_ALG1 run the paper's Algorithm 1 instead of classic
@@ -291,10 +293,14 @@ int crsolve_batch_destroy(crsolve_batch b);
  *   system whose intermediates exceed it returns CRSOLVE_ENOMEM and enqueues
  *   nothing (about N * (5.5 m^2 + 3.5 m k) * 16 bytes must fit, e.g. N up to
  *   ~4500 for m = 8, k = 4).
- *   The first call on a device looks up the array's address and prepares the
- *   kernels; make it before any stream capture.  All calls share the array
- *   and it keeps the last call's contents, so calls that overlap on the GPU
- *   race: serialise them.  After a breakdown x holds NaN.  With info != NULL
+ *   Every call looks up the array's device address (cudaGetSymbolAddress,
+ *   with the caller's device current) and sets the shared-memory limits of
+ *   its kernels; nothing is cached between calls, so a device reset or
+ *   another context of the device never leaves a stale address.  The first
+ *   call on a device also loads the library's kernels onto it: make it
+ *   before any stream capture.  All calls share the array and it keeps the
+ *   last call's contents, so calls that overlap on the GPU race: serialise
+ *   them.  After a breakdown x holds NaN.  With info != NULL
  *   the call synchronises the stream and reports the breakdown status there;
  *   with info == NULL it is asynchronous.
  */
@@ -339,21 +345,81 @@ int crsolve_timing_read(crsolve_plan p, crsolve_kernel_time *out, int32_t cap, i
 /*
  * Mixed precision (plans created with CRSOLVE_MIXED).  The levels of the
  * reduction with more than 2 blocks are factored and solved in FP32; the two
- * coarsest levels, the breakdown decision, the residual
- * r = y - A x and the iterative refinement x += A~^{-1} r are FP64.  In this
- * mode crsolve_factor and crsolve_solve synchronise the stream, and A and B
- * must stay valid and unchanged until the plan is re-factored or destroyed
- * (the residual reads them).  A breakdown in the FP32 levels is re-decided by
- * an FP64 factorisation, so the flags are always the FP64 ones.  Refinement
- * hands over to the FP64 path (factor + solve) when it does not contract, or
- * when the steps still needed at the observed contraction rate would cost more
- * than that path (each step: one FP64 residual and one FP32 correction sweep);
- * the handover comes after the first or second residual.
- * crsolve_mixed_stats reports the last solve: FP64 residuals computed,
- * delta = |last correction|_inf / |x|_inf, rho = observed contraction per
- * refinement step, and whether the FP64 path was used instead.
+ * coarsest levels, the breakdown decision, the residuals and products of the
+ * refinement and the refinement itself are FP64.  The refinement is
+ * preconditioned conjugate gradients per right-hand-side column (A is
+ * Hermitian positive definite) with the FP32 solve as preconditioner, the
+ * CG variant of the mixed-precision iterative refinement of Carson and Higham
+ * (SIAM J. Sci. Comput. 39, 2017); it stops when the estimated error
+ * (observed contraction times the last relative correction) is below 1e-11, a
+ * tenth of the stated bound 1e-10.  For m > 32 the FP64-accurate residuals
+ * and products come from exact splitting on the tensor cores (see
+ * crsolve_residual, method CRSOLVE_RESIDUAL_SPLIT) unless the plan was
+ * created with CRSOLVE_PLAN_FP64_RESIDUAL.  In this mode crsolve_factor and
+ * crsolve_solve synchronise the stream, and A and B must stay valid and
+ * unchanged until the plan is re-factored or destroyed (the residual reads
+ * them).  A breakdown in the FP32 levels is re-decided by an FP64
+ * factorisation, so the flags are always the FP64 ones.  The iteration hands
+ * over to the FP64 path (factor + solve) when it does not contract, loses
+ * positive curvature, or when the steps still needed at the observed rate
+ * would cost more than that path.
+ * crsolve_mixed_stats reports the last solve: FP64-accurate residuals and
+ * products computed (1 + CG steps), delta = the last relative correction
+ * (largest over the columns of |alpha p|_inf / |x|_inf), rho = the observed
+ * contraction per step, and whether the FP64 path was used instead.
  */
 int crsolve_mixed_stats(crsolve_plan p, int32_t *iterations, double *delta, double *rho, int32_t *fp64_fallback);
+
+/*
+ * crsolve_residual -- r = y - A x for the block-tridiagonal A of eq. Axb
+ * (A_j Hermitian, read from its lower triangle and the real part of its
+ * diagonal; B_j at block (j+1, j), B_j^H at (j, j+1)), the residual of the
+ * iterative refinement in the mixed-precision form.  Layouts as for
+ * crsolve_factor / crsolve_solve: A [N][m][m], B [N-1][m][m] (NULL iff
+ * N == 1), x, y, r [N][m][k], all device memory, 16-byte aligned; r must not
+ * alias x (it may alias y).
+ *   method CRSOLVE_RESIDUAL_FP64: FP64 fused multiply-adds; no workspace;
+ *   asynchronous.
+ *   method CRSOLVE_RESIDUAL_SPLIT: every product exact on the BF16 tensor
+ *   cores (error-free splitting of Ozaki, Ogita, Oishi and Rump, 2012: each
+ *   entry cut into nine 6-bit integer slices on a per-row / per-column binary
+ *   grid, slice products accumulated exactly in FP32 in tensor memory), then
+ *   y - A x with two FP64 roundings; the dropped slice products and the
+ *   truncation add less than about 2^-50 K max|row of A| max|column of x|
+ *   (K = 6m), within the error bound of an FP64 dot product.  Needs a
+ *   256-byte aligned device workspace of crsolve_residual_workspace_bytes;
+ *   synchronises the stream and returns CRSOLVE_ETIMEOUT if a bounded wait of
+ *   the tensor-core pipeline gave up.  The paper has no counterpart.
+ */
+enum { CRSOLVE_RESIDUAL_FP64 = 0, CRSOLVE_RESIDUAL_SPLIT = 1 };
+int crsolve_residual_workspace_bytes(int64_t N, int32_t m, int32_t k, int32_t method, size_t *bytes);
+int crsolve_residual(int64_t N, int32_t m, int32_t k, const crsolve_z *A, const crsolve_z *B, const crsolve_z *x,
+                     const crsolve_z *y, crsolve_z *r, int32_t method, void *workspace, size_t workspace_bytes,
+                     void *stream);
+
+/*
+ * crsolve_peak_probe -- measured arithmetic rate of the current device, for
+ * rooflines (the paper has no counterpart).  kind CRSOLVE_PROBE_FP64_FMA
+ * times independent FP64 fused multiply-add chains (the pipe that bounds the
+ * FP64 path), CRSOLVE_PROBE_FP32_FMA the FP32 ones; no memory traffic.
+ * Writes the rate in GFLOP/s (2 flop per FMA) to *gflops and, when not NULL,
+ * the FMA lanes per SM per clock cycle (clock-independent) to *fma_per_clk_sm
+ * and the SM clock the kernel ran at to *sm_mhz.  Runs two kernels (a short
+ * warm-up and the timed one, ~0.1 s) on the stream and synchronises it.
+ * CRSOLVE_EINVAL for a NULL gflops or an unknown kind.
+ */
+enum { CRSOLVE_PROBE_FP64_FMA = 0, CRSOLVE_PROBE_FP32_FMA = 1 };
+int crsolve_peak_probe(int32_t kind, double *gflops, double *fma_per_clk_sm, double *sm_mhz, void *stream);
+
+/*
+ * crsolve_check_bounded_wait -- exercises the bounded mbarrier wait of the
+ * tensor-core kernels on its own (the paper has no counterpart): one CTA
+ * waits, with a limit of max_polls polls (and about two seconds), on an
+ * mbarrier that nothing arrives at.  Returns CRSOLVE_ETIMEOUT when the wait
+ * gave up as it should, CRSOLVE_OK if it completed.  workspace: 4 bytes of
+ * device memory.  Synchronises the stream.
+ */
+int crsolve_check_bounded_wait(int32_t max_polls, void *workspace, void *stream);
 
 /* Kernels this plan has launched since it was created. */
 int crsolve_launch_count(crsolve_plan p, int64_t *count);
@@ -376,6 +442,22 @@ int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t 
 /* Number of levels of the plan (floor(log2 N) + 1) and the level sizes; with
  * CRSOLVE_PLAN_ALG1, log2 N + 1 levels of N blocks each (2^l systems of N/2^l). */
 int crsolve_plan_levels(crsolve_plan p, int32_t *nlev, int64_t *sizes /* [nlev] or NULL */);
+
+/*
+ * Bounds-checked builds (compiled with CRSOLVE_DEBUG_BOUNDS, the library
+ * libcrsolve_debug.so; the paper has no counterpart).  Every global-memory
+ * index of the level kernels (and of the tensor-core residual) is checked
+ * against the array extents implied by the level sizes (A [N_l][m][m],
+ * B [N_l-1][m][m], L [no][m][m], Z [no][m][2m], y, x [N_l][m][k], ...); an
+ * out-of-range index is skipped (a load reads zero) and the smallest record
+ * (level << 56 | array << 48 | index, array numbers as in crs::DbgArray) is
+ * kept in a word of the plan's (or batch's) workspace, cleared by every
+ * crsolve_factor / crsolve_solve_host / batch launch.  These calls
+ * synchronise the stream and write that record (all ones: no out-of-range
+ * access) to *record.  Release builds return CRSOLVE_EUNSUPPORTED.
+ */
+int crsolve_debug_bounds(crsolve_plan p, uint64_t *record, void *stream);
+int crsolve_batch_debug_bounds(crsolve_batch b, uint64_t *record, void *stream);
 
 /*
  * crsolve_debug_level_system -- device pointers of the reduced system

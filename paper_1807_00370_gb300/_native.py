@@ -27,6 +27,11 @@ CRSOLVE_FP64 = 0
 CRSOLVE_MIXED = 1
 CRSOLVE_PLAN_HOST_STAGING = 1
 CRSOLVE_PLAN_ALG1 = 2
+CRSOLVE_PLAN_FP64_RESIDUAL = 4
+CRSOLVE_RESIDUAL_FP64 = 0
+CRSOLVE_RESIDUAL_SPLIT = 1
+CRSOLVE_PROBE_FP64_FMA = 0
+CRSOLVE_PROBE_FP32_FMA = 1
 CRSOLVE_MAX_M = 64
 CRSOLVE_MAX_K = 4096
 
@@ -82,6 +87,12 @@ SIGNATURES = {
     "crsolve_batch_destroy": (ctypes.c_int, [_P]),
     "crsolve_solve_noalloc": (ctypes.c_int, [_I64, _I32, _I32, _P, _P, _P, _P, ctypes.POINTER(CrsolveInfo), _P]),
     "crsolve_tile_get": (ctypes.c_int, [_I32] + [ctypes.POINTER(_I32)] * 5),
+    "crsolve_peak_probe": (ctypes.c_int, [_I32] + [ctypes.POINTER(ctypes.c_double)] * 3 + [_P]),
+    "crsolve_check_bounded_wait": (ctypes.c_int, [_I32, _P, _P]),
+    "crsolve_debug_bounds": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), _P]),
+    "crsolve_batch_debug_bounds": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), _P]),
+    "crsolve_residual_workspace_bytes": (ctypes.c_int, [_I64, _I32, _I32, _I32, ctypes.POINTER(_SZ)]),
+    "crsolve_residual": (ctypes.c_int, [_I64, _I32, _I32, _P, _P, _P, _P, _P, _I32, _P, _SZ, _P]),
 }
 
 
@@ -92,7 +103,9 @@ class CrsolveError(RuntimeError):
 
 
 def lib_path() -> str:
-    return _build.LIB
+    """The library to load: libcrsolve.so, or the bounds-checked
+    libcrsolve_debug.so when CRSOLVE_LIBRARY=debug."""
+    return _build.DEBUG_LIB if os.environ.get("CRSOLVE_LIBRARY") == "debug" else _build.LIB
 
 
 def load(build_if_missing: bool = True):
@@ -101,11 +114,13 @@ def load(build_if_missing: bool = True):
     with _lock:
         if _lib is not None:
             return _lib
-        if build_if_missing and _build.is_stale():
-            _build.build()
-        if not os.path.exists(_build.LIB):
-            raise RuntimeError(f"libcrsolve.so not built ({_build.LIB}); run paper_1807_00370_gb300.build.build()")
-        lib = ctypes.CDLL(_build.LIB)
+        path = lib_path()
+        debug = path == _build.DEBUG_LIB
+        if build_if_missing and _build.is_stale(debug):
+            _build.build(debug=debug)
+        if not os.path.exists(path):
+            raise RuntimeError(f"{os.path.basename(path)} not built ({path}); run paper_1807_00370_gb300.build.build()")
+        lib = ctypes.CDLL(path)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(lib, name)
             fn.restype = res

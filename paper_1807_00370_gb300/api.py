@@ -16,7 +16,7 @@ from . import _native as nat
 __all__ = ["Plan", "crsolve_plan_create", "crsolve_factor", "crsolve_solve", "crsolve_backward",
            "crsolve_info_get", "crsolve_solve_host", "crsolve_plan_levels",
            "crsolve_debug_level_system", "crsolve_timing_enable", "crsolve_timing_read",
-           "crsolve_launch_count", "crsolve_mixed_stats", "crsolve_tile_set", "crsolve_tile_get", "crsolve_solve_noalloc", "solve", "CRSolveFn",
+           "crsolve_launch_count", "crsolve_mixed_stats", "crsolve_tile_set", "crsolve_tile_get", "crsolve_solve_noalloc", "crsolve_peak_probe", "crsolve_residual", "solve", "CRSolveFn",
            "NotPositiveDefinite"]
 
 
@@ -246,6 +246,41 @@ def crsolve_launch_count(plan: Plan) -> int:
     c = ctypes.c_int64()
     nat.check(nat.load().crsolve_launch_count(plan.handle, ctypes.byref(c)), "crsolve_launch_count")
     return int(c.value)
+
+
+def crsolve_residual(A: torch.Tensor, B: torch.Tensor | None, x: torch.Tensor, y: torch.Tensor,
+                     method: str = "split", r: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """r = y - A x for the block-tridiagonal system (method "fp64" or "split":
+    exact slice products on the tensor cores, FP64 accuracy)."""
+    N, m, _ = A.shape
+    k = x.shape[-1]
+    _need(A, (N, m, m), "A")
+    if N > 1:
+        _need(B, (N - 1, m, m), "B", A.device)
+    _need(x, (N, m, k), "x", A.device)
+    _need(y, (N, m, k), "y", A.device)
+    if r is None:
+        r = torch.empty_like(y)
+    code = {"fp64": nat.CRSOLVE_RESIDUAL_FP64, "split": nat.CRSOLVE_RESIDUAL_SPLIT}[method]
+    lib = nat.load()
+    nbytes = ctypes.c_size_t()
+    nat.check(lib.crsolve_residual_workspace_bytes(N, m, k, code, ctypes.byref(nbytes)),
+              "crsolve_residual_workspace_bytes")
+    ws = torch.empty(max(int(nbytes.value), 1), dtype=torch.uint8, device=A.device)
+    with torch.cuda.device(A.device):
+        nat.check(lib.crsolve_residual(N, m, k, _vp(A), _vp(B) if N > 1 else None, _vp(x), _vp(y), _vp(r), code,
+                                       _vp(ws), int(nbytes.value), _stream(stream)), "crsolve_residual")
+    return r
+
+
+def crsolve_peak_probe(kind: str = "fp64", stream=None) -> dict:
+    """Measured FMA rate of the current device ("fp64" or "fp32"):
+    {"gflops", "fma_per_clk_sm", "sm_mhz"}."""
+    code = {"fp64": nat.CRSOLVE_PROBE_FP64_FMA, "fp32": nat.CRSOLVE_PROBE_FP32_FMA}[kind]
+    v, c, f = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    nat.check(nat.load().crsolve_peak_probe(code, ctypes.byref(v), ctypes.byref(c), ctypes.byref(f), _stream(stream)),
+              "crsolve_peak_probe")
+    return {"gflops": float(v.value), "fma_per_clk_sm": float(c.value), "sm_mhz": float(f.value)}
 
 
 def crsolve_tile_set(mt: int, nb_factor: int, nb_solve: int, kc: int, threads: int,

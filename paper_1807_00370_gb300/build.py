@@ -17,6 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libcrsolve.so")
+# the same sources with every kernel index checked against the level sizes
+DEBUG_LIB = os.path.join(BUILD, "libcrsolve_debug.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
@@ -37,27 +39,42 @@ def _deps():
         glob.glob(os.path.join(INCLUDE, "*.h")) + [os.path.abspath(__file__)]
 
 
-def is_stale() -> bool:
-    if not os.path.exists(LIB):
+def is_stale(debug: bool = False) -> bool:
+    lib = DEBUG_LIB if debug else LIB
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(d) > t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile and link libcrsolve.so if any source is newer (or force)."""
-    if not force and not is_stale():
+def _variants(debug):
+    """(library, object directory, extra flags) of the builds to run."""
+    out = [(LIB, BUILD, [])]
+    if debug:
+        out.append((DEBUG_LIB, os.path.join(BUILD, "debug"), ["-DCRSOLVE_DEBUG_BOUNDS"]))
+    return out
+
+
+def build(force: bool = False, verbose: bool = False, debug: bool = False) -> str:
+    """Compile and link libcrsolve.so (and with debug=True also the
+    bounds-checked libcrsolve_debug.so) if any source is newer (or force).
+    All translation units of both libraries compile in parallel."""
+    todo = [v for v in _variants(debug) if force or is_stale(v[0] == DEBUG_LIB)]
+    if not todo:
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
-    procs, objs = [], []
-    for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        objs.append(obj)
-        cmd = [nvcc, *ARCH, *NVCC_FLAGS, "-c", src, "-o", obj]
-        if verbose:
-            print(" ".join(cmd), file=sys.stderr)
-        procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+    procs, links = [], []
+    for lib, odir, extra in todo:
+        os.makedirs(odir, exist_ok=True)
+        objs = []
+        for src in _sources():
+            obj = os.path.join(odir, os.path.basename(src)[:-3] + ".o")
+            objs.append(obj)
+            cmd = [nvcc, *ARCH, *NVCC_FLAGS, *extra, "-c", src, "-o", obj]
+            if verbose:
+                print(" ".join(cmd), file=sys.stderr)
+            procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
+        links.append((lib, objs))
     failed = []
     for src, pr in procs:
         out, _ = pr.communicate()
@@ -66,11 +83,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if failed:
         msg = "\n".join(f"--- {s}\n{o}" for s, o in failed)
         raise RuntimeError(f"nvcc failed:\n{msg}")
-    tmp = LIB + f".{os.getpid()}.tmp"
-    subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
-    os.replace(tmp, LIB)
+    for lib, objs in links:
+        tmp = lib + f".{os.getpid()}.tmp"
+        subprocess.run([nvcc, *ARCH, "-shared", "-o", tmp, *objs], check=True)
+        os.replace(tmp, lib)
     return LIB
 
 
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose=True))
+    print(build(force="--force" in sys.argv, verbose=True, debug="--debug" in sys.argv))

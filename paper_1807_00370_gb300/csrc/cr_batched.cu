@@ -46,6 +46,7 @@ struct BatchArgs {
     int64_t slot_bytes;
     unsigned long long *status;  // [nsys]
     BatchTiles tiles;
+    unsigned long long *dbg;     // bounds-checked builds: first out-of-range access
 };
 
 __host__ __device__ inline int64_t al16(int64_t b) { return (b + 15) & ~(int64_t)15; }
@@ -118,6 +119,7 @@ __device__ inline void make_level_args(LevelArgs &a, const BatchArgs &ba, const 
     a.x = l == 0 ? ba.x + d.offY : Yp;
     a.xn = Yq;
     a.status = ba.status + sid;
+    a.dbg = ba.dbg;
 }
 
 // The whole classic cyclic reduction of one system, run by one CTA.  The
@@ -207,7 +209,7 @@ struct crsolve_batch_s {
     int64_t slot_bytes = 0, nA = 0, nB = 0, nY = 0;
     int32_t nslots = 0;
     size_t smem = 0;
-    size_t offSys = 0, offOrder = 0, offCounter = 0, offStatus = 0, offSlots = 0, total = 0;
+    size_t offSys = 0, offOrder = 0, offCounter = 0, offStatus = 0, offDbg = 0, offSlots = 0, total = 0;
     char *ws = nullptr;
     bool uploaded = false;
     cudaGraphExec_t gexec = nullptr;
@@ -261,6 +263,7 @@ void layout(crsolve_batch_s *b, int32_t nslots) {
     b->offOrder = take(b->order.size() * sizeof(int32_t));
     b->offCounter = take(sizeof(int32_t));
     b->offStatus = take(b->sys.size() * sizeof(unsigned long long));
+    b->offDbg = take(sizeof(unsigned long long));
     b->offSlots = take(0);
     b->nslots = nslots;
     b->total = b->offSlots + (size_t)nslots * (size_t)b->slot_bytes;
@@ -280,6 +283,10 @@ int enqueue(crsolve_batch_s *b, const z2 *A, const z2 *B, const z2 *y, z2 *x, cu
     ba.slot_bytes = b->slot_bytes;
     ba.status = reinterpret_cast<unsigned long long *>(b->ws + b->offStatus);
     ba.tiles = b->tiles;
+    ba.dbg = reinterpret_cast<unsigned long long *>(b->ws + b->offDbg);
+#ifdef CRSOLVE_DEBUG_BOUNDS
+    if (cudaMemsetAsync(ba.dbg, 0xFF, sizeof(unsigned long long), s) != cudaSuccess) return CRSOLVE_ECUDA;
+#endif
     crs::k_batch<<<b->nslots, b->threads, b->smem, s>>>(ba);
     return cudaGetLastError() == cudaSuccess ? CRSOLVE_OK : CRSOLVE_ECUDA;
 }
@@ -441,6 +448,24 @@ int crsolve_batch_graph_launch(crsolve_batch b, const crsolve_z *A, const crsolv
         memcpy(b->gptr, ptrs, sizeof(ptrs));
     }
     return cudaGraphLaunch(b->gexec, static_cast<cudaStream_t>(stream)) == cudaSuccess ? CRSOLVE_OK : CRSOLVE_ECUDA;
+}
+
+int crsolve_batch_debug_bounds(crsolve_batch b, uint64_t *record, void *stream) {
+    if (!b || !record) return CRSOLVE_EINVAL;
+#ifdef CRSOLVE_DEBUG_BOUNDS
+    if (!b->ws) return CRSOLVE_ENOMEM;
+    unsigned long long v = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&v, b->ws + b->offDbg, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    *record = v;
+    return CRSOLVE_OK;
+#else
+    (void)stream;
+    *record = ~0ull;
+    return CRSOLVE_EUNSUPPORTED;
+#endif
 }
 
 int crsolve_batch_info(crsolve_batch b, crsolve_info *out, void *stream) {

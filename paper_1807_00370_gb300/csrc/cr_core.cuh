@@ -339,7 +339,7 @@ __device__ bool herk_tc_f32(const LevelArgsT<float> &a, int64_t t, const float2 
                         v.x -= dr;
                         v.y -= di;
                     }
-                } else if (hasL && hasR) {
+                } else if (hasL && hasR && CRS_IN(a, kDbgBn, (t - 1) * mm + (p - m) * m + q)) {
                     a.Bn[(t - 1) * mm + (p - m) * m + q] = make_float2(-dr, -di);
                 }
             }
@@ -386,11 +386,11 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
                     const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
                     const int64_t t = t0 + b, pos = 2 * t;
                     if (r >= c) {
-                        va[u] = __ldg(a.A + pos * mm + rem);
-                        if (t < a.ne) vv[u] = __ldg(a.A + (pos + 1) * mm + rem);
+                        if (CRS_IN(a, kDbgA, pos * mm + rem)) va[u] = __ldg(a.A + pos * mm + rem);
+                        if (t < a.ne && CRS_IN(a, kDbgA, (pos + 1) * mm + rem)) vv[u] = __ldg(a.A + (pos + 1) * mm + rem);
                     }
-                    if (pos >= 1) vp[u] = __ldg(a.B + (pos - 1) * mm + rem);
-                    if (pos + 1 < a.Nl) vq[u] = __ldg(a.B + pos * mm + rem);
+                    if (pos >= 1 && CRS_IN(a, kDbgB, (pos - 1) * mm + rem)) vp[u] = __ldg(a.B + (pos - 1) * mm + rem);
+                    if (pos + 1 < a.Nl && CRS_IN(a, kDbgB, pos * mm + rem)) vq[u] = __ldg(a.B + pos * mm + rem);
                 }
             }
 #pragma unroll
@@ -416,15 +416,17 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
             const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
             const int64_t t = t0 + b, pos = 2 * t;
             if (r >= c) {
-                sL[b * TRI + tri(r, c)] = a.A[pos * mm + rem];
+                sL[b * TRI + tri(r, c)] = CRS_IN(a, kDbgA, pos * mm + rem) ? a.A[pos * mm + rem] : zmk(R(0), R(0));
                 if (t < a.ne) {
-                    C v = a.A[(pos + 1) * mm + rem];
+                    C v = CRS_IN(a, kDbgA, (pos + 1) * mm + rem) ? a.A[(pos + 1) * mm + rem] : zmk(R(0), R(0));
                     if (r == c) v.y = R(0);
                     sV[b * TRI + tri(r, c)] = v;
                 }
             }
-            sZ[(b * MT + r) * LDZ + c] = (pos >= 1) ? a.B[(pos - 1) * mm + rem] : zmk(R(0), R(0));
-            sZ[(b * MT + c) * LDZ + m + r] = (pos + 1 < a.Nl) ? zconj(a.B[pos * mm + rem]) : zmk(R(0), R(0));
+            sZ[(b * MT + r) * LDZ + c] =
+                (pos >= 1 && CRS_IN(a, kDbgB, (pos - 1) * mm + rem)) ? a.B[(pos - 1) * mm + rem] : zmk(R(0), R(0));
+            sZ[(b * MT + c) * LDZ + m + r] =
+                (pos + 1 < a.Nl && CRS_IN(a, kDbgB, pos * mm + rem)) ? zconj(a.B[pos * mm + rem]) : zmk(R(0), R(0));
         }
     }
     __syncthreads();
@@ -530,15 +532,17 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
     // keep L, 1/diag(L) and Z for the solves
     for (int e = tid; e < nbh * mm; e += NT) {
         const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        a.L[(t0 + b) * mm + rem] = (r >= c) ? sL[b * TRI + tri(r, c)] : zmk(R(0), R(0));
+        if (CRS_IN(a, kDbgL, (t0 + b) * mm + rem))
+            a.L[(t0 + b) * mm + rem] = (r >= c) ? sL[b * TRI + tri(r, c)] : zmk(R(0), R(0));
     }
     for (int e = tid; e < nbh * m; e += NT) {
         const int b = e / m, r = e - b * m;
-        a.inv[(t0 + b) * m + r] = sInv[b * MT + r];
+        if (CRS_IN(a, kDbgInv, (t0 + b) * m + r)) a.inv[(t0 + b) * m + r] = sInv[b * MT + r];
     }
     for (int e = tid; e < nbh * m * m2; e += NT) {
         const int b = e / (m * m2), rem = e - b * (m * m2), r = rem / m2, c = rem - r * m2;
-        a.Z[(t0 + b) * (int64_t)(m * m2) + rem] = sZ[(b * MT + r) * LDZ + c];
+        if (CRS_IN(a, kDbgZ, (t0 + b) * (int64_t)(m * m2) + rem))
+            a.Z[(t0 + b) * (int64_t)(m * m2) + rem] = sZ[(b * MT + r) * LDZ + c];
     }
     __syncthreads();
 
@@ -611,7 +615,7 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
                 sW[b * TRI + tri(p, q)] = acc;
             } else if (kind == 1) {
                 *dst = acc;
-            } else {
+            } else if (CRS_IN(a, kDbgBn, (t - 1) * mm + (p - m) * m + q)) {
                 a.Bn[(t - 1) * mm + (p - m) * m + q] = acc;
             }
         }
@@ -631,19 +635,21 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
             if (a.inline_fix) {
                 // the previous chunk (same CTA, earlier) left V_{j-1} = A - Q^H Q
                 const int64_t o = (j - 1) * mm;
-                C v = zsub(a.An[o + r * m + c], sW[f]);
-                if (r == c) v.y = R(0);
-                a.An[o + r * m + c] = v;
-                if (r != c) a.An[o + c * m + r] = zconj(v);
-            } else {
+                if (CRS_IN(a, kDbgAn, o + r * m + c) && CRS_IN(a, kDbgAn, o + c * m + r)) {
+                    C v = zsub(a.An[o + r * m + c], sW[f]);
+                    if (r == c) v.y = R(0);
+                    a.An[o + r * m + c] = v;
+                    if (r != c) a.An[o + c * m + r] = zconj(v);
+                }
+            } else if (CRS_IN(a, kDbgWbd, chunk * mm + r * m + c)) {
                 a.Wbd[chunk * mm + r * m + c] = sW[f];
             }
         }
         if (j >= a.ne) continue;
         C v = sV[b * TRI + f];
         if (b + 1 < nbh) v = zsub(v, sW[(b + 1) * TRI + f]);
-        a.An[j * mm + r * m + c] = v;
-        if (r != c) a.An[j * mm + c * m + r] = zconj(v);
+        if (CRS_IN(a, kDbgAn, j * mm + r * m + c)) a.An[j * mm + r * m + c] = v;
+        if (r != c && CRS_IN(a, kDbgAn, j * mm + c * m + r)) a.An[j * mm + c * m + r] = zconj(v);
     }
 }
 
@@ -665,6 +671,9 @@ __device__ __forceinline__ void factor_fix_items(const LevelArgsT<R> &a, int64_t
         const int f = (int)(e - (c - c_first) * nl);
         const int p = tri_row(f), q = f - p * (p + 1) / 2;
         const int64_t j = c * a.nb - 1;
+        if (!CRS_IN(a, kDbgAn, j * mm + p * m + q) || !CRS_IN(a, kDbgAn, j * mm + q * m + p) ||
+            !CRS_IN(a, kDbgWbd, c * mm + p * m + q))
+            continue;
         C v = zsub(a.An[j * mm + p * m + q], a.Wbd[c * mm + p * m + q]);
         if (p == q) v.y = R(0);
         a.An[j * mm + p * m + q] = v;
@@ -698,22 +707,24 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t
 
     for (int e = tid; e < nbh * mm; e += NT) {
         const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        if (r >= c) sL[b * TRI + tri(r, c)] = a.L[(t0 + b) * mm + rem];
+        if (r >= c) sL[b * TRI + tri(r, c)] = CRS_IN(a, kDbgL, (t0 + b) * mm + rem) ? a.L[(t0 + b) * mm + rem] : zmk(R(0), R(0));
     }
     for (int e = tid; e < nbh * m; e += NT) {
         const int b = e / m, r = e - b * m;
-        sInv[b * MT + r] = a.inv[(t0 + b) * m + r];
+        sInv[b * MT + r] = CRS_IN(a, kDbgInv, (t0 + b) * m + r) ? a.inv[(t0 + b) * m + r] : R(0);
     }
     for (int e = tid; e < nbh * m * kw; e += NT) {
         const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
         const int64_t t = t0 + b;
-        sR[(b * MT + r) * kc + c] = a.y[(2 * t) * mk + r * k + c0 + c];
-        if (t < a.ne) sV[(b * MT + r) * kc + c] = a.y[(2 * t + 1) * mk + r * k + c0 + c];
+        const int64_t yo = (2 * t) * mk + r * k + c0 + c;
+        sR[(b * MT + r) * kc + c] = CRS_IN(a, kDbgY, yo) ? a.y[yo] : zmk(R(0), R(0));
+        if (t < a.ne) sV[(b * MT + r) * kc + c] = CRS_IN(a, kDbgY, yo + mk) ? a.y[yo + mk] : zmk(R(0), R(0));
     }
     if constexpr (kStageZ) {
         for (int e = tid; e < nbh * m * m2; e += NT) {
             const int b = e / (m * m2), rem = e - b * (m * m2), r = rem / m2, c = rem - r * m2;
-            sZs[(b * MT + r) * 2 * MT + c] = a.Z[(t0 + b) * (int64_t)(m * m2) + rem];
+            sZs[(b * MT + r) * 2 * MT + c] =
+                CRS_IN(a, kDbgZ, (t0 + b) * (int64_t)(m * m2) + rem) ? a.Z[(t0 + b) * (int64_t)(m * m2) + rem] : zmk(R(0), R(0));
         }
     }
     __syncthreads();
@@ -730,7 +741,7 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t
 
     for (int e = tid; e < nbh * m * kw; e += NT) {
         const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
-        a.r[(t0 + b) * mk + r * k + c0 + c] = sR[(b * MT + r) * kc + c];
+        if (CRS_IN(a, kDbgR, (t0 + b) * mk + r * k + c0 + c)) a.r[(t0 + b) * mk + r * k + c0 + c] = sR[(b * MT + r) * kc + c];
     }
     // Z^H r: rows p < m give P^H r (kept in sW for the left even block), rows
     // p >= m give Q^H r (subtracted from the right even block in place)
@@ -790,7 +801,8 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t
 #pragma unroll
             for (int s = 0; s < MT; ++s)
                 if (s < m) {
-                    const C z = __ldg(Zt + s * m2);
+                    const int64_t zo = t * (int64_t)(m * m2) + p + s * m2;
+                    const C z = CRS_IN(a, kDbgZ, zo) ? __ldg(Zt + s * m2) : zmk(R(0), R(0));
                     zmac_ca(acc, zmk(flip_if(z.x, sg), flip_if(z.y, sg)), Rb[s * kc]);
                 }
             *dst = acc;
@@ -804,15 +816,15 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t
         if (b == 0 && j >= 1) {
             if (a.inline_fix) {
                 const int64_t o = (j - 1) * mk + r * k + c0 + c;
-                a.yn[o] = zsub(a.yn[o], sW[r * kc + c]);
-            } else {
+                if (CRS_IN(a, kDbgYn, o)) a.yn[o] = zsub(a.yn[o], sW[r * kc + c]);
+            } else if (CRS_IN(a, kDbgCbd, chunk * mk + r * k + c0 + c)) {
                 a.cbd[chunk * mk + r * k + c0 + c] = sW[r * kc + c];
             }
         }
         if (j >= a.ne) continue;
         C v = sV[(b * MT + r) * kc + c];
         if (b + 1 < nbh) v = zsub(v, sW[((b + 1) * MT + r) * kc + c]);
-        a.yn[j * mk + r * k + c0 + c] = v;
+        if (CRS_IN(a, kDbgYn, j * mk + r * k + c0 + c)) a.yn[j * mk + r * k + c0 + c] = v;
     }
 }
 
@@ -822,7 +834,8 @@ __device__ __forceinline__ void solve_down_fix_items(const LevelArgsT<R> &a, int
     const int64_t mk = (int64_t)a.m * a.k, ncta = crs_num_ctas(a.no, a.nb), total = (ncta - 1) * mk;
     for (int64_t e = first; e < total; e += stride) {
         const int64_t c = 1 + e / mk, rem = e - (c - 1) * mk, j = c * a.nb - 1;
-        a.yn[j * mk + rem] = zsub(a.yn[j * mk + rem], a.cbd[c * mk + rem]);
+        if (CRS_IN(a, kDbgYn, j * mk + rem) && CRS_IN(a, kDbgCbd, c * mk + rem))
+            a.yn[j * mk + rem] = zsub(a.yn[j * mk + rem], a.cbd[c * mk + rem]);
     }
 }
 
@@ -853,34 +866,38 @@ __device__ __forceinline__ void solve_up_chunk(const LevelArgsT<R> &a, int64_t c
         for (int e = tid; e < nbh * m * kw; e += NT) {
             const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
             const int64_t t = t0 + b;
-            a.x[(2 * t) * mk + r * k + c0 + c] = nan2;
-            if (t < a.ne) a.x[(2 * t + 1) * mk + r * k + c0 + c] = nan2;
+            if (CRS_IN(a, kDbgX, (2 * t) * mk + r * k + c0 + c)) a.x[(2 * t) * mk + r * k + c0 + c] = nan2;
+            if (t < a.ne && CRS_IN(a, kDbgX, (2 * t + 1) * mk + r * k + c0 + c))
+                a.x[(2 * t + 1) * mk + r * k + c0 + c] = nan2;
         }
         return;
     }
 
     for (int e = tid; e < nbh * mm; e += NT) {
         const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        if (r >= c) sL[b * TRI + tri(r, c)] = a.L[(t0 + b) * mm + rem];
+        if (r >= c) sL[b * TRI + tri(r, c)] = CRS_IN(a, kDbgL, (t0 + b) * mm + rem) ? a.L[(t0 + b) * mm + rem] : zmk(R(0), R(0));
     }
     for (int e = tid; e < nbh * m; e += NT) {
         const int b = e / m, r = e - b * m;
-        sInv[b * MT + r] = a.inv[(t0 + b) * m + r];
+        sInv[b * MT + r] = CRS_IN(a, kDbgInv, (t0 + b) * m + r) ? a.inv[(t0 + b) * m + r] : R(0);
     }
     for (int e = tid; e < nbh * m * kw; e += NT) {
         const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
         const int64_t t = t0 + b;
-        sW[(b * MT + r) * kc + c] = a.r[t * mk + r * k + c0 + c];
+        const int64_t ro = t * mk + r * k + c0 + c;
+        sW[(b * MT + r) * kc + c] = CRS_IN(a, kDbgR, ro) ? a.r[ro] : zmk(R(0), R(0));
         // [x_left; x_right] = [xn_{t-1}; xn_t], zero past the boundary
-        sX[(b * 2 * MT + r) * kc + c] = (t >= 1) ? a.xn[(t - 1) * mk + r * k + c0 + c] : zmk(R(0), R(0));
-        const C xr = (t < a.ne) ? a.xn[t * mk + r * k + c0 + c] : zmk(R(0), R(0));
+        sX[(b * 2 * MT + r) * kc + c] = (t >= 1 && CRS_IN(a, kDbgXn, ro - mk)) ? a.xn[ro - mk] : zmk(R(0), R(0));
+        const C xr = (t < a.ne && CRS_IN(a, kDbgXn, ro)) ? a.xn[ro] : zmk(R(0), R(0));
         sX[(b * 2 * MT + m + r) * kc + c] = xr;
-        if (t < a.ne) a.x[(2 * t + 1) * mk + r * k + c0 + c] = xr;  // even unknowns
+        if (t < a.ne && CRS_IN(a, kDbgX, (2 * t + 1) * mk + r * k + c0 + c))
+            a.x[(2 * t + 1) * mk + r * k + c0 + c] = xr;  // even unknowns
     }
     if constexpr (kStageZ) {
         for (int e = tid; e < nbh * m * m2; e += NT) {
             const int b = e / (m * m2), rem = e - b * (m * m2), r = rem / m2, c = rem - r * m2;
-            sZs[(b * MT + r) * 2 * MT + c] = a.Z[(t0 + b) * (int64_t)(m * m2) + rem];
+            sZs[(b * MT + r) * 2 * MT + c] =
+                CRS_IN(a, kDbgZ, (t0 + b) * (int64_t)(m * m2) + rem) ? a.Z[(t0 + b) * (int64_t)(m * m2) + rem] : zmk(R(0), R(0));
         }
     }
     __syncthreads();
@@ -927,7 +944,7 @@ __device__ __forceinline__ void solve_up_chunk(const LevelArgsT<R> &a, int64_t c
             const C *Zr = a.Z + t * (int64_t)(m * m2) + r * m2;
 #pragma unroll
             for (int s = 0; s < 2 * MT; ++s)
-                if (s < m2) zmsub(acc, __ldg(Zr + s), Xb[s * kc]);
+                if (s < m2 && CRS_IN(a, kDbgZ, t * (int64_t)(m * m2) + r * m2 + s)) zmsub(acc, __ldg(Zr + s), Xb[s * kc]);
             sW[(b * MT + r) * kc + c] = acc;
         }
     }
@@ -945,7 +962,8 @@ __device__ __forceinline__ void solve_up_chunk(const LevelArgsT<R> &a, int64_t c
     }
     for (int e = tid; e < nbh * m * kw; e += NT) {
         const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;
-        a.x[(2 * (t0 + b)) * mk + r * k + c0 + c] = sW[(b * MT + r) * kc + c];
+        if (CRS_IN(a, kDbgX, (2 * (t0 + b)) * mk + r * k + c0 + c))
+            a.x[(2 * (t0 + b)) * mk + r * k + c0 + c] = sW[(b * MT + r) * kc + c];
     }
 }
 

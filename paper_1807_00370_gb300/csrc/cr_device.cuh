@@ -136,8 +136,62 @@ struct LevelArgsT {
     // rows it reads are complete.  For the factor fix-up kernel the same
     // fields give the range of chunk boundaries (c_count = 0: 1 .. chunks-1).
     int64_t c_begin, c_count;
+    // Bounds-checked builds (CRSOLVE_DEBUG_BOUNDS): the first out-of-range
+    // access is recorded here (see dbg_in); nullptr otherwise.
+    unsigned long long *dbg;
 };
 using LevelArgs = LevelArgsT<double>;
+
+// Arrays of a level, for the bounds checks of debug builds.
+enum DbgArray { kDbgA = 1, kDbgB, kDbgL, kDbgInv, kDbgZ, kDbgWbd, kDbgAn, kDbgBn, kDbgY, kDbgR, kDbgCbd, kDbgYn,
+                kDbgXn, kDbgX, kDbgResid };
+
+
+// Element count of array `which` of a level, from the level sizes alone:
+// A [Nl][m][m], B [Nl-1][m][m], L [no][m][m], inv [no][m], Z [no][m][2m],
+// Wbd [ctas][m][m], An [ne][m][m], Bn [ne-1][m][m], y and x [Nl][m][k],
+// r [no][m][k], cbd [ctas][m][k], yn and xn [ne][m][k].
+template <class R>
+__device__ __forceinline__ int64_t dbg_extent(const LevelArgsT<R> &a, int which) {
+    const int64_t mm = (int64_t)a.m * a.m, mk = (int64_t)a.m * a.k;
+    const int64_t ctas = a.nb > 0 ? (a.no + a.nb - 1) / a.nb : 0;
+    switch (which) {
+        case kDbgA: return a.Nl * mm;
+        case kDbgB: return (a.Nl > 1 ? a.Nl - 1 : 0) * mm;
+        case kDbgL: return a.no * mm;
+        case kDbgInv: return a.no * a.m;
+        case kDbgZ: return a.no * 2 * mm;
+        case kDbgWbd: return ctas * mm;
+        case kDbgAn: return a.ne * mm;
+        case kDbgBn: return (a.ne > 1 ? a.ne - 1 : 0) * mm;
+        case kDbgY: case kDbgX: return a.Nl * mk;
+        case kDbgR: return a.no * mk;
+        case kDbgCbd: return ctas * mk;
+        case kDbgYn: case kDbgXn: return a.ne * mk;
+        default: return 0;
+    }
+}
+
+// Debug builds: is idx inside array `which`?  If not, the first such access
+// (smallest record: level, array, index) is kept in *a.dbg and the caller
+// skips the access (a load gives zero), so a faulty index never touches
+// memory.  Release builds: always true, no code.
+#ifdef CRSOLVE_DEBUG_BOUNDS
+template <class R>
+__device__ __forceinline__ bool dbg_in(const LevelArgsT<R> &a, int which, int64_t idx) {
+    if (idx >= 0 && idx < dbg_extent(a, which)) return true;
+    if (a.dbg) {
+        const unsigned long long rec = ((unsigned long long)(a.level & 0xFF) << 56) |
+                                       ((unsigned long long)which << 48) |
+                                       ((unsigned long long)idx & 0xFFFFFFFFFFFFull);
+        atomicMin(a.dbg, rec);
+    }
+    return false;
+}
+#define CRS_IN(a, which, idx) (::crs::dbg_in((a), ::crs::which, (int64_t)(idx)))
+#else
+#define CRS_IN(a, which, idx) (true)
+#endif
 
 // 1-based block index that a breakdown of the level block at 0-based position
 // pos0 reports.  Classic reduction: the local index pos0 + 1.  Algorithm 1

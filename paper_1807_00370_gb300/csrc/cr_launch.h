@@ -58,6 +58,41 @@ cudaError_t launch_update(z2 *x, const c2 *d, int64_t n, int first, unsigned lon
                           cudaStream_t s);
 cudaError_t launch_residual(int64_t N, int m, int k, const z2 *A, const z2 *B, const z2 *x, const z2 *y, z2 *r,
                             int nsm, cudaStream_t s);
+// Preconditioned conjugate gradients of the mixed-precision form, per
+// right-hand-side column (cr_mixed.cu).  launch_dot reduces Re sum conj(a) b
+// over the rows = N m rows of [rows][k] block vectors into dot_partials(nsm)
+// x k partial sums `part`, then (mode 0) out = the dots, (mode 1) out = alpha
+// = num / (-dot) with *flag set on a non-positive curvature, or (mode 2) out =
+// beta = (dot - num2) / num and num = dot.
+int dot_partials(int nsm);
+cudaError_t launch_dot(const z2 *a, const c2 *b, int64_t rows, int k, double *part, double *out, int mode, double *num,
+                       const double *num2, int *flag, int nsm, cudaStream_t s);
+cudaError_t launch_dot(const z2 *a, const z2 *b, int64_t rows, int k, double *part, double *out, int mode, double *num,
+                       const double *num2, int *flag, int nsm, cudaStream_t s);
+// x += alpha p, r += alpha w over n = N m k entries; norms[c] = max |alpha p|,
+// norms[k + c] = max |x| of column c (atomic max, zeroed by the caller).
+cudaError_t launch_pcg_update(z2 *x, z2 *r, const z2 *p, const z2 *w, const double *alpha, int64_t n, int k,
+                              unsigned long long *norms, int nsm, cudaStream_t s);
+// p = z + beta p (first: p = z); z is the FP32 correction.
+cudaError_t launch_pcg_direction(z2 *p, const c2 *z, const double *beta, int64_t n, int k, int first, int nsm,
+                                 cudaStream_t s);
+// FP64 residual r = y - A x by exact splitting on the BF16 tensor cores
+// (cr_resid_tc.cu, m <= 64).  erow [N][m] holds the binary exponent of the
+// largest entry of every row of [B_{j-1} | A_j | B_j^H] (launch_row_exponents,
+// once per matrix); ecol [N][k] the largest exponent of every column of every
+// x_j (computed by launch_residual_tc before the product).
+struct ResidTcArgs {
+    int64_t N;
+    int m, k;
+    const z2 *A, *B, *x, *y;   // y may be NULL (r = -A x)
+    z2 *r;
+    int *erow, *ecol;
+    int *err;      // set to 1 if a bounded wait gave up
+    unsigned long long *dbg;   // bounds-checked builds: first out-of-range access
+};
+size_t residual_tc_smem_bytes();
+cudaError_t launch_row_exponents(const ResidTcArgs &a, int nsm, cudaStream_t s);
+cudaError_t launch_residual_tc(const ResidTcArgs &a, int nsm, cudaStream_t s);
 // Adjoint outer products gA, gB from x and gy.
 cudaError_t launch_adjoint_outer(int64_t N, int m, int k, const z2 *x, const z2 *gy, z2 *gA,
                                  z2 *gB, int nsm, cudaStream_t s);

@@ -1,0 +1,609 @@
+// cr_resid_tc.cu -- the FP64 residual r = y - A x of the block-tridiagonal
+// system of eq. Axb on the BF16 tensor cores, by exact splitting (the
+// error-free transformation of Ozaki, Ogita, Oishi and Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication and its applications", Numer. Algorithms 59, 2012).
+//
+// The iterative refinement of the mixed-precision form needs residuals to
+// FP64 accuracy; on GB300 the FP64 pipe runs at 1/64 of the FP32 rate, so the
+// plain FP64 residual costs about a quarter of a whole FP64 solve at m = 64.
+// Here every product is formed exactly on the tensor cores instead:
+//
+//   * Complex to real: block row j of A x is one real product
+//       [Re r; Im r] = [[Re M, -Im M], [Im M, Re M]] [Re x; Im x]
+//     with M the concatenation [B_{j-1} | A_j | B_j^H] (A_j Hermitian from its
+//     lower triangle) and x the stack [x_{j-1}; x_j; x_{j+1}]: M = 128 rows
+//     (real parts of the m <= 64 output rows, then imaginary parts), K = 3 *
+//     2 * 64 = 384 (each complex column s contributes K indices 2s (times
+//     Re x) and 2s+1 (times Im x)), N = 32 right-hand-side columns per pass.
+//   * Exact splitting: every row of the real matrix gets one exponent E (the
+//     largest binary exponent in the row), every column of the x stack one
+//     exponent F.  A matrix entry v becomes the 60-bit integer
+//     Q = round(|v| / 2^(E-59)), cut into ten 6-bit slices q_0..q_9 (most
+//     significant first); an x entry the 54-bit integer round(|x| / 2^(F-53))
+//     in nine slices t_0..t_8.  Each slice, with the entry's sign, is an
+//     integer |q| <= 63, exact in BF16.  Entries within 2^-7 of their row's
+//     largest are represented exactly (all 53 bits); smaller ones to half a
+//     unit of 2^-60 of it.  The matrix grid is finer than the x grid on
+//     purpose: a representation error of the matrix is the same in every
+//     refinement step, so the refinement converges to the solution of the
+//     perturbed matrix and the error is multiplied by kappa; an error of x
+//     changes with x and is not.
+//   * Products: for every slice pair (i, j) with d = i + j <= 9 the MMA
+//     accumulates q_i t_j into the FP32 accumulator acc_d in tensor memory.
+//     A diagonal holds at most 9 pairs, so |acc_d| <= 9 * 384 * 63^2 < 2^24:
+//     every partial sum is an exact integer in FP32 and the accumulators
+//     hold the exact sums.  Slice i is multiplied by the x slices
+//     t_0..t_{min(8, 9-i)} in one MMA (two when that is wider than 256
+//     columns) whose accumulator address is acc_i, so each product lands in
+//     acc_{i+j}.
+//   * Epilogue (integer): A x = (p0 2^30 + p1) 2^(E + F - 64) with p0, p1
+//     the exact integers sum_{d<=4} acc_d 2^(6(4-d)) and sum_{d>=5} acc_d
+//     2^(6(9-d)); y goes onto the same grid and r = y - A x is formed exactly
+//     in 128-bit integers and rounded once.  So the residual is more precise
+//     than an FP64 one (whose products and sums each round): besides the final
+//     rounding, only the dropped pairs i + j > 9 and the rounding of entries
+//     onto their grids remain, less than about 2^-51 * K * max|row| *
+//     max|column| in all.  Iterative refinement with such a residual is not
+//     limited to kappa * u_FP64 (Carson and Higham's extra-precise residual).
+//
+// Data flow per CTA (persistent over block rows, one CTA per SM): 16 warps cut
+// a K-chunk of 32 into slices in shared memory (double-buffered, K-major, no
+// swizzle) while one thread issues the MMAs of the previous chunk
+// (tcgen05.mma kind::f16, BF16 inputs, FP32 accumulation in tensor memory)
+// and commits them to the chunk buffer's mbarrier; after the last chunk all
+// warps read the nine accumulators back (tcgen05.ld) and write r.  Every
+// mbarrier wait is bounded; on a timeout the kernel records the error, waits
+// (bounded) for its MMAs, frees tensor memory and returns.
+#include "crsolve.h"
+#include "cr_launch.h"
+#include "cr_tc.cuh"
+
+namespace crs {
+namespace {
+
+constexpr int kRtM = 128;                                // MMA rows
+constexpr int kRtNSA = 10;                               // slices of a matrix entry (60-bit grid)
+constexpr int kRtNSX = 9;                                // slices of an x entry (54-bit grid)
+constexpr int kRtND = 10;                                // slice-product diagonals d = i + j kept
+constexpr int kRtNC = 32;                                // right-hand-side columns per pass
+constexpr int kRtKC = 32;                                // real K per chunk (16 complex columns)
+constexpr int kRtASlice = kRtM * kRtKC * 2;              // 8192 bytes per matrix slice per chunk
+constexpr int kRtAStage = kRtNSA * kRtASlice;            // 81920 bytes of matrix slices per chunk
+constexpr int kRtBStage = kRtNSX * kRtNC * kRtKC * 2;    // 18432 bytes of x slices per chunk
+constexpr int kRtStage = kRtAStage + kRtBStage;
+constexpr int kRtThreads = 512;
+constexpr int kRtTmemCols = 512;                         // ten accumulators of 32 columns (320), rounded
+constexpr int kExpZero = -4096, kExpNonFinite = 4096;    // exponent of an all-zero / non-finite set
+constexpr int kRtWaitPolls = 1 << 24;
+
+// Binary exponent e of v (|v| < 2^(e+1)), kExpZero for 0, kExpNonFinite for
+// Inf / NaN.
+__device__ __forceinline__ int dexp(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    if (eb == 0x7FF) return kExpNonFinite;
+    if ((b & 0x7FFFFFFFFFFFFFFFull) == 0) return kExpZero;
+    return eb == 0 ? -1022 : eb - 1023;
+}
+
+// |v| on the grid 2^(E + 1 - G) of a row or column with exponent E (G bits,
+// |v| < 2^(E+1)), rounded to the nearest grid point: exact for entries within
+// 2^(53-G) of the largest, and half a grid unit at most below that.  Values
+// that round (they are below 2^(E+1-G+53)) cannot reach 2^G.
+template <int G>
+__device__ __forceinline__ unsigned long long fixq(double v, int E) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int eb = (int)((b >> 52) & 0x7FF);
+    unsigned long long S = b & 0x000FFFFFFFFFFFFFull;
+    int e = -1022;
+    if (eb != 0) {
+        S |= 1ull << 52;
+        e = eb - 1023;
+    }
+    const int sh = e - E + G - 53;    // <= G - 53 since e <= E
+    if (sh >= 0) return S << sh;
+    if (sh < -54) return 0;
+    return (S + (1ull << (-sh - 1))) >> (-sh);
+}
+
+// BF16 bits of the integer mag (0..63) with the sign bit sg (0 or 0x8000).
+__device__ __forceinline__ uint32_t bf16_int(uint32_t mag, uint32_t sg) {
+    const float f = __uint_as_float(0x4B000000u | mag) - 8388608.0f;
+    return (__float_as_uint(f) >> 16) | sg;
+}
+
+// Byte offset of element (r, k) of a K-major, unswizzled tile of 16-bit
+// elements with kRtKC columns: core matrices of 8 rows x 8 elements (16 bytes
+// per row, 128 bytes per core matrix), K-adjacent cores 128 bytes apart,
+// 8-row groups (kRtKC / 8) * 128 = 512 bytes apart.
+__device__ __forceinline__ int kmaj16(int r, int k) {
+    return (r >> 3) * 512 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// Chunk entry e of the matrix part (64 rows i x 16 complex columns sl) and of
+// the x part (16 rows sl x 32 columns c).  A warp's 32 consecutive e cover 8
+// rows (or columns) mod 8 x 4 K-pairs mod 4, so its 32 shared-memory words
+// fall in 32 different banks; its loads are 64-byte row pieces or 128-byte
+// column pieces.
+__device__ __forceinline__ int a_row(int e) { return ((e >> 7) << 3) | ((e >> 2) & 7); }
+__device__ __forceinline__ int a_col(int e) { return (((e >> 5) & 3) << 2) | (e & 3); }
+__device__ __forceinline__ int x_col(int e) { return (((e >> 5) & 3) << 3) | ((e >> 2) & 7); }
+__device__ __forceinline__ int x_row(int e) { return ((e >> 7) << 2) | (e & 3); }
+
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    // kind::f16 instruction descriptor: FP32 accumulator (bits 4-5 = 1), A and
+    // B BF16 (bits 7-9, 10-12 = 1), both K-major, N >> 3 at bit 17, M >> 4 at 24
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+// 4 consecutive columns of the calling warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;"); }
+
+// 2^e as a double (0 below the subnormal range, Inf above the normal one).
+__device__ __forceinline__ double pow2(int e) {
+    if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
+    return ldexp(1.0, e);
+}
+
+// Bounds-checked builds: is idx inside A [N][m][m] (which = kDbgA), B
+// [N-1][m][m] (kDbgB) or a block vector [N][m][k] (kDbgResid)?  The first
+// out-of-range access is recorded in *a.dbg (level field 0xFF) and skipped.
+__device__ __forceinline__ bool rin(const ResidTcArgs &a, int which, int64_t idx) {
+#ifdef CRSOLVE_DEBUG_BOUNDS
+    const int64_t mm = (int64_t)a.m * a.m;
+    const int64_t ext = which == kDbgA ? a.N * mm : which == kDbgB ? (a.N > 1 ? a.N - 1 : 0) * mm
+                                                                   : a.N * (int64_t)a.m * a.k;
+    if (idx >= 0 && idx < ext) return true;
+    if (a.dbg)
+        atomicMin(a.dbg, (0xFFull << 56) | ((unsigned long long)which << 48) | ((unsigned long long)idx & 0xFFFFFFFFFFFFull));
+    return false;
+#else
+    (void)a;
+    (void)which;
+    (void)idx;
+    return true;
+#endif
+}
+
+// The product's fixed-point sum T = p0 2^30 + p1 (an exact integer) and y,
+// combined into r = y - T 2^se with a single rounding: y goes onto the same
+// grid 2^se (exactly, unless its bits reach below the grid, which lies about
+// 2^-66 of the product's largest term under it), the difference is formed
+// exactly as a 128-bit integer and rounded to the nearest double (ties to
+// even).  Returns false (and the caller falls back to FP64 arithmetic) for a
+// non-finite y, a y far above the product, or a result outside the normal
+// double range.
+__device__ __forceinline__ bool resid_exact(double y, long long p0, long long p1, int se, double &out) {
+    const unsigned long long yb = (unsigned long long)__double_as_longlong(y);
+    const int eyb = (int)((yb >> 52) & 0x7FF);
+    if (eyb == 0x7FF) return false;
+    unsigned long long My = yb & 0x000FFFFFFFFFFFFFull;
+    int ey = -1022;
+    if (eyb != 0) {
+        My |= 1ull << 52;
+        ey = eyb - 1023;
+    }
+    const int sy = ey - 52 - se;     // y = My 2^sy on the grid 2^se
+    __int128 Y = 0;
+    if (My != 0) {
+        if (sy > 60) return false;
+        if (sy >= 0) Y = (__int128)My << sy;
+        else if (sy > -60) Y = (__int128)((My + (1ull << (-sy - 1))) >> (-sy));
+    }
+    if (yb >> 63) Y = -Y;
+    const __int128 R = Y - (((__int128)p0 << 30) + (__int128)p1);
+    if (R == 0) {
+        out = 0.0;
+        return true;
+    }
+    const bool neg = R < 0;
+    const unsigned __int128 U = neg ? (unsigned __int128)(-R) : (unsigned __int128)R;
+    const unsigned long long hi = (unsigned long long)(U >> 64), lo = (unsigned long long)U;
+    const int nbits = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);
+    int sh = nbits - 53;
+    unsigned long long mant;
+    if (sh <= 0) {
+        mant = lo << (-sh);
+    } else {
+        mant = (unsigned long long)(U >> sh);
+        const unsigned __int128 rem = U - ((unsigned __int128)mant << sh);
+        const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+        if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+        if (mant == (1ull << 53)) {
+            mant >>= 1;
+            ++sh;
+        }
+    }
+    const int e = 52 + sh + se;      // the value is mant 2^(sh + se), mant in [2^52, 2^53)
+    if (e < -1022 || e > 1023) return false;
+    out = __longlong_as_double((long long)(((unsigned long long)neg << 63) |
+                                           ((unsigned long long)(e + 1023) << 52) | (mant & 0x000FFFFFFFFFFFFFull)));
+    return true;
+}
+
+// Entry (i, s) of the complex block b of row j's coupling row
+// [B_{j-1} | A_j | B_j^H]: zero outside the matrix.
+__device__ __forceinline__ z2 coupling(const ResidTcArgs &a, int64_t j, int b, int i, int s) {
+    const int m = a.m;
+    const int64_t mm = (int64_t)m * m;
+    if (i >= m || s >= m) return zmk(0.0, 0.0);
+    if (b == 0) {
+        const int64_t o = (j - 1) * mm + (int64_t)i * m + s;
+        if (j == 0 || !rin(a, kDbgB, o)) return zmk(0.0, 0.0);
+        return __ldg(a.B + o);
+    }
+    if (b == 1) {
+        const int64_t o = j * mm + (s <= i ? (int64_t)i * m + s : (int64_t)s * m + i);
+        if (!rin(a, kDbgA, o)) return zmk(0.0, 0.0);
+        if (s < i) return __ldg(a.A + o);
+        if (s == i) return zmk(__ldg(&a.A[o].x), 0.0);
+        const z2 v = __ldg(a.A + o);
+        return zmk(v.x, -v.y);
+    }
+    const int64_t o = j * mm + (int64_t)s * m + i;
+    if (j + 1 >= a.N || !rin(a, kDbgB, o)) return zmk(0.0, 0.0);
+    const z2 v = __ldg(a.B + o);
+    return zmk(v.x, -v.y);
+}
+
+__global__ void __launch_bounds__(256) k_row_exponents(ResidTcArgs a) {
+    const int m = a.m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.N * m; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / m;
+        const int i = (int)(e - j * m);
+        int E = kExpZero;
+        for (int b = 0; b < 3; ++b)
+            for (int s = 0; s < m; ++s) {
+                const z2 v = coupling(a, j, b, i, s);
+                E = max(E, max(dexp(v.x), dexp(v.y)));
+            }
+        a.erow[e] = E;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_col_exponents(ResidTcArgs a) {
+    const int m = a.m, k = a.k;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.N * k; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t j = e / k;
+        const int c = (int)(e - j * k);
+        int F = kExpZero;
+        for (int i = 0; i < m; ++i) {
+            const z2 v = __ldg(a.x + (j * m + i) * (int64_t)k + c);
+            F = max(F, max(dexp(v.x), dexp(v.y)));
+        }
+        a.ecol[e] = F;
+    }
+}
+
+__global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(base + 2 * kRtStage);   // [2]
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + 2 * kRtStage + 16);
+    int *sEr = reinterpret_cast<int *>(base + 2 * kRtStage + 32);        // [64]
+    int *sEc = sEr + 64;                                                  // [32]
+    int *sAbort = sEc + kRtNC;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = a.m, k = a.k;
+    const int64_t mm = (int64_t)m * m, mk = (int64_t)m * k;
+
+    if (tid == 0) {
+        mbar_init(smem_u32(&mbar[0]), 1);
+        mbar_init(smem_u32(&mbar[1]), 1);
+        *sAbort = 0;
+    }
+    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), kRtTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    uint32_t uses0 = 0, uses1 = 0;  // commits issued per buffer
+    bool ok = true;
+    const int npass = (k + kRtNC - 1) / kRtNC;
+
+    // The raw FP64 values of the next chunk are loaded into registers while
+    // the current one is cut into slices, so that the loads' latency hides
+    // behind the integer work (and, across a pass boundary, behind the
+    // epilogue).  Thread tid handles the matrix entries tid + u * 512 of a
+    // chunk and x entry tid.
+    constexpr int kAPer = (64 * 16) / kRtThreads;
+    static_assert((64 * 16) % kRtThreads == 0 && 16 * kRtNC == kRtThreads, "one x entry per thread");
+    z2 cur_a[kAPer], nxt_a[kAPer], cur_x, nxt_x;
+    auto fetch = [&](int64_t jj, int c0, int q, z2 (&va)[kAPer], z2 &vx) {
+        const int b = q >> 2, s0 = (q & 3) * 16;
+#pragma unroll
+        for (int u = 0; u < kAPer; ++u) {
+            const int e = tid + u * kRtThreads;
+            va[u] = coupling(a, jj, b, a_row(e), s0 + a_col(e));
+        }
+        const int s = s0 + x_row(tid), col = c0 + x_col(tid);
+        const int64_t jb = jj - 1 + b;
+        vx = zmk(0.0, 0.0);
+        if (s < m && col < k && jb >= 0 && jb < a.N && rin(a, kDbgResid, jb * mk + (int64_t)s * k + col))
+            vx = __ldg(a.x + jb * mk + (int64_t)s * k + col);
+    };
+    int64_t j = blockIdx.x;
+    int pass = 0;
+    if (j < a.N) fetch(j, 0, 0, cur_a, cur_x);
+    while (j < a.N && ok) {
+        const int col0 = pass * kRtNC;
+        // the (row, pass) after this one: its first chunk is fetched during the last chunk
+        int64_t jn = j;
+        int pn = pass + 1;
+        if (pn == npass) {
+            pn = 0;
+            jn = j + gridDim.x;
+        }
+        if (tid < 64) sEr[tid] = tid < m ? a.erow[j * m + tid] : kExpZero;
+        if (tid >= 64 && tid < 64 + kRtNC) {
+            const int c = tid - 64, col = col0 + c;
+            int F = kExpZero;
+            if (col < k) {
+                F = a.ecol[j * k + col];
+                if (j > 0) F = max(F, a.ecol[(j - 1) * k + col]);
+                if (j + 1 < a.N) F = max(F, a.ecol[(j + 1) * k + col]);
+            }
+            sEc[c] = F;
+        }
+        __syncthreads();
+        for (int q = 0; q < 12; ++q) {
+            const int buf = (int)((uses0 + uses1) & 1u);
+            const uint32_t ub = buf ? uses1 : uses0;
+            // the buffer's previous MMAs must have read it
+            if (ub > 0 && !mbar_wait(smem_u32(&mbar[buf]), (ub - 1) & 1u, kRtWaitPolls)) *sAbort = 1;
+            __syncthreads();
+            if (*sAbort) {
+                ok = false;
+                break;
+            }
+            if (q + 1 < 12) fetch(j, col0, q + 1, nxt_a, nxt_x);
+            else if (jn < a.N) fetch(jn, pn * kRtNC, 0, nxt_a, nxt_x);
+            unsigned char *As = base + buf * kRtStage, *Bs = As + kRtAStage;
+            // matrix slices: 64 rows x 16 complex columns (see a_row / a_col
+            // for the bank-conflict-free map)
+#pragma unroll
+            for (int u = 0; u < kAPer; ++u) {
+                const int e = tid + u * kRtThreads, i = a_row(e), sl = a_col(e);
+                const z2 v = cur_a[u];
+                const int E = sEr[i];
+                const unsigned long long qr = fixq<60>(v.x, E), qi = fixq<60>(v.y, E);
+                const uint32_t sgr = v.x < 0.0 ? 0x8000u : 0u, sgi = v.y < 0.0 ? 0x8000u : 0u;
+                const int o_re = kmaj16(i, 2 * sl), o_im = kmaj16(i + 64, 2 * sl);
+#pragma unroll
+                for (int n = 0; n < kRtNSA; ++n) {
+                    const int sh = 54 - 6 * n;
+                    const uint32_t mr = (uint32_t)(qr >> sh) & 63u, mi = (uint32_t)(qi >> sh) & 63u;
+                    const uint32_t br = bf16_int(mr, sgr), bi = bf16_int(mi, sgi), bni = bi ^ 0x8000u;
+                    unsigned char *An = As + n * kRtASlice;
+                    // real row i: (Re M, -Im M); imaginary row i + 64: (Im M, Re M)
+                    *reinterpret_cast<uint32_t *>(An + o_re) = br | (bni << 16);
+                    *reinterpret_cast<uint32_t *>(An + o_im) = bi | (br << 16);
+                }
+            }
+            // x slices: 16 complex rows x 32 columns
+            {
+                const int c = x_col(tid), sl = x_row(tid);
+                const z2 v = cur_x;
+                const int F = sEc[c];
+                const unsigned long long qr = fixq<54>(v.x, F), qi = fixq<54>(v.y, F);
+                const uint32_t sgr = v.x < 0.0 ? 0x8000u : 0u, sgi = v.y < 0.0 ? 0x8000u : 0u;
+#pragma unroll
+                for (int n = 0; n < kRtNSX; ++n) {
+                    const int sh = 48 - 6 * n;
+                    const uint32_t mr = (uint32_t)(qr >> sh) & 63u, mi = (uint32_t)(qi >> sh) & 63u;
+                    *reinterpret_cast<uint32_t *>(Bs + kmaj16(n * kRtNC + c, 2 * sl)) =
+                        bf16_int(mr, sgr) | (bf16_int(mi, sgi) << 16);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kAPer; ++u) cur_a[u] = nxt_a[u];
+            cur_x = nxt_x;
+            fence_async_smem();
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            if (tid == 0) {
+                const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+                for (int t = 0; t < kRtKC / 16; ++t) {
+                    // the first products of a pass start the accumulators
+                    // (acc_0..acc_8 by slice 0, acc_9 by slice 1)
+                    const uint32_t acc = (q == 0 && t == 0) ? 0u : 1u;
+                    const uint64_t bd = umma_desc(b0 + t * 256, 128, 512);
+                    const uint64_t bd8 = umma_desc(b0 + 8 * (kRtNC / 8) * 512 + t * 256, 128, 512);
+                    for (int i = 0; i < kRtNSA; ++i) {
+                        const uint64_t ad = umma_desc(a0 + i * kRtASlice + t * 256, 128, 512);
+                        const int jmax = min(kRtNSX - 1, kRtND - 1 - i);
+                        if (jmax == kRtNSX - 1) {
+                            // x slices 0..7 (N = 256), then slice 8 (N = 32)
+                            mma_bf16(tmem + i * kRtNC, ad, bd, idesc_bf16(kRtM, 256), i == 0 ? acc : 1u);
+                            mma_bf16(tmem + (i + 8) * kRtNC, ad, bd8, idesc_bf16(kRtM, kRtNC), acc);
+                        } else {
+                            mma_bf16(tmem + i * kRtNC, ad, bd, idesc_bf16(kRtM, (jmax + 1) * kRtNC), 1u);
+                        }
+                    }
+                }
+                tc_commit(smem_u32(&mbar[buf]));
+            }
+            if (buf) ++uses1;
+            else ++uses0;
+        }
+        if (!ok) break;
+        // all MMAs of this pass: wait for the last commit (it tracks every earlier MMA)
+        {
+            const int lb = (int)((uses0 + uses1 - 1) & 1u);
+            if (!mbar_wait(smem_u32(&mbar[lb]), ((lb ? uses1 : uses0) - 1) & 1u, kRtWaitPolls)) *sAbort = 1;
+        }
+        tc_fence_after();
+        __syncthreads();
+        if (*sAbort) {
+            ok = false;
+            break;
+        }
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns 8 (w / 4) .. +7
+        const int p = (warp & 3) * 32 + lane, quarter = warp >> 2;
+        const int i = p & 63, part = p >> 6;
+        const int Er = sEr[i];
+        for (int g = 0; g < 2; ++g) {
+            const int cb = quarter * 8 + g * 4;
+            uint32_t acc[kRtND][4];
+#pragma unroll
+            for (int d = 0; d < kRtND; ++d)
+                tmem_ld4(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(d * kRtNC + cb), acc[d]);
+            tmem_wait_ld();
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int c = cb + cc, col = col0 + c;
+                if (i >= m || col >= k) continue;
+                const int F = sEc[c];
+                long long p0 = 0, p1 = 0;
+#pragma unroll
+                for (int d = 0; d < 5; ++d) p0 = p0 * 64 + (long long)__float2int_rn(__uint_as_float(acc[d][cc]));
+#pragma unroll
+                for (int d = 5; d < kRtND; ++d) p1 = p1 * 64 + (long long)__float2int_rn(__uint_as_float(acc[d][cc]));
+                const int64_t ro = (j * m + i) * (int64_t)k + col;
+                if (!rin(a, kDbgResid, ro)) continue;
+                double *dst = &a.r[ro].x + part;
+                const double yv = a.y ? (&a.y[ro].x)[part] : 0.0;
+                double rv;
+                if (Er == kExpNonFinite || F == kExpNonFinite) {
+                    rv = __longlong_as_double(0x7FF8000000000000ll);
+                } else if (Er == kExpZero || F == kExpZero) {
+                    rv = yv;
+                } else if (!resid_exact(yv, p0, p1, Er + F - 64, rv)) {
+                    const double val = fma((double)p0, 1073741824.0, (double)p1);
+                    rv = fma(-val, pow2(Er + F - 64), yv);
+                }
+                *dst = rv;
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+        tc_fence_after();
+        j = jn;
+        pass = pn;
+    }
+    if (!ok) {
+        if (tid == 0 && a.err) atomicExch(a.err, 1);
+        // let every committed MMA finish before tensor memory is released
+        if (uses0 > 0) mbar_wait(smem_u32(&mbar[0]), (uses0 - 1) & 1u, kRtWaitPolls);
+        if (uses1 > 0) mbar_wait(smem_u32(&mbar[1]), (uses1 - 1) & 1u, kRtWaitPolls);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kRtTmemCols);
+}
+
+}  // namespace
+
+size_t residual_tc_smem_bytes() { return 2 * (size_t)kRtStage + 1024 + 1024; }
+
+cudaError_t launch_row_exponents(const ResidTcArgs &a, int nsm, cudaStream_t s) {
+    const int64_t n = a.N * a.m;
+    int64_t g = (n + 255) / 256;
+    if (g > (int64_t)nsm * 16) g = (int64_t)nsm * 16;
+    k_row_exponents<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_residual_tc(const ResidTcArgs &a, int nsm, cudaStream_t s) {
+    const int64_t n = a.N * a.k;
+    int64_t g = (n + 255) / 256;
+    if (g > (int64_t)nsm * 16) g = (int64_t)nsm * 16;
+    k_col_exponents<<<(unsigned)(g < 1 ? 1 : g), 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t smem = residual_tc_smem_bytes();
+    e = cudaFuncSetAttribute(k_residual_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t grid = a.N < nsm ? a.N : nsm;
+    k_residual_tc<<<(unsigned)grid, kRtThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace crs
+
+// ---------------------------------------------------------------- C ABI
+
+namespace {
+
+size_t split_ws_bytes(int64_t N, int m, int k) {
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    return up(256) + up((size_t)N * m * sizeof(int)) + up((size_t)N * k * sizeof(int));
+}
+
+}  // namespace
+
+extern "C" int crsolve_residual_workspace_bytes(int64_t N, int32_t m, int32_t k, int32_t method, size_t *bytes) {
+    if (!bytes || N < 1 || m < 1 || k < 1) return CRSOLVE_EINVAL;
+    if (m > CRSOLVE_MAX_M || k > CRSOLVE_MAX_K) return CRSOLVE_EUNSUPPORTED;
+    if (method == CRSOLVE_RESIDUAL_FP64) {
+        *bytes = 0;
+        return CRSOLVE_OK;
+    }
+    if (method != CRSOLVE_RESIDUAL_SPLIT) return CRSOLVE_EUNSUPPORTED;
+    *bytes = split_ws_bytes(N, m, k);
+    return CRSOLVE_OK;
+}
+
+extern "C" int crsolve_residual(int64_t N, int32_t m, int32_t k, const crsolve_z *A, const crsolve_z *B,
+                                const crsolve_z *x, const crsolve_z *y, crsolve_z *r, int32_t method,
+                                void *workspace, size_t workspace_bytes, void *stream) {
+    if (N < 1 || m < 1 || k < 1 || !A || !x || !y || !r || (N > 1 && !B)) return CRSOLVE_EINVAL;
+    if (m > CRSOLVE_MAX_M || k > CRSOLVE_MAX_K) return CRSOLVE_EUNSUPPORTED;
+    if ((((uintptr_t)A | (uintptr_t)B | (uintptr_t)x | (uintptr_t)y | (uintptr_t)r) & 15u) ||
+        (const void *)r == (const void *)x)
+        return CRSOLVE_EINVAL;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    using crs::z2;
+    if (method == CRSOLVE_RESIDUAL_FP64)
+        return crs::launch_residual(N, m, k, reinterpret_cast<const z2 *>(A), reinterpret_cast<const z2 *>(B),
+                                    reinterpret_cast<const z2 *>(x), reinterpret_cast<const z2 *>(y),
+                                    reinterpret_cast<z2 *>(r), nsm, s) == cudaSuccess
+                   ? CRSOLVE_OK
+                   : CRSOLVE_ECUDA;
+    if (method != CRSOLVE_RESIDUAL_SPLIT) return CRSOLVE_EUNSUPPORTED;
+    if (!workspace || workspace_bytes < split_ws_bytes(N, m, k) || ((uintptr_t)workspace & 255u))
+        return CRSOLVE_EINVAL;
+    char *ws = static_cast<char *>(workspace);
+    auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    crs::ResidTcArgs a{};
+    a.N = N; a.m = m; a.k = k;
+    a.A = reinterpret_cast<const z2 *>(A);
+    a.B = reinterpret_cast<const z2 *>(B);
+    a.x = reinterpret_cast<const z2 *>(x);
+    a.y = reinterpret_cast<const z2 *>(y);
+    a.r = reinterpret_cast<z2 *>(r);
+    a.err = reinterpret_cast<int *>(ws);
+    a.erow = reinterpret_cast<int *>(ws + up(256));
+    a.ecol = reinterpret_cast<int *>(ws + up(256) + up((size_t)N * m * sizeof(int)));
+    if (cudaMemsetAsync(a.err, 0, sizeof(int), s) != cudaSuccess) return CRSOLVE_ECUDA;
+    if (crs::launch_row_exponents(a, nsm, s) != cudaSuccess) return CRSOLVE_ECUDA;
+    if (crs::launch_residual_tc(a, nsm, s) != cudaSuccess) return CRSOLVE_ECUDA;
+    int err = 0;
+    if (cudaMemcpyAsync(&err, a.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    return err ? CRSOLVE_ETIMEOUT : CRSOLVE_OK;
+}

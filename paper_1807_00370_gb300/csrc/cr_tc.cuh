@@ -61,14 +61,19 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
 }
 
 // Wait for the completion of the mbarrier phase with parity `phase`; gives up
-// after max_iter polls and returns false.
+// after max_iter polls or about two seconds of SM clock (4e9 cycles),
+// whichever comes first, and returns false.  (A poll of try_wait may itself
+// suspend the thread for a hardware time limit, so the poll count alone does
+// not bound the time.)
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase, int max_iter) {
     uint32_t done = 0;
+    const long long t0 = clock64();
     for (int it = 0; it < max_iter && !done; ++it) {
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
             : "=r"(done)
             : "r"(mbar), "r"(phase));
+        if (!done && clock64() - t0 > 4000000000ll) break;
     }
     return done != 0;
 }

@@ -52,7 +52,7 @@ struct crsolve_plan_s {
     int m = 0, kmax = 0, precision = 0, mt = 0, device = 0, nsm = 0;
     uint32_t flags = 0;
     std::vector<LevelPlan> lev;
-    size_t offStatus = 0, offWbd = 0, offCbd = 0;
+    size_t offStatus = 0, offDbg = 0, offWbd = 0, offCbd = 0;
     size_t offSA = 0, offSB = 0, offSY = 0, offSX = 0;
     size_t total = 0;
     char *ws = nullptr;
@@ -74,6 +74,7 @@ struct crsolve_plan_s {
     std::vector<LevelPlan> lev32;                // FP32 layout of levels < lT
     size_t offWbd32 = 0, offCbd32 = 0, offA32 = 0, offB32 = 0, offY32 = 0, offX32 = 0, offR64 = 0, offNorms = 0,
            offErr = 0;
+    size_t offP64 = 0, offW64 = 0, offDot = 0, offScal = 0, offErow = 0, offEcol = 0;   // conjugate gradients
     const crsolve_z *A64 = nullptr, *B64 = nullptr;  // the caller's FP64 system, read by the residual
     bool fallback = false;                       // FP32 factor broke down: everything in FP64
     int last_iters = 0;
@@ -142,6 +143,7 @@ crs::LevelArgs level_args(const crsolve_plan_s *p, int l, const z2 *A0, const z2
     a.yn = reinterpret_cast<z2 *>(ws + L.offYn);
     a.xn = reinterpret_cast<const z2 *>(ws + L.offXn);
     a.status = reinterpret_cast<unsigned long long *>(ws + p->offStatus);
+    a.dbg = reinterpret_cast<unsigned long long *>(ws + p->offDbg);
     return a;
 }
 
@@ -168,7 +170,24 @@ crs::LevelArgsT<float> level_args32(const crsolve_plan_s *p, int l) {
     a.x = reinterpret_cast<C *>(ws + (l == 0 ? p->offX32 : p->lev32[l - 1].offXn));
     a.status = reinterpret_cast<unsigned long long *>(ws + p->offStatus);
     a.err = reinterpret_cast<int *>(ws + p->offErr);
+    a.dbg = reinterpret_cast<unsigned long long *>(ws + p->offDbg);
     return a;
+}
+
+// The mixed form's residuals by exact splitting on the tensor cores (m > 32,
+// unless the plan asks for the FP64 pipe).
+bool mixed_uses_split(const crsolve_plan_s *p) { return p->m > 32 && !(p->flags & CRSOLVE_PLAN_FP64_RESIDUAL); }
+
+// Bounds-checked builds: clear the plan's out-of-range record (all ones =
+// none) before a factorisation; release builds enqueue nothing.
+int debug_reset(crsolve_plan_s *p, cudaStream_t s) {
+#ifdef CRSOLVE_DEBUG_BOUNDS
+    if (cudaMemsetAsync(p->ws + p->offDbg, 0xFF, sizeof(unsigned long long), s) != cudaSuccess) return CRSOLVE_ECUDA;
+#else
+    (void)p;
+    (void)s;
+#endif
+    return CRSOLVE_OK;
 }
 
 int ensure_prepared(crsolve_plan_s *p) {
@@ -651,6 +670,16 @@ int mixed_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
                          [&] { return crs::launch_factor_fix(a, p->nsm, s); })))
             return rc;
     }
+    if (mixed_uses_split(p)) {
+        // binary exponents of the rows of [B_{j-1} | A_j | B_j^H] for the residual's splitting
+        crs::ResidTcArgs ra{};
+        ra.N = p->N; ra.m = p->m; ra.k = 1;
+        ra.A = A; ra.B = B;
+        ra.erow = reinterpret_cast<int *>(ws + p->offErow);
+        ra.dbg = reinterpret_cast<unsigned long long *>(ws + p->offDbg);
+        if ((rc = launch(p, CRSOLVE_K_RESIDUAL, 0, p->N, s, [&] { return crs::launch_row_exponents(ra, p->nsm, s); })))
+            return rc;
+    }
     unsigned long long st = 0;
     int err = 0;
     if (cudaMemcpyAsync(&st, ws + p->offStatus, sizeof(st), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -733,69 +762,204 @@ int mixed_correction(crsolve_plan_s *p, int k, const z2 *r, cudaStream_t s) {
     return CRSOLVE_OK;
 }
 
-// Iterative refinement: x_0 = A~^{-1} y, then r_i = y - A x_i in FP64 and
-// x_{i+1} = x_i + A~^{-1} r_i.  With delta_i = |d_i|_inf / |x_{i+1}|_inf and
-// rho = delta_i / delta_{i-1} (the observed contraction), the error of
-// x_{i+1} is about rho * delta_i; stop when that is below 1e-13 (or delta_i
-// is at FP64 resolution).  The FP64 path takes over when refinement cannot
-// pay: no contraction (rho > 0.5 twice, or rho >= 1), or more steps predicted
-// at the observed rate (delta shrinking by rho per step) than the FP64
-// factor + solve would cost (mixed_step_cost).
+// Mixed-precision solve: preconditioned conjugate gradients (per right-hand-side
+// column; A is Hermitian positive definite) with the FP32 cyclic-reduction
+// solve A~^{-1} as preconditioner and FP64 matrix-vector products, the
+// iterative-refinement scheme of Carson and Higham ("A new analysis of
+// iterative refinement and its application to accurate solution of
+// ill-conditioned sparse linear systems", SIAM J. Sci. Comput. 39, 2017) with
+// CG in place of GMRES.  The preconditioner is applied in FP32 and so is not
+// exactly the same linear map from step to step: beta is the flexible
+// (Polak-Ribiere) one, (r_{i+1}, z_{i+1} - z_i) / (r_i, z_i).
 //
-// Cost of one refinement step relative to an FP64 factor + solve, in FP64
-// flops per block row: the FP64 residual 3 m^2 k complex multiply-adds
-// (24 m^2 k flop); the FP32 correction sweep 40 m^2 k flop, at about 1/8 of
-// its FP64 time on GB300 (FP32 levels 11 ms vs FP64 85 ms per sweep at
-// N = 2^14, m = 64, k = 32); the FP64 path 25.33 m^3 + 40 m^2 k.
-double mixed_step_cost(int m, int k) {
-    const double mm = (double)m * m, step = 24.0 * mm * k + 5.0 * mm * k;
+//   x_0 = A~^{-1} y,  r_0 = y - A x_0,  z_0 = p_0 = A~^{-1} r_0
+//   w_i = -A p_i,  alpha_i = (r_i, z_i) / (p_i, A p_i)
+//   x_{i+1} = x_i + alpha_i p_i,  r_{i+1} = r_i + alpha_i w_i
+//   z_{i+1} = A~^{-1} r_{i+1},  p_{i+1} = z_{i+1} + beta_i p_i
+//
+// The residuals and products are FP64-accurate: for m > 32 (and unless the
+// plan asks for the FP64 pipe) by exact splitting on the tensor cores
+// (cr_resid_tc.cu), else by FP64 FMA.  Stop rule, with delta_i the largest
+// relative correction max_c |alpha p|_c / |x|_c and rho = delta_i /
+// delta_{i-1}: stop when delta_i <= kMixedTol, a tenth of the stated bound
+// 1e-10 (the error left is about the next correction, smaller still), or when
+// the geometric extrapolation rho * delta_i of the remaining error is below
+// kMixedTol / 10 with delta_i <= 1e-8 and rho <= 1e-2.  The extrapolation is
+// trusted only that late: CG's first steps can shrink the correction by
+// orders of magnitude more than the steps after them (measured: 0.055 ->
+// 3.3e-7 -> 2.4e-9 at kappa ~ 1e6).  The FP64 path takes over when the
+// iteration does not contract (rho > 0.9 twice, rho >= 2, a non-positive
+// curvature, NaN) or when the steps still needed at the observed rate would
+// cost more than the FP64 factor + solve.
+//
+// CG updates the residual recursively (r += alpha w); rounding makes it
+// drift from the true y - A x by about u * (steps) * |A| |x|, which reaches
+// the solution multiplied by kappa.  The first correction estimates kappa
+// (delta_1 ~ kappa * u_FP32): above kMixedVerifyAbove (kappa >~ 1e3) the
+// first stop is followed by a restart from the true residual (a refinement
+// step in the sense of Carson and Higham), and the solve ends at the next
+// stop; the drift of the restarted run acts on a residual already reduced by
+// the error at the restart.  Measured at kappa ~ 1e6 without the restart:
+// corrections down to 1e-16, error 2.8e-9 against the oracle.
+constexpr double kMixedTol = 1e-11, kMixedExtrapFrom = 1e-8, kMixedVerifyAbove = 1e-4;
+
+// Cost of one step (an FP32 correction sweep and an FP64-accurate product)
+// relative to the FP64 factor + solve, in FP64-pipe flops per block row:
+// the FP32 sweep 40 m^2 k flop at about 1/8 of its FP64 time (measured), the
+// product 24 m^2 k flop on the FP64 pipe, or about 1/16 of that with the
+// tensor-core splitting; the FP64 path 25.33 m^3 + 40 m^2 k.
+double mixed_step_cost(int m, int k, bool split) {
+    const double mm = (double)m * m, step = (split ? 1.5 : 24.0) * mm * k + 5.0 * mm * k;
     return step / (25.33 * mm * m + 40.0 * mm * k);
+}
+
+// r = y - A x (y may be NULL: r = -A x), FP64-accurate.
+int mixed_residual(crsolve_plan_s *p, int k, const z2 *x, const z2 *y, z2 *r, cudaStream_t s) {
+    const WsMap ws = p->map();
+    if (!mixed_uses_split(p)) {
+        if (y) {
+            return launch(p, CRSOLVE_K_RESIDUAL, 0, p->N, s, [&] {
+                return crs::launch_residual(p->N, p->m, k, reinterpret_cast<const z2 *>(p->A64),
+                                            reinterpret_cast<const z2 *>(p->B64), x, y, r, p->nsm, s);
+            });
+        }
+        // -A x: the FP64 kernel subtracts from a zero right-hand side
+        if (cudaMemsetAsync(r, 0, p->N * (size_t)p->m * k * sizeof(z2), s) != cudaSuccess) return CRSOLVE_ECUDA;
+        return launch(p, CRSOLVE_K_RESIDUAL, 0, p->N, s, [&] {
+            return crs::launch_residual(p->N, p->m, k, reinterpret_cast<const z2 *>(p->A64),
+                                        reinterpret_cast<const z2 *>(p->B64), x, r, r, p->nsm, s);
+        });
+    }
+    crs::ResidTcArgs a{};
+    a.N = p->N; a.m = p->m; a.k = k;
+    a.A = reinterpret_cast<const z2 *>(p->A64);
+    a.B = reinterpret_cast<const z2 *>(p->B64);
+    a.x = x; a.y = y; a.r = r;
+    a.erow = reinterpret_cast<int *>(ws + p->offErow);
+    a.ecol = reinterpret_cast<int *>(ws + p->offEcol);
+    a.err = reinterpret_cast<int *>(ws + p->offErr);
+    a.dbg = reinterpret_cast<unsigned long long *>(ws + p->offDbg);
+    return launch(p, CRSOLVE_K_RESIDUAL, 0, p->N, s, [&] { return crs::launch_residual_tc(a, p->nsm, s); });
 }
 
 int mixed_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     const WsMap ws = p->map();
-    const int64_t n = p->N * (int64_t)p->m * k;
+    const int64_t rows = p->N * (int64_t)p->m, n = rows * k;
     unsigned long long *norms = reinterpret_cast<unsigned long long *>(ws + p->offNorms);
     z2 *r = reinterpret_cast<z2 *>(ws + p->offR64);
-    const crs::c2 *d = reinterpret_cast<const crs::c2 *>(ws + p->offX32);
-    double prev = 0.0, rho = 1.0;
-    int slow = 0, rc;
+    z2 *pd = reinterpret_cast<z2 *>(ws + p->offP64);
+    z2 *w = reinterpret_cast<z2 *>(ws + p->offW64);
+    const crs::c2 *z = reinterpret_cast<const crs::c2 *>(ws + p->offX32);
+    double *part = reinterpret_cast<double *>(ws + p->offDot);
+    double *alpha = reinterpret_cast<double *>(ws + p->offScal);
+    double *beta = alpha + p->kmax, *rz = beta + p->kmax, *rzc = rz + p->kmax;
+    int *errw = reinterpret_cast<int *>(ws + p->offErr);   // [0] a bounded wait gave up, [1] curvature lost
+    int *flag = errw + 1;
+    int rc;
+    const size_t kb = (size_t)k * sizeof(unsigned long long);
     p->last_iters = 0;
-    for (int it = 0; it < kMixedMaxIter; ++it) {
-        if (it > 0) {
-            if ((rc = launch(p, CRSOLVE_K_RESIDUAL, 0, p->N, s, [&] {
-                     return crs::launch_residual(p->N, p->m, k, reinterpret_cast<const z2 *>(p->A64),
-                                                 reinterpret_cast<const z2 *>(p->B64), x, y, r, p->nsm, s);
-                 })))
-                return rc;
-            p->last_iters = it;
-        }
-        if ((rc = mixed_correction(p, k, it == 0 ? y : r, s))) return rc;
-        if (cudaMemsetAsync(norms, 0, 2 * sizeof(unsigned long long), s) != cudaSuccess) return CRSOLVE_ECUDA;
-        if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s,
-                         [&] { return crs::launch_update(x, d, n, it == 0, norms, p->nsm, s); })))
+    p->last_delta = p->last_rho = 0.0;
+    if (cudaMemsetAsync(flag, 0, sizeof(int), s) != cudaSuccess) return CRSOLVE_ECUDA;
+    // x_0 = A~^{-1} y
+    if ((rc = mixed_correction(p, k, y, s))) return rc;
+    if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s,
+                     [&] { return crs::launch_update(x, z, n, 1, norms, p->nsm, s); })))
+        return rc;
+    // r_0 = y - A x_0, z_0 = A~^{-1} r_0, p_0 = z_0, rz = (r_0, z_0)
+    if ((rc = mixed_residual(p, k, x, y, r, s))) return rc;
+    p->last_iters = 1;
+    if ((rc = mixed_correction(p, k, r, s))) return rc;
+    if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s,
+                     [&] { return crs::launch_pcg_direction(pd, z, beta, n, k, 1, p->nsm, s); })))
+        return rc;
+    if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s, [&] {
+             return crs::launch_dot(r, z, rows, k, part, rz, 0, nullptr, nullptr, nullptr, p->nsm, s);
+         })))
+        return rc;
+    double prev = 0.0;
+    int slow = 0, since = 0;
+    bool verify = false, restarted = false;
+    std::vector<unsigned long long> hn(2 * (size_t)k);
+    for (int it = 1; it <= kMixedMaxIter; ++it) {
+        ++since;
+        // w = -A p, alpha = (r, z) / (p, A p)
+        if ((rc = mixed_residual(p, k, pd, nullptr, w, s))) return rc;
+        p->last_iters += 1;
+        if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s, [&] {
+                 return crs::launch_dot(pd, w, rows, k, part, alpha, 1, rz, nullptr, flag, p->nsm, s);
+             })))
             return rc;
-        unsigned long long hn[2];
-        if (cudaMemcpyAsync(hn, norms, sizeof(hn), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        // x += alpha p, r += alpha w, and the column maxima of the correction and of x
+        if (cudaMemsetAsync(norms, 0, 2 * kb, s) != cudaSuccess) return CRSOLVE_ECUDA;
+        if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s, [&] {
+                 return crs::launch_pcg_update(x, r, pd, w, alpha, n, k, norms, p->nsm, s);
+             })))
+            return rc;
+        int hflag[2] = {0, 0};
+        if (cudaMemcpyAsync(hn.data(), norms, 2 * kb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            cudaMemcpyAsync(hflag, errw, sizeof(hflag), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
             cudaStreamSynchronize(s) != cudaSuccess)
             return CRSOLVE_ECUDA;
-        double dn, xn;
-        memcpy(&dn, &hn[0], 8);
-        memcpy(&xn, &hn[1], 8);
-        const double delta = xn > 0 ? dn / xn : 0.0;
-        if (!(delta == delta)) break;                       // NaN: give up on FP32
-        if (it > 0) {
-            rho = prev > 0 ? delta / prev : 0.0;
-            p->last_delta = delta; p->last_rho = rho;
-            if (rho * delta <= 1e-13 || delta <= 4.4e-16) return CRSOLVE_OK;
-            slow = rho > 0.5 ? slow + 1 : 0;
-            if (slow >= 2 || !(rho < 1.0)) break;
-            // steps still needed for rho^n * delta <= 1e-13, against the fallback
-            const double need = std::ceil(std::log(1e-13 / (rho * delta)) / std::log(rho));
-            if (need * mixed_step_cost(p->m, k) > 1.0) break;
+        if (hflag[0]) return CRSOLVE_ETIMEOUT;
+        double delta = 0.0;
+        for (int c = 0; c < k; ++c) {
+            double dn, xn;
+            memcpy(&dn, &hn[c], 8);
+            memcpy(&xn, &hn[k + c], 8);
+            const double dc = xn > 0 ? dn / xn : (dn > 0 ? 1.0 : 0.0);
+            delta = (dc == dc && delta == delta) ? std::max(delta, dc) : NAN;
+        }
+        if (hflag[1] || !(delta == delta)) break;           // lost positive curvature or NaN: FP64
+        const double rho = since > 1 ? (prev > 0 ? delta / prev : 0.0) : 0.0;
+        p->last_delta = delta;
+        p->last_rho = rho;
+        if (it == 1) verify = delta > kMixedVerifyAbove;
+        // the correction itself below the tolerance, or (extrapolation) a fast,
+        // small contraction that puts the remaining error a decade below it
+        const bool extrap = since > 1 && delta <= kMixedExtrapFrom && rho <= 1e-2 && rho * delta <= 0.1 * kMixedTol;
+        if (delta <= kMixedTol || extrap) {
+            if (!verify || restarted) return CRSOLVE_OK;
+            // the recursive residual may have drifted from y - A x: restart
+            // from the true residual (one refinement step) and go on
+            restarted = true;
+            since = 0;
+            prev = 0.0;
+            slow = 0;
+            if ((rc = mixed_residual(p, k, x, y, r, s))) return rc;
+            p->last_iters += 1;
+            if ((rc = mixed_correction(p, k, r, s))) return rc;
+            if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s,
+                             [&] { return crs::launch_pcg_direction(pd, z, beta, n, k, 1, p->nsm, s); })))
+                return rc;
+            if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s, [&] {
+                     return crs::launch_dot(r, z, rows, k, part, rz, 0, nullptr, nullptr, nullptr, p->nsm, s);
+                 })))
+                return rc;
+            continue;
+        }
+        if (since > 1) {
+            slow = rho > 0.9 ? slow + 1 : 0;
+            if (slow >= 2 || !(rho < 2.0)) break;
+            if (rho < 1.0) {
+                // steps still needed for rho^n * delta <= kMixedTol, against the FP64 path
+                const double need = std::ceil(std::log(kMixedTol / (rho * delta)) / std::log(rho));
+                if (need * mixed_step_cost(p->m, k, mixed_uses_split(p)) > 1.0) break;
+            }
         }
         prev = delta;
-        p->last_delta = delta; p->last_rho = rho;
+        // beta = (r_{i+1}, z_{i+1} - z_i) / (r_i, z_i): (r_{i+1}, z_i) first, while z still holds z_i
+        if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s, [&] {
+                 return crs::launch_dot(r, z, rows, k, part, rzc, 0, nullptr, nullptr, nullptr, p->nsm, s);
+             })))
+            return rc;
+        if ((rc = mixed_correction(p, k, r, s))) return rc;
+        if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s, [&] {
+                 return crs::launch_dot(r, z, rows, k, part, beta, 2, rz, rzc, nullptr, p->nsm, s);
+             })))
+            return rc;
+        if ((rc = launch(p, CRSOLVE_K_UPDATE, 0, p->N, s,
+                         [&] { return crs::launch_pcg_direction(pd, z, beta, n, k, 0, p->nsm, s); })))
+            return rc;
     }
     // no convergence in mixed precision: factor and solve in FP64
     p->fallback = true;
@@ -822,6 +986,7 @@ void layout(crsolve_plan_s *p) {
     p->alev[0].clear();
     p->alev[1].clear();
     p->offStatus = take(cur, 256);
+    p->offDbg = take(cur, 256);
     if (alg1) {
         int L = 0;
         while ((int64_t(1) << L) < N) ++L;
@@ -909,8 +1074,14 @@ void layout(crsolve_plan_s *p) {
         p->offY32 = take(cur, N * mk * c32);
         p->offX32 = take(cur, N * mk * c32);
         p->offR64 = take(cur, N * mk * zsz);
-        p->offNorms = take(cur, 16);
+        p->offNorms = take(cur, 2 * (size_t)p->kmax * sizeof(unsigned long long));
         p->offErr = take(cur, 16);
+        p->offP64 = take(cur, N * mk * zsz);
+        p->offW64 = take(cur, N * mk * zsz);
+        p->offDot = take(cur, (size_t)crs::dot_partials(p->nsm) * p->kmax * sizeof(double));
+        p->offScal = take(cur, 5 * (size_t)p->kmax * sizeof(double));
+        p->offErow = take(cur, (size_t)N * m * sizeof(int));
+        p->offEcol = take(cur, (size_t)N * p->kmax * sizeof(int));
     }
     p->total = cur;
     p->scr_total = scur;
@@ -927,7 +1098,8 @@ int crsolve_plan_create(int64_t N, int32_t m, int32_t kmax, int32_t precision, u
     if (N < 1 || m < 1 || kmax < 1) return CRSOLVE_EINVAL;
     if (m > CRSOLVE_MAX_M || kmax > CRSOLVE_MAX_K) return CRSOLVE_EUNSUPPORTED;
     if (precision != CRSOLVE_FP64 && precision != CRSOLVE_MIXED) return CRSOLVE_EUNSUPPORTED;
-    if (flags & ~(uint32_t)(CRSOLVE_PLAN_HOST_STAGING | CRSOLVE_PLAN_ALG1)) return CRSOLVE_EINVAL;
+    if (flags & ~(uint32_t)(CRSOLVE_PLAN_HOST_STAGING | CRSOLVE_PLAN_ALG1 | CRSOLVE_PLAN_FP64_RESIDUAL))
+        return CRSOLVE_EINVAL;
     const bool alg1 = (flags & CRSOLVE_PLAN_ALG1) != 0;
     if (alg1 && ((N & (N - 1)) != 0 || precision != CRSOLVE_FP64)) return CRSOLVE_EUNSUPPORTED;
     crsolve_plan_s *p = new (std::nothrow) crsolve_plan_s();
@@ -993,6 +1165,7 @@ int crsolve_factor(crsolve_plan p, const crsolve_z *A, const crsolve_z *B, void 
     int rc = check_device(p);
     if (rc) return rc;
     if ((rc = ensure_prepared(p))) return rc;
+    if ((rc = debug_reset(p, static_cast<cudaStream_t>(stream)))) return rc;
     if (p->precision == CRSOLVE_MIXED && p->lT > 0)
         return mixed_factor(p, reinterpret_cast<const z2 *>(A), reinterpret_cast<const z2 *>(B),
                             static_cast<cudaStream_t>(stream));
@@ -1072,6 +1245,7 @@ int crsolve_solve_host(crsolve_plan p, int32_t k, const crsolve_z *A_host, const
     int rc = check_device(p);
     if (rc) return rc;
     if ((rc = ensure_prepared(p))) return rc;
+    if ((rc = debug_reset(p, static_cast<cudaStream_t>(stream)))) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     // the level-0 system is staged in the scratch region: a split plan can
     // rebuild its coarse levels from level keep >= 1 later, not from level 0
@@ -1214,6 +1388,24 @@ int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t 
     *nb_factor = ts.nb_factor; *nb_solve = ts.nb_solve; *kc = ts.kc_max; *threads = ts.threads;
     *threads_solve = ts.threads_solve;
     return CRSOLVE_OK;
+}
+
+int crsolve_debug_bounds(crsolve_plan p, uint64_t *record, void *stream) {
+    if (!p || !record) return CRSOLVE_EINVAL;
+#ifdef CRSOLVE_DEBUG_BOUNDS
+    if (!p->ws) return CRSOLVE_ENOMEM;
+    unsigned long long v = 0;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaMemcpyAsync(&v, p->ws + p->offDbg, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    *record = v;
+    return CRSOLVE_OK;
+#else
+    (void)stream;
+    *record = ~0ull;
+    return CRSOLVE_EUNSUPPORTED;
+#endif
 }
 
 int crsolve_plan_levels(crsolve_plan p, int32_t *nlev, int64_t *sizes) {

@@ -11,16 +11,19 @@
 // GPU that loads the library holds that array until the process exits.
 //
 // Rules for callers:
-//   - The first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress (with that device current) and raises the kernels'
-//     shared-memory limits; make that first call before any stream capture.
+//   - Every call looks up the array's device address with
+//     cudaGetSymbolAddress, with the caller's device current, and raises the
+//     shared-memory limits of the kernels it launches.  Nothing is cached
+//     between calls, so the address is never stale (after cudaDeviceReset, or
+//     under another context of the same device).  The first call on a device
+//     also loads the library's kernels onto it: make that first call before
+//     any stream capture.
 //   - All calls share the array and it keeps the last call's contents: calls
 //     whose work overlaps on the GPU (different streams, or different host
 //     threads on one device) race.  Serialise them.
 //   - A system whose intermediates do not fit in the array is rejected with
 //     CRSOLVE_ENOMEM before anything is launched.
 #include <cstdint>
-#include <mutex>
 
 #include "crsolve.h"
 #include "cr_launch.h"
@@ -30,14 +33,9 @@ using crs::z2;
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = size_t(32) << 20;
-constexpr int kMaxDevices = 64;
 constexpr int kMaxLevels = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
-
-std::mutex g_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
-bool g_prepared[kMaxDevices][5] = {};
 
 struct NaLevel {
     int64_t Nl, no, ne;
@@ -50,8 +48,6 @@ size_t bump(size_t &cursor, size_t bytes) {
     return off;
 }
 
-int mt_index(int mt) { return mt == 4 ? 0 : mt == 8 ? 1 : mt == 16 ? 2 : mt == 32 ? 3 : 4; }
-
 }  // namespace
 
 extern "C" int crsolve_solve_noalloc(int64_t N, int32_t m, int32_t k, const crsolve_z *A, const crsolve_z *B,
@@ -61,12 +57,19 @@ extern "C" int crsolve_solve_noalloc(int64_t N, int32_t m, int32_t k, const crso
     if ((((uintptr_t)A | (uintptr_t)y | (uintptr_t)x | (uintptr_t)B) & 15u) || (const void *)x == (const void *)y)
         return CRSOLVE_EINVAL;
 
+    // The level-0 factors and the level-1 system alone take N complex m x m
+    // blocks, so a larger N cannot fit.  Rejecting it first keeps every size
+    // product below from overflowing (and the breakdown record's 40-bit block
+    // index exact).
+    if ((uint64_t)N > kNoAllocScratchBytes / ((size_t)m * m * sizeof(crsolve_z)) || (uint64_t)N >= (1ull << 40))
+        return CRSOLVE_ENOMEM;
     // level schedule and the layout of the fixed array (no heap, no device allocation)
     NaLevel lev[kMaxLevels];
     int nlev = 0;
     const size_t zsz = sizeof(crsolve_z), mm = (size_t)m * m, mk = (size_t)m * k;
     size_t cur = 0;
     const size_t offStatus = bump(cur, 256);
+    const size_t offDbg = bump(cur, 256);
     for (int64_t Nl = N;; Nl /= 2) {
         NaLevel &L = lev[nlev++];
         L.Nl = Nl; L.no = (Nl + 1) / 2; L.ne = Nl / 2;
@@ -86,27 +89,24 @@ extern "C" int crsolve_solve_noalloc(int64_t N, int32_t m, int32_t k, const crso
     if (cur > kNoAllocScratchBytes) return CRSOLVE_ENOMEM;
 
     int dev = -1, nsm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return CRSOLVE_ECUDA;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return CRSOLVE_ECUDA;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return CRSOLVE_ECUDA;
     const int mt = crs::pick_mt(m);
-    char *ws = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_mu);
-        if (!g_scratch_ptr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CRSOLVE_ECUDA;
-            g_scratch_ptr[dev] = p;
-        }
-        if (!g_prepared[dev][mt_index(mt)]) {
-            if (crs::prepare_kernels(mt) != cudaSuccess) return CRSOLVE_ECUDA;
-            g_prepared[dev][mt_index(mt)] = true;
-        }
-        ws = static_cast<char *>(g_scratch_ptr[dev]);
-    }
+    // Set-up, with the caller's device current: the device address of the
+    // array (in host code g_noalloc_scratch names a host-side stand-in, not
+    // device memory) and the kernels' shared-memory limits.
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CRSOLVE_ECUDA;
+    if (crs::prepare_kernels(mt) != cudaSuccess) return CRSOLVE_ECUDA;
+    char *ws = static_cast<char *>(p);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     unsigned long long *status = reinterpret_cast<unsigned long long *>(ws + offStatus);
+    unsigned long long *dbg = reinterpret_cast<unsigned long long *>(ws + offDbg);
     // the array keeps the previous call's contents: the status must start as "no breakdown"
     if (cudaMemsetAsync(status, 0xFF, sizeof(unsigned long long), s) != cudaSuccess) return CRSOLVE_ECUDA;
+#ifdef CRSOLVE_DEBUG_BOUNDS
+    if (cudaMemsetAsync(dbg, 0xFF, sizeof(unsigned long long), s) != cudaSuccess) return CRSOLVE_ECUDA;
+#endif
 
     auto args = [&](int l) {
         crs::LevelArgs a{};
@@ -127,6 +127,7 @@ extern "C" int crsolve_solve_noalloc(int64_t N, int32_t m, int32_t k, const crso
         a.xn = reinterpret_cast<const z2 *>(ws + L.offXn);
         a.x = l == 0 ? reinterpret_cast<z2 *>(x) : reinterpret_cast<z2 *>(ws + lev[l - 1].offXn);
         a.status = status;
+        a.dbg = dbg;
         return a;
     };
     for (int l = 0; l < nlev; ++l) {

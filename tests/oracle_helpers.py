@@ -119,3 +119,64 @@ def shift_blocks(A, blocks, excess=0.5):
         lam = np.linalg.eigvalsh(herm_from_lower(A[b - 1])).min()
         A[b - 1] -= (lam + excess) * np.eye(m)
     return A
+
+
+def _split27(a):
+    c = 134217729.0 * a          # 2^27 + 1 (Veltkamp)
+    hi = c - (c - a)
+    return hi, a - hi
+
+
+def _two_prod(a, b):
+    """a * b = p + e exactly (Dekker), elementwise on float64 arrays."""
+    p = a * b
+    ah, al = _split27(a)
+    bh, bl = _split27(b)
+    return p, ((ah * bh - p) + ah * bl + al * bh) + al * bl
+
+
+def _two_sum(a, b):
+    """a + b = s + e exactly (Knuth), elementwise."""
+    s = a + b
+    bb = s - a
+    return s, (a - (s - bb)) + (b - bb)
+
+
+def coupling_blocks(A, B, j):
+    """The three complex blocks [B_{j-1} | A_j | B_j^H] of block row j (A_j
+    Hermitian from its lower triangle), zero outside the matrix."""
+    N, m, _ = A.shape
+    z = np.zeros((m, m), np.complex128)
+    return (B[j - 1] if j > 0 else z, herm_from_lower(A[j]), B[j].conj().T if j + 1 < N else z)
+
+
+def residual_dd(A, B, x, y, rows=None):
+    """r = y - A x for the listed block rows (default all), every real
+    product and sum carried as an unevaluated pair of doubles (Dot2 of Ogita,
+    Rump and Oishi): the result is the exact residual rounded, up to a
+    relative 2^-104-level error in the sums.  Returns [len(rows)][m][k]."""
+    N, m, k = y.shape
+    rows = list(range(N)) if rows is None else list(rows)
+    out = np.empty((len(rows), m, k), np.complex128)
+    for n, j in enumerate(rows):
+        sr, er = y[j].real.copy(), np.zeros((m, k))
+        si, ei = y[j].imag.copy(), np.zeros((m, k))
+        for b, M in enumerate(coupling_blocks(A, B, j)):
+            jb = j - 1 + b
+            if jb < 0 or jb >= N:
+                continue
+            X = x[jb]
+            for s in range(m):
+                mr, mi = M[:, s].real[:, None], M[:, s].imag[:, None]
+                xr, xi = X[s].real[None, :], X[s].imag[None, :]
+                # re: - (mr xr - mi xi); im: - (mr xi + mi xr)
+                for (u, v, sg, tgt) in ((mr, xr, -1.0, 0), (mi, xi, 1.0, 0), (mr, xi, -1.0, 1), (mi, xr, -1.0, 1)):
+                    p, e = _two_prod(np.broadcast_to(u, (m, k)) * sg, np.broadcast_to(v, (m, k)))
+                    if tgt == 0:
+                        sr, e2 = _two_sum(sr, p)
+                        er = er + (e + e2)
+                    else:
+                        si, e2 = _two_sum(si, p)
+                        ei = ei + (e + e2)
+        out[n] = (sr + er) + 1j * (si + ei)
+    return out

@@ -53,7 +53,7 @@ def _create(N, m, k, prec=0, flags=0):
     (8, 65, 1, 0, 0, nat.CRSOLVE_EUNSUPPORTED),
     (8, 4, 5000, 0, 0, nat.CRSOLVE_EUNSUPPORTED),
     (8, 4, 1, 7, 0, nat.CRSOLVE_EUNSUPPORTED),
-    (8, 4, 1, 0, 4, nat.CRSOLVE_EINVAL),
+    (8, 4, 1, 0, 8, nat.CRSOLVE_EINVAL),
     # Algorithm 1 needs N a power of two and FP64
     (6, 4, 1, 0, nat.CRSOLVE_PLAN_ALG1, nat.CRSOLVE_EUNSUPPORTED),
     (8, 4, 1, nat.CRSOLVE_MIXED, nat.CRSOLVE_PLAN_ALG1, nat.CRSOLVE_EUNSUPPORTED),
@@ -72,3 +72,10 @@ def test_null_plan_is_rejected():
     assert lib.crsolve_info_get(None, None, None) == nat.CRSOLVE_EINVAL
     assert lib.crsolve_workspace_bytes(None, None) == nat.CRSOLVE_EINVAL
     assert nat.strerror(nat.CRSOLVE_NOT_PD).startswith("matrix is not positive definite")
+
+
+def test_peak_probe_rejects_bad_arguments_without_a_gpu():
+    lib = nat.load()
+    v = ctypes.c_double()
+    assert lib.crsolve_peak_probe(7, ctypes.byref(v), None, None, None) == nat.CRSOLVE_EINVAL
+    assert lib.crsolve_peak_probe(nat.CRSOLVE_PROBE_FP64_FMA, None, None, None, None) == nat.CRSOLVE_EINVAL

@@ -24,10 +24,10 @@ BOUND = 1e-10
 SHIFTS = os.path.join(os.path.dirname(__file__), "golden", "kappa_shifts.json")
 
 
-def _mixed(A, B, y):
+def _mixed(A, B, y, flags=0):
     N, m, k = y.shape
     dA, dB, dy = to_dev(A, B if N > 1 else None, y)
-    plan = crs.Plan(N, m, k, precision=nat.CRSOLVE_MIXED)
+    plan = crs.Plan(N, m, k, precision=nat.CRSOLVE_MIXED, flags=flags)
     crs.crsolve_factor(plan, dA, dB)
     x = crs.crsolve_solve(plan, dy)
     return x.cpu().numpy(), crs.crsolve_info_get(plan), crs.crsolve_mixed_stats(plan)
@@ -79,10 +79,21 @@ def test_mixed_at_controlled_kappa(cuda_ok, kappa):
     err = rel_err(x, xo)
     print(f"kappa~{kappa:.0e}: rel err vs oracle {err:.2e}, stats {st}")
     assert err <= BOUND, (err, st)
-    # refinement that cannot beat the FP64 path hands over early: at the
-    # latest once the second residual has shown the contraction rate
-    if st["fp64_fallback"]:
-        assert st["iterations"] <= 2, st
+    # the conjugate-gradient refinement converges in mixed precision at every kappa
+    assert not st["fp64_fallback"], st
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e6])
+def test_mixed_with_fp64_pipe_residuals(cuda_ok, kappa):
+    """The same refinement with every residual and product on the FP64 pipe
+    (CRSOLVE_PLAN_FP64_RESIDUAL) instead of the tensor-core splitting."""
+    case, shift = _kappa_case("mixed_N2p10_m64_k32", kappa)
+    A, B, y = synthetic.gen_system(case["N"], case["m"], case["k"], case["seed"], shift=shift)
+    x, info, st = _mixed(A, B, y, flags=nat.CRSOLVE_PLAN_FP64_RESIDUAL)
+    xo, io = oracle.cr_solve(A, B, y)
+    assert info == io and info["status"] == 0
+    assert rel_err(x, xo) <= BOUND, st
+    assert not st["fp64_fallback"], st
 
 
 def test_plain_fp64_at_kappa_1e6(cuda_ok):
