@@ -381,17 +381,25 @@ int crsolve_mixed_stats(crsolve_plan p, int32_t *iterations, double *delta, doub
  *   method CRSOLVE_RESIDUAL_FP64: FP64 fused multiply-adds; no workspace;
  *   asynchronous.
  *   method CRSOLVE_RESIDUAL_SPLIT: every product exact on the BF16 tensor
- *   cores (error-free splitting of Ozaki, Ogita, Oishi and Rump, 2012: each
- *   entry cut into nine 6-bit integer slices on a per-row / per-column binary
- *   grid, slice products accumulated exactly in FP32 in tensor memory), then
- *   y - A x with two FP64 roundings; the dropped slice products and the
- *   truncation add less than about 2^-50 K max|row of A| max|column of x|
- *   (K = 6m), within the error bound of an FP64 dot product.  Needs a
+ *   cores (error-free splitting of Ozaki, Ogita, Oishi and Rump, 2012: a
+ *   matrix entry cut into ten 6-bit integer slices on a per-row binary grid
+ *   of 60 bits, an x entry into nine on a per-column grid of 54 bits, slice
+ *   products with i + j <= 11 accumulated exactly in FP32 in tensor memory),
+ *   then y - A x formed exactly in 128-bit integers and rounded once; the
+ *   dropped slice products and the grids add less than about 2^-50 K
+ *   max|row of A| max|column of x| (K = 6m), within the error bound of an
+ *   FP64 dot product, and, unlike an FP64 residual, nothing is rounded per
+ *   product or per sum.  Needs a
  *   256-byte aligned device workspace of crsolve_residual_workspace_bytes;
  *   synchronises the stream and returns CRSOLVE_ETIMEOUT if a bounded wait of
  *   the tensor-core pipeline gave up.  The paper has no counterpart.
+ *   method CRSOLVE_RESIDUAL_SPLIT_IMAGE: the same result, bit for bit, with
+ *   the matrix slices first written to the workspace in the tensor cores'
+ *   shared-memory layout (about 0.94 MiB per block row) and then copied in by
+ *   bulk copies; the mixed-precision form does this once per factorisation
+ *   and reuses the slices for every residual of its refinement.
  */
-enum { CRSOLVE_RESIDUAL_FP64 = 0, CRSOLVE_RESIDUAL_SPLIT = 1 };
+enum { CRSOLVE_RESIDUAL_FP64 = 0, CRSOLVE_RESIDUAL_SPLIT = 1, CRSOLVE_RESIDUAL_SPLIT_IMAGE = 2 };
 int crsolve_residual_workspace_bytes(int64_t N, int32_t m, int32_t k, int32_t method, size_t *bytes);
 int crsolve_residual(int64_t N, int32_t m, int32_t k, const crsolve_z *A, const crsolve_z *B, const crsolve_z *x,
                      const crsolve_z *y, crsolve_z *r, int32_t method, void *workspace, size_t workspace_bytes,

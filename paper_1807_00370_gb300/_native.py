@@ -30,6 +30,7 @@ CRSOLVE_PLAN_ALG1 = 2
 CRSOLVE_PLAN_FP64_RESIDUAL = 4
 CRSOLVE_RESIDUAL_FP64 = 0
 CRSOLVE_RESIDUAL_SPLIT = 1
+CRSOLVE_RESIDUAL_SPLIT_IMAGE = 2
 CRSOLVE_PROBE_FP64_FMA = 0
 CRSOLVE_PROBE_FP32_FMA = 1
 CRSOLVE_MAX_M = 64

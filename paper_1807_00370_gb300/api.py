@@ -250,8 +250,9 @@ def crsolve_launch_count(plan: Plan) -> int:
 
 def crsolve_residual(A: torch.Tensor, B: torch.Tensor | None, x: torch.Tensor, y: torch.Tensor,
                      method: str = "split", r: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """r = y - A x for the block-tridiagonal system (method "fp64" or "split":
-    exact slice products on the tensor cores, FP64 accuracy)."""
+    """r = y - A x for the block-tridiagonal system (method "fp64", "split":
+    exact slice products on the tensor cores, or "split_image": the same with
+    the matrix slices precomputed in the workspace)."""
     N, m, _ = A.shape
     k = x.shape[-1]
     _need(A, (N, m, m), "A")
@@ -261,7 +262,8 @@ def crsolve_residual(A: torch.Tensor, B: torch.Tensor | None, x: torch.Tensor, y
     _need(y, (N, m, k), "y", A.device)
     if r is None:
         r = torch.empty_like(y)
-    code = {"fp64": nat.CRSOLVE_RESIDUAL_FP64, "split": nat.CRSOLVE_RESIDUAL_SPLIT}[method]
+    code = {"fp64": nat.CRSOLVE_RESIDUAL_FP64, "split": nat.CRSOLVE_RESIDUAL_SPLIT,
+            "split_image": nat.CRSOLVE_RESIDUAL_SPLIT_IMAGE}[method]
     lib = nat.load()
     nbytes = ctypes.c_size_t()
     nat.check(lib.crsolve_residual_workspace_bytes(N, m, k, code, ctypes.byref(nbytes)),

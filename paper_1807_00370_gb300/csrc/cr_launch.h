@@ -89,9 +89,15 @@ struct ResidTcArgs {
     int *erow, *ecol;
     int *err;      // set to 1 if a bounded wait gave up
     unsigned long long *dbg;   // bounds-checked builds: first out-of-range access
+    // optional: the matrix slices of every (block row, K-chunk) precomputed in
+    // the shared-memory layout (residual_image_bytes(N), launch_matrix_image);
+    // the product then copies them in instead of cutting the matrix each time
+    const unsigned char *img;
 };
 size_t residual_tc_smem_bytes();
+size_t residual_image_bytes(int64_t N);
 cudaError_t launch_row_exponents(const ResidTcArgs &a, int nsm, cudaStream_t s);
+cudaError_t launch_matrix_image(const ResidTcArgs &a, unsigned char *img, int nsm, cudaStream_t s);
 cudaError_t launch_residual_tc(const ResidTcArgs &a, int nsm, cudaStream_t s);
 // Adjoint outer products gA, gB from x and gy.
 cudaError_t launch_adjoint_outer(int64_t N, int m, int k, const z2 *x, const z2 *gy, z2 *gA,

@@ -29,23 +29,26 @@
 //     refinement step, so the refinement converges to the solution of the
 //     perturbed matrix and the error is multiplied by kappa; an error of x
 //     changes with x and is not.
-//   * Products: for every slice pair (i, j) with d = i + j <= 9 the MMA
-//     accumulates q_i t_j into the FP32 accumulator acc_d in tensor memory.
-//     A diagonal holds at most 9 pairs, so |acc_d| <= 9 * 384 * 63^2 < 2^24:
-//     every partial sum is an exact integer in FP32 and the accumulators
-//     hold the exact sums.  Slice i is multiplied by the x slices
-//     t_0..t_{min(8, 9-i)} in one MMA (two when that is wider than 256
-//     columns) whose accumulator address is acc_i, so each product lands in
-//     acc_{i+j}.
-//   * Epilogue (integer): A x = (p0 2^30 + p1) 2^(E + F - 64) with p0, p1
-//     the exact integers sum_{d<=4} acc_d 2^(6(4-d)) and sum_{d>=5} acc_d
-//     2^(6(9-d)); y goes onto the same grid and r = y - A x is formed exactly
-//     in 128-bit integers and rounded once.  So the residual is more precise
-//     than an FP64 one (whose products and sums each round): besides the final
-//     rounding, only the dropped pairs i + j > 9 and the rounding of entries
-//     onto their grids remain, less than about 2^-51 * K * max|row| *
-//     max|column| in all.  Iterative refinement with such a residual is not
-//     limited to kappa * u_FP64 (Carson and Higham's extra-precise residual).
+//   * Products: for every slice pair (i, j) with d = i + j <= 11 the MMA
+//     accumulates q_i t_j into the FP32 accumulator acc_d in tensor memory
+//     (69 of the 90 pairs).  A diagonal holds at most 9 pairs, so |acc_d| <=
+//     9 * 384 * 63^2 < 2^24: every partial sum is an exact integer in FP32
+//     and the accumulators hold the exact sums.  Slice i is multiplied by the
+//     x slices t_0..t_{min(8, 11-i)} in one MMA (two when that is wider than
+//     256 columns) whose accumulator address is acc_i, so each product lands
+//     in acc_{i+j}.  The dropped pairs i + j >= 12 are below 2^-62 of the
+//     product of any entry within 2^-7 of its row's largest and its x.  (With
+//     d <= 9 they were ~2^-53 of such products, and always of the same sign as
+//     the product: a systematic shrink of A that refinement converges to and
+//     kappa amplifies, 8.6e-11 at kappa ~ 1e6.)
+//   * Epilogue (integer): A x = T 2^(E + F - 76) with the exact integer
+//     T = sum_d acc_d 2^(6(11-d)) (128-bit); y goes onto the same grid and
+//     r = y - A x is formed exactly in 128-bit integers and rounded once.
+//     So the residual is more precise than an FP64 one (whose products and
+//     sums each round): besides the final rounding only the rounding of
+//     entries onto their grids and the dropped pairs remain.  Iterative
+//     refinement with such a residual is not limited to kappa * u_FP64
+//     (Carson and Higham's extra-precise residual).
 //
 // Data flow per CTA (persistent over block rows, one CTA per SM): 16 warps cut
 // a K-chunk of 32 into slices in shared memory (double-buffered, K-major, no
@@ -65,7 +68,7 @@ namespace {
 constexpr int kRtM = 128;                                // MMA rows
 constexpr int kRtNSA = 10;                               // slices of a matrix entry (60-bit grid)
 constexpr int kRtNSX = 9;                                // slices of an x entry (54-bit grid)
-constexpr int kRtND = 10;                                // slice-product diagonals d = i + j kept
+constexpr int kRtND = 12;                                // slice-product diagonals d = i + j kept
 constexpr int kRtNC = 32;                                // right-hand-side columns per pass
 constexpr int kRtKC = 32;                                // real K per chunk (16 complex columns)
 constexpr int kRtASlice = kRtM * kRtKC * 2;              // 8192 bytes per matrix slice per chunk
@@ -73,7 +76,7 @@ constexpr int kRtAStage = kRtNSA * kRtASlice;            // 81920 bytes of matri
 constexpr int kRtBStage = kRtNSX * kRtNC * kRtKC * 2;    // 18432 bytes of x slices per chunk
 constexpr int kRtStage = kRtAStage + kRtBStage;
 constexpr int kRtThreads = 512;
-constexpr int kRtTmemCols = 512;                         // ten accumulators of 32 columns (320), rounded
+constexpr int kRtTmemCols = 512;                         // twelve accumulators of 32 columns (384), rounded
 constexpr int kExpZero = -4096, kExpNonFinite = 4096;    // exponent of an all-zero / non-finite set
 constexpr int kRtWaitPolls = 1 << 24;
 
@@ -107,11 +110,17 @@ __device__ __forceinline__ unsigned long long fixq(double v, int E) {
     return (S + (1ull << (-sh - 1))) >> (-sh);
 }
 
-// BF16 bits of the integer mag (0..63) with the sign bit sg (0 or 0x8000).
-__device__ __forceinline__ uint32_t bf16_int(uint32_t mag, uint32_t sg) {
-    const float f = __uint_as_float(0x4B000000u | mag) - 8388608.0f;
-    return (__float_as_uint(f) >> 16) | sg;
+// FP32 bits of the signed integer (mag 0..63, sign from base): base is
+// 0x4B000000 (2^23) with the entry's sign bit, off = -2^23 with the same
+// sign, so (2^23 + mag) - 2^23 = mag exactly; its high 16 bits are the BF16
+// value (exact: 6 significant bits).  Integer and FP32 pipes only.
+__device__ __forceinline__ uint32_t f32_int(uint32_t mag, uint32_t base, float off) {
+    return __float_as_uint(__uint_as_float(base | mag) + off);
 }
+// The high halves of two FP32 words as a BF16 pair (lo in the low half).
+__device__ __forceinline__ uint32_t bf16_pair(uint32_t lo, uint32_t hi) { return __byte_perm(lo, hi, 0x7632); }
+// Sign bit of a double from its bits (no FP64 instruction).
+__device__ __forceinline__ uint32_t dsign(double v) { return (uint32_t)((unsigned long long)__double_as_longlong(v) >> 63) << 31; }
 
 // Byte offset of element (r, k) of a K-major, unswizzled tile of 16-bit
 // elements with kRtKC columns: core matrices of 8 rows x 8 elements (16 bytes
@@ -154,6 +163,19 @@ __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;"); }
 
+// One arrival on the mbarrier that also announces `bytes` of transaction count.
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+
+// Bulk copy of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global to this CTA's shared memory, completing on the mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
 // 2^e as a double (0 below the subnormal range, Inf above the normal one).
 __device__ __forceinline__ double pow2(int e) {
     if (e >= -1022 && e <= 1023) return __longlong_as_double((long long)(e + 1023) << 52);
@@ -180,7 +202,7 @@ __device__ __forceinline__ bool rin(const ResidTcArgs &a, int which, int64_t idx
 #endif
 }
 
-// The product's fixed-point sum T = p0 2^30 + p1 (an exact integer) and y,
+// The product's fixed-point sum T (an exact integer) and y,
 // combined into r = y - T 2^se with a single rounding: y goes onto the same
 // grid 2^se (exactly, unless its bits reach below the grid, which lies about
 // 2^-66 of the product's largest term under it), the difference is formed
@@ -188,7 +210,7 @@ __device__ __forceinline__ bool rin(const ResidTcArgs &a, int which, int64_t idx
 // even).  Returns false (and the caller falls back to FP64 arithmetic) for a
 // non-finite y, a y far above the product, or a result outside the normal
 // double range.
-__device__ __forceinline__ bool resid_exact(double y, long long p0, long long p1, int se, double &out) {
+__device__ __forceinline__ bool resid_exact(double y, __int128 T, int se, double &out) {
     const unsigned long long yb = (unsigned long long)__double_as_longlong(y);
     const int eyb = (int)((yb >> 52) & 0x7FF);
     if (eyb == 0x7FF) return false;
@@ -206,7 +228,7 @@ __device__ __forceinline__ bool resid_exact(double y, long long p0, long long p1
         else if (sy > -60) Y = (__int128)((My + (1ull << (-sy - 1))) >> (-sy));
     }
     if (yb >> 63) Y = -Y;
-    const __int128 R = Y - (((__int128)p0 << 30) + (__int128)p1);
+    const __int128 R = Y - T;
     if (R == 0) {
         out = 0.0;
         return true;
@@ -252,13 +274,49 @@ __device__ __forceinline__ z2 coupling(const ResidTcArgs &a, int64_t j, int b, i
         if (!rin(a, kDbgA, o)) return zmk(0.0, 0.0);
         if (s < i) return __ldg(a.A + o);
         if (s == i) return zmk(__ldg(&a.A[o].x), 0.0);
-        const z2 v = __ldg(a.A + o);
-        return zmk(v.x, -v.y);
+        return zconj(__ldg(a.A + o));        // sign flip on the integer pipe
     }
     const int64_t o = j * mm + (int64_t)s * m + i;
     if (j + 1 >= a.N || !rin(a, kDbgB, o)) return zmk(0.0, 0.0);
-    const z2 v = __ldg(a.B + o);
-    return zmk(v.x, -v.y);
+    return zconj(__ldg(a.B + o));
+}
+
+// Cut matrix entry v (row i, complex column sl of a K-chunk; row exponent E)
+// into its ten slices and store them as BF16 pairs in the ten tiles at dst
+// (shared memory, or a precomputed image in global memory with the same
+// layout): real row i gets (Re M, -Im M), imaginary row i + 64 (Im M, Re M).
+__device__ __forceinline__ void slice_matrix_entry(z2 v, int E, int i, int sl, unsigned char *dst) {
+    const unsigned long long qr = fixq<60>(v.x, E), qi = fixq<60>(v.y, E);
+    const uint32_t sr = dsign(v.x), si = dsign(v.y);
+    const uint32_t baser = 0x4B000000u | sr, basei = 0x4B000000u | si;
+    const float offr = __uint_as_float(0xCB000000u ^ sr), offi = __uint_as_float(0xCB000000u ^ si);
+    const int o_re = kmaj16(i, 2 * sl), o_im = kmaj16(i + 64, 2 * sl);
+#pragma unroll
+    for (int n = 0; n < kRtNSA; ++n) {
+        const int sh = 54 - 6 * n;
+        const uint32_t mr = (uint32_t)(qr >> sh) & 63u, mi = (uint32_t)(qi >> sh) & 63u;
+        const uint32_t fr = f32_int(mr, baser, offr), fi = f32_int(mi, basei, offi);
+        unsigned char *An = dst + n * kRtASlice;
+        *reinterpret_cast<uint32_t *>(An + o_re) = bf16_pair(fr, fi ^ 0x80000000u);
+        *reinterpret_cast<uint32_t *>(An + o_im) = bf16_pair(fi, fr);
+    }
+}
+
+// Precomputed matrix slices: image (j, q) (block row j, K-chunk q) holds the
+// kRtAStage bytes that the product would cut into shared memory for that
+// chunk.  One CTA of kRtThreads per image, grid-stride over the 12 N images.
+__global__ void __launch_bounds__(kRtThreads) k_matrix_image(ResidTcArgs a, unsigned char *img) {
+    const int m = a.m;
+    for (int64_t g = blockIdx.x; g < a.N * 12; g += gridDim.x) {
+        const int64_t j = g / 12;
+        const int q = (int)(g - j * 12), b = q >> 2, s0 = (q & 3) * 16;
+        unsigned char *dst = img + g * (int64_t)kRtAStage;
+        for (int e = threadIdx.x; e < 64 * 16; e += kRtThreads) {
+            const int i = a_row(e), sl = a_col(e);
+            const int E = i < m ? a.erow[j * m + i] : kExpZero;
+            slice_matrix_entry(coupling(a, j, b, i, s0 + sl), E, i, sl, dst);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(256) k_row_exponents(ResidTcArgs a) {
@@ -290,12 +348,14 @@ __global__ void __launch_bounds__(256) k_col_exponents(ResidTcArgs a) {
     }
 }
 
+template <bool kImg>
 __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(base + 2 * kRtStage);   // [2]
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + 2 * kRtStage + 16);
-    int *sEr = reinterpret_cast<int *>(base + 2 * kRtStage + 32);        // [64]
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(base + 2 * kRtStage);   // [2] MMAs of a buffer done
+    uint64_t *fbar = mbar + 2;                                           // [2] image copy into a buffer done
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + 2 * kRtStage + 32);
+    int *sEr = reinterpret_cast<int *>(base + 2 * kRtStage + 64);        // [64]
     int *sEc = sEr + 64;                                                  // [32]
     int *sAbort = sEc + kRtNC;
 
@@ -306,6 +366,8 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
         mbar_init(smem_u32(&mbar[1]), 1);
+        mbar_init(smem_u32(&fbar[0]), 1);
+        mbar_init(smem_u32(&fbar[1]), 1);
         *sAbort = 0;
     }
     if (warp == 0) tmem_alloc(smem_u32(tmem_slot), kRtTmemCols);
@@ -328,10 +390,12 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
     z2 cur_a[kAPer], nxt_a[kAPer], cur_x, nxt_x;
     auto fetch = [&](int64_t jj, int c0, int q, z2 (&va)[kAPer], z2 &vx) {
         const int b = q >> 2, s0 = (q & 3) * 16;
+        if constexpr (!kImg) {
 #pragma unroll
-        for (int u = 0; u < kAPer; ++u) {
-            const int e = tid + u * kRtThreads;
-            va[u] = coupling(a, jj, b, a_row(e), s0 + a_col(e));
+            for (int u = 0; u < kAPer; ++u) {
+                const int e = tid + u * kRtThreads;
+                va[u] = coupling(a, jj, b, a_row(e), s0 + a_col(e));
+            }
         }
         const int s = s0 + x_row(tid), col = c0 + x_col(tid);
         const int64_t jb = jj - 1 + b;
@@ -373,28 +437,24 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
                 ok = false;
                 break;
             }
+            unsigned char *As = base + buf * kRtStage, *Bs = As + kRtAStage;
+            if constexpr (kImg) {
+                // the chunk's matrix slices, copied in while the x slices are cut
+                if (tid == 0) {
+                    mbar_expect_tx(smem_u32(&fbar[buf]), (uint32_t)kRtAStage);
+                    bulk_g2s(smem_u32(As), a.img + (j * 12 + q) * (int64_t)kRtAStage, (uint32_t)kRtAStage,
+                             smem_u32(&fbar[buf]));
+                }
+            }
             if (q + 1 < 12) fetch(j, col0, q + 1, nxt_a, nxt_x);
             else if (jn < a.N) fetch(jn, pn * kRtNC, 0, nxt_a, nxt_x);
-            unsigned char *As = base + buf * kRtStage, *Bs = As + kRtAStage;
             // matrix slices: 64 rows x 16 complex columns (see a_row / a_col
             // for the bank-conflict-free map)
+            if constexpr (!kImg) {
 #pragma unroll
-            for (int u = 0; u < kAPer; ++u) {
-                const int e = tid + u * kRtThreads, i = a_row(e), sl = a_col(e);
-                const z2 v = cur_a[u];
-                const int E = sEr[i];
-                const unsigned long long qr = fixq<60>(v.x, E), qi = fixq<60>(v.y, E);
-                const uint32_t sgr = v.x < 0.0 ? 0x8000u : 0u, sgi = v.y < 0.0 ? 0x8000u : 0u;
-                const int o_re = kmaj16(i, 2 * sl), o_im = kmaj16(i + 64, 2 * sl);
-#pragma unroll
-                for (int n = 0; n < kRtNSA; ++n) {
-                    const int sh = 54 - 6 * n;
-                    const uint32_t mr = (uint32_t)(qr >> sh) & 63u, mi = (uint32_t)(qi >> sh) & 63u;
-                    const uint32_t br = bf16_int(mr, sgr), bi = bf16_int(mi, sgi), bni = bi ^ 0x8000u;
-                    unsigned char *An = As + n * kRtASlice;
-                    // real row i: (Re M, -Im M); imaginary row i + 64: (Im M, Re M)
-                    *reinterpret_cast<uint32_t *>(An + o_re) = br | (bni << 16);
-                    *reinterpret_cast<uint32_t *>(An + o_im) = bi | (br << 16);
+                for (int u = 0; u < kAPer; ++u) {
+                    const int e = tid + u * kRtThreads, i = a_row(e), sl = a_col(e);
+                    slice_matrix_entry(cur_a[u], sEr[i], i, sl, As);
                 }
             }
             // x slices: 16 complex rows x 32 columns
@@ -403,13 +463,15 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
                 const z2 v = cur_x;
                 const int F = sEc[c];
                 const unsigned long long qr = fixq<54>(v.x, F), qi = fixq<54>(v.y, F);
-                const uint32_t sgr = v.x < 0.0 ? 0x8000u : 0u, sgi = v.y < 0.0 ? 0x8000u : 0u;
+                const uint32_t sr = dsign(v.x), si = dsign(v.y);
+                const uint32_t baser = 0x4B000000u | sr, basei = 0x4B000000u | si;
+                const float offr = __uint_as_float(0xCB000000u ^ sr), offi = __uint_as_float(0xCB000000u ^ si);
 #pragma unroll
                 for (int n = 0; n < kRtNSX; ++n) {
                     const int sh = 48 - 6 * n;
                     const uint32_t mr = (uint32_t)(qr >> sh) & 63u, mi = (uint32_t)(qi >> sh) & 63u;
                     *reinterpret_cast<uint32_t *>(Bs + kmaj16(n * kRtNC + c, 2 * sl)) =
-                        bf16_int(mr, sgr) | (bf16_int(mi, sgi) << 16);
+                        bf16_pair(f32_int(mr, baser, offr), f32_int(mi, basei, offi));
                 }
             }
 #pragma unroll
@@ -420,6 +482,9 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
             __syncthreads();
             tc_fence_after();
             if (tid == 0) {
+                if constexpr (kImg) {
+                    if (!mbar_wait(smem_u32(&fbar[buf]), ub & 1u, kRtWaitPolls)) *sAbort = 1;
+                }
                 const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
                 for (int t = 0; t < kRtKC / 16; ++t) {
                     // the first products of a pass start the accumulators
@@ -472,11 +537,10 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
                 const int c = cb + cc, col = col0 + c;
                 if (i >= m || col >= k) continue;
                 const int F = sEc[c];
-                long long p0 = 0, p1 = 0;
+                // T = sum_d acc_d 2^(6 (11 - d)), exact (|T| < 2^91)
+                __int128 T = 0;
 #pragma unroll
-                for (int d = 0; d < 5; ++d) p0 = p0 * 64 + (long long)__float2int_rn(__uint_as_float(acc[d][cc]));
-#pragma unroll
-                for (int d = 5; d < kRtND; ++d) p1 = p1 * 64 + (long long)__float2int_rn(__uint_as_float(acc[d][cc]));
+                for (int d = 0; d < kRtND; ++d) T = T * 64 + (__int128)__float2int_rn(__uint_as_float(acc[d][cc]));
                 const int64_t ro = (j * m + i) * (int64_t)k + col;
                 if (!rin(a, kDbgResid, ro)) continue;
                 double *dst = &a.r[ro].x + part;
@@ -486,9 +550,8 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
                     rv = __longlong_as_double(0x7FF8000000000000ll);
                 } else if (Er == kExpZero || F == kExpZero) {
                     rv = yv;
-                } else if (!resid_exact(yv, p0, p1, Er + F - 64, rv)) {
-                    const double val = fma((double)p0, 1073741824.0, (double)p1);
-                    rv = fma(-val, pow2(Er + F - 64), yv);
+                } else if (!resid_exact(yv, T, Er + F - 76, rv)) {
+                    rv = fma(-(double)T, pow2(Er + F - 76), yv);
                 }
                 *dst = rv;
             }
@@ -504,6 +567,11 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
         // let every committed MMA finish before tensor memory is released
         if (uses0 > 0) mbar_wait(smem_u32(&mbar[0]), (uses0 - 1) & 1u, kRtWaitPolls);
         if (uses1 > 0) mbar_wait(smem_u32(&mbar[1]), (uses1 - 1) & 1u, kRtWaitPolls);
+        if (kImg) {
+            // and every image copy (each use of a buffer was one copy)
+            if (uses0 > 0) mbar_wait(smem_u32(&fbar[0]), (uses0 - 1) & 1u, kRtWaitPolls);
+            if (uses1 > 0) mbar_wait(smem_u32(&fbar[1]), (uses1 - 1) & 1u, kRtWaitPolls);
+        }
     }
     tc_fence_before();
     __syncthreads();
@@ -514,6 +582,15 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
 }  // namespace
 
 size_t residual_tc_smem_bytes() { return 2 * (size_t)kRtStage + 1024 + 1024; }
+
+size_t residual_image_bytes(int64_t N) { return (size_t)N * 12 * (size_t)kRtAStage; }
+
+cudaError_t launch_matrix_image(const ResidTcArgs &a, unsigned char *img, int nsm, cudaStream_t s) {
+    int64_t g = a.N * 12;
+    if (g > (int64_t)nsm * 8) g = (int64_t)nsm * 8;
+    k_matrix_image<<<(unsigned)g, kRtThreads, 0, s>>>(a, img);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_row_exponents(const ResidTcArgs &a, int nsm, cudaStream_t s) {
     const int64_t n = a.N * a.m;
@@ -531,10 +608,16 @@ cudaError_t launch_residual_tc(const ResidTcArgs &a, int nsm, cudaStream_t s) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const size_t smem = residual_tc_smem_bytes();
-    e = cudaFuncSetAttribute(k_residual_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     const int64_t grid = a.N < nsm ? a.N : nsm;
-    k_residual_tc<<<(unsigned)grid, kRtThreads, smem, s>>>(a);
+    if (a.img) {
+        e = cudaFuncSetAttribute(k_residual_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_residual_tc<true><<<(unsigned)grid, kRtThreads, smem, s>>>(a);
+    } else {
+        e = cudaFuncSetAttribute(k_residual_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        k_residual_tc<false><<<(unsigned)grid, kRtThreads, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -544,9 +627,10 @@ cudaError_t launch_residual_tc(const ResidTcArgs &a, int nsm, cudaStream_t s) {
 
 namespace {
 
-size_t split_ws_bytes(int64_t N, int m, int k) {
+size_t split_ws_bytes(int64_t N, int m, int k, bool image) {
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
-    return up(256) + up((size_t)N * m * sizeof(int)) + up((size_t)N * k * sizeof(int));
+    return up(256) + up((size_t)N * m * sizeof(int)) + up((size_t)N * k * sizeof(int)) +
+           (image ? up(crs::residual_image_bytes(N)) : 0);
 }
 
 }  // namespace
@@ -558,8 +642,8 @@ extern "C" int crsolve_residual_workspace_bytes(int64_t N, int32_t m, int32_t k,
         *bytes = 0;
         return CRSOLVE_OK;
     }
-    if (method != CRSOLVE_RESIDUAL_SPLIT) return CRSOLVE_EUNSUPPORTED;
-    *bytes = split_ws_bytes(N, m, k);
+    if (method != CRSOLVE_RESIDUAL_SPLIT && method != CRSOLVE_RESIDUAL_SPLIT_IMAGE) return CRSOLVE_EUNSUPPORTED;
+    *bytes = split_ws_bytes(N, m, k, method == CRSOLVE_RESIDUAL_SPLIT_IMAGE);
     return CRSOLVE_OK;
 }
 
@@ -583,8 +667,9 @@ extern "C" int crsolve_residual(int64_t N, int32_t m, int32_t k, const crsolve_z
                                     reinterpret_cast<z2 *>(r), nsm, s) == cudaSuccess
                    ? CRSOLVE_OK
                    : CRSOLVE_ECUDA;
-    if (method != CRSOLVE_RESIDUAL_SPLIT) return CRSOLVE_EUNSUPPORTED;
-    if (!workspace || workspace_bytes < split_ws_bytes(N, m, k) || ((uintptr_t)workspace & 255u))
+    if (method != CRSOLVE_RESIDUAL_SPLIT && method != CRSOLVE_RESIDUAL_SPLIT_IMAGE) return CRSOLVE_EUNSUPPORTED;
+    const bool image = method == CRSOLVE_RESIDUAL_SPLIT_IMAGE;
+    if (!workspace || workspace_bytes < split_ws_bytes(N, m, k, image) || ((uintptr_t)workspace & 255u))
         return CRSOLVE_EINVAL;
     char *ws = static_cast<char *>(workspace);
     auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
@@ -600,6 +685,12 @@ extern "C" int crsolve_residual(int64_t N, int32_t m, int32_t k, const crsolve_z
     a.ecol = reinterpret_cast<int *>(ws + up(256) + up((size_t)N * m * sizeof(int)));
     if (cudaMemsetAsync(a.err, 0, sizeof(int), s) != cudaSuccess) return CRSOLVE_ECUDA;
     if (crs::launch_row_exponents(a, nsm, s) != cudaSuccess) return CRSOLVE_ECUDA;
+    if (image) {
+        unsigned char *img = reinterpret_cast<unsigned char *>(
+            ws + up(256) + up((size_t)N * m * sizeof(int)) + up((size_t)N * k * sizeof(int)));
+        if (crs::launch_matrix_image(a, img, nsm, s) != cudaSuccess) return CRSOLVE_ECUDA;
+        a.img = img;
+    }
     if (crs::launch_residual_tc(a, nsm, s) != cudaSuccess) return CRSOLVE_ECUDA;
     int err = 0;
     if (cudaMemcpyAsync(&err, a.err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||

@@ -75,6 +75,7 @@ struct crsolve_plan_s {
     size_t offWbd32 = 0, offCbd32 = 0, offA32 = 0, offB32 = 0, offY32 = 0, offX32 = 0, offR64 = 0, offNorms = 0,
            offErr = 0;
     size_t offP64 = 0, offW64 = 0, offDot = 0, offScal = 0, offErow = 0, offEcol = 0;   // conjugate gradients
+    size_t offAimg = 0;                                                                   // residual's matrix slices
     const crsolve_z *A64 = nullptr, *B64 = nullptr;  // the caller's FP64 system, read by the residual
     bool fallback = false;                       // FP32 factor broke down: everything in FP64
     int last_iters = 0;
@@ -679,6 +680,11 @@ int mixed_factor(crsolve_plan_s *p, const z2 *A, const z2 *B, cudaStream_t s) {
         ra.dbg = reinterpret_cast<unsigned long long *>(ws + p->offDbg);
         if ((rc = launch(p, CRSOLVE_K_RESIDUAL, 0, p->N, s, [&] { return crs::launch_row_exponents(ra, p->nsm, s); })))
             return rc;
+        // the matrix slices of every residual of the refinement, once
+        if ((rc = launch(p, CRSOLVE_K_RESIDUAL, 0, p->N, s, [&] {
+                 return crs::launch_matrix_image(ra, reinterpret_cast<unsigned char *>(ws + p->offAimg), p->nsm, s);
+             })))
+            return rc;
     }
     unsigned long long st = 0;
     int err = 0;
@@ -839,6 +845,7 @@ int mixed_residual(crsolve_plan_s *p, int k, const z2 *x, const z2 *y, z2 *r, cu
     a.ecol = reinterpret_cast<int *>(ws + p->offEcol);
     a.err = reinterpret_cast<int *>(ws + p->offErr);
     a.dbg = reinterpret_cast<unsigned long long *>(ws + p->offDbg);
+    a.img = reinterpret_cast<const unsigned char *>(ws + p->offAimg);
     return launch(p, CRSOLVE_K_RESIDUAL, 0, p->N, s, [&] { return crs::launch_residual_tc(a, p->nsm, s); });
 }
 
@@ -1082,6 +1089,7 @@ void layout(crsolve_plan_s *p) {
         p->offScal = take(cur, 5 * (size_t)p->kmax * sizeof(double));
         p->offErow = take(cur, (size_t)N * m * sizeof(int));
         p->offEcol = take(cur, (size_t)N * p->kmax * sizeof(int));
+        if (mixed_uses_split(p)) p->offAimg = take(cur, crs::residual_image_bytes(N));
     }
     p->total = cur;
     p->scr_total = scur;

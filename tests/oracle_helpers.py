@@ -156,27 +156,32 @@ def residual_dd(A, B, x, y, rows=None):
     Rump and Oishi): the result is the exact residual rounded, up to a
     relative 2^-104-level error in the sums.  Returns [len(rows)][m][k]."""
     N, m, k = y.shape
-    rows = list(range(N)) if rows is None else list(rows)
-    out = np.empty((len(rows), m, k), np.complex128)
-    for n, j in enumerate(rows):
-        sr, er = y[j].real.copy(), np.zeros((m, k))
-        si, ei = y[j].imag.copy(), np.zeros((m, k))
-        for b, M in enumerate(coupling_blocks(A, B, j)):
-            jb = j - 1 + b
-            if jb < 0 or jb >= N:
-                continue
-            X = x[jb]
-            for s in range(m):
-                mr, mi = M[:, s].real[:, None], M[:, s].imag[:, None]
-                xr, xi = X[s].real[None, :], X[s].imag[None, :]
-                # re: - (mr xr - mi xi); im: - (mr xi + mi xr)
-                for (u, v, sg, tgt) in ((mr, xr, -1.0, 0), (mi, xi, 1.0, 0), (mr, xi, -1.0, 1), (mi, xr, -1.0, 1)):
-                    p, e = _two_prod(np.broadcast_to(u, (m, k)) * sg, np.broadcast_to(v, (m, k)))
-                    if tgt == 0:
-                        sr, e2 = _two_sum(sr, p)
-                        er = er + (e + e2)
-                    else:
-                        si, e2 = _two_sum(si, p)
-                        ei = ei + (e + e2)
-        out[n] = (sr + er) + 1j * (si + ei)
-    return out
+    rows = np.arange(N) if rows is None else np.asarray(list(rows))
+    R = len(rows)
+    Ms, Xs = [], []
+    for b in range(3):
+        M = np.zeros((R, m, m), np.complex128)
+        X = np.zeros((R, m, k), np.complex128)
+        for n, j in enumerate(rows):
+            M[n] = coupling_blocks(A, B, int(j))[b]
+            jb = int(j) - 1 + b
+            if 0 <= jb < N:
+                X[n] = x[jb]
+        Ms.append(M)
+        Xs.append(X)
+    sr, er = y[rows].real.copy(), np.zeros((R, m, k))
+    si, ei = y[rows].imag.copy(), np.zeros((R, m, k))
+    for M, X in zip(Ms, Xs):
+        for s in range(m):
+            mr, mi = M[:, :, s].real[:, :, None], M[:, :, s].imag[:, :, None]
+            xr, xi = X[:, s, :].real[:, None, :], X[:, s, :].imag[:, None, :]
+            # re: - (mr xr - mi xi); im: - (mr xi + mi xr)
+            for (u, v, sg, tgt) in ((mr, xr, -1.0, 0), (mi, xi, 1.0, 0), (mr, xi, -1.0, 1), (mi, xr, -1.0, 1)):
+                p, e = _two_prod(np.broadcast_to(u * sg, (R, m, k)), np.broadcast_to(v, (R, m, k)))
+                if tgt == 0:
+                    sr, e2 = _two_sum(sr, p)
+                    er = er + (e + e2)
+                else:
+                    si, e2 = _two_sum(si, p)
+                    ei = ei + (e + e2)
+    return (sr + er) + 1j * (si + ei)

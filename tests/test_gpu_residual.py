@@ -4,11 +4,12 @@ residual of the mixed-precision form's iterative refinement.
 Reference: the compensated residual of tests/oracle_helpers (pinned on the
 CPU against rational arithmetic), i.e. the exact residual rounded.
 
-Bound: the tensor-core method ("split": exact slice products, nine 6-bit
-slices per entry on a per-row / per-column binary grid) drops slice products
-and truncates below 2^-53 of each row's and column's largest entry; its
-stated error bound per entry is 2^-50 * K * max|row| * max|column| with
-K = 6m real terms, the size of an FP64 dot product's rounding error bound.
+Bound: the tensor-core method ("split": exact slice products; matrix entries
+on a 60-bit per-row grid, x on a 54-bit per-column grid, pairs of slices
+with i + j <= 11 kept, y - A x formed exactly and rounded once) has the
+stated error bound per entry 2^-50 * K * max|row| * max|column| (K = 6m
+real terms) plus the final rounding, the size of an FP64 dot product's
+rounding error bound.
 The FP64 method is held to the classical bound gamma_K * sum |a| |x|.
 On integer data both must be exact.
 """
@@ -125,3 +126,12 @@ def test_zero_and_non_finite_inputs(cuda_ok):
     assert bad[2:5, :, 2].all()
     bad[2:5, :, 2] = False
     assert not bad.any()
+
+
+@pytest.mark.parametrize("N,m,k", [(5, 64, 32), (160, 64, 33), (7, 40, 5)])
+def test_precomputed_matrix_slices_give_the_same_bits(cuda_ok, N, m, k):
+    """"split_image" (matrix slices written once to the workspace and copied
+    in by bulk copies, as the mixed form does) equals "split" bit for bit."""
+    A, B, y = synthetic.gen_system(N, m, k, seed=N * k)
+    x = synthetic.gen_system(N, m, k, seed=N * k + 1)[2]
+    assert np.array_equal(_gpu(A, B, x, y, "split_image"), _gpu(A, B, x, y, "split"))
