@@ -57,12 +57,12 @@ FP64_FMA_PER_CLK_SM, N_SM, SM_MAX_MHZ = 2, 152, 2070.0
 FP64_PEAK_GFLOPS = FP64_FMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ / 1e3
 # DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum
 # + dram__bytes_write.sum of k_factor_odd<8, double>, level 0 of N = 2^18, 2^17
-# odd blocks), valid only while the kernel sources are the ones captured: the
-# SHA-256 of the files below at capture time.  Otherwise the line reports null.
-TRAFFIC_CAPTURE = {"bytes_per_odd_block": (537.9e6 + 624.6e6) / (1 << 17),
-                   "sources": ("paper_1807_00370_gb300/csrc/cr_core.cuh", "paper_1807_00370_gb300/csrc/cr_device.cuh",
-                               "paper_1807_00370_gb300/csrc/cr_levels.cu"),
-                   "sha256": None}
+# odd blocks: 538,057,472 + 624,746,752 bytes), valid only while the sources
+# of the kernel's device code are the ones captured (their SHA-256 below).
+# Otherwise the line reports null.
+TRAFFIC_CAPTURE = {"bytes_per_odd_block": (538057472 + 624746752) / (1 << 17),
+                   "sources": ("paper_1807_00370_gb300/csrc/cr_core.cuh", "paper_1807_00370_gb300/csrc/cr_device.cuh"),
+                   "sha256": "d42dc7e57ed026148ada2a9c505885863e6d772af98f7ced9a7d726ed499baf5"}
 
 
 def captured_traffic_per_odd_block():
@@ -76,6 +76,32 @@ def captured_traffic_per_odd_block():
         with open(os.path.join(ROOT, rel), "rb") as f:
             h.update(f.read())
     return TRAFFIC_CAPTURE["bytes_per_odd_block"] if h.hexdigest() == TRAFFIC_CAPTURE["sha256"] else None
+
+
+def host_link(dev, pinned):
+    """Bandwidth of the host link for the e2e number: a pinned host tensor
+    copied to the device and back (CUDA events), and the CPUs the process
+    may run on against the GPU's local CPUs (a far NUMA node slows pinned
+    copies)."""
+    import torch
+    out = {}
+    d = torch.empty(pinned.shape, dtype=pinned.dtype, device=dev)
+    for name, src, dst in (("h2d_gbs", pinned, d), ("d2h_gbs", d, pinned)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = 3 * pinned.numel() * pinned.element_size() / (e0.elapsed_time(e1) * 1e-3) / 1e9
+    del d
+    try:
+        out["process_cpus"] = len(os.sched_getaffinity(0))
+    except Exception:  # noqa: BLE001
+        pass
+    return out
 
 
 def fp64_probe():
@@ -1015,7 +1041,8 @@ def main():
         el = time.perf_counter() - t0
         e2e = {"value": N_BLOCKS * args.e2e_steps / el * ws, "unit": "block-rows/s",
                "h2d_bytes_per_step": int(tA.numel() + tB.numel() + ty.numel()) * 16,
-               "d2h_bytes_per_step": int(tx.numel()) * 16 + 8, "steps": args.e2e_steps}
+               "d2h_bytes_per_step": int(tx.numel()) * 16 + 8, "steps": args.e2e_steps,
+               "host_link": host_link(dev, tA)}
 
     cpu = None
     sample_err = None

@@ -446,6 +446,12 @@ int crsolve_tile_set(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc
                      int32_t threads_solve);
 int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads,
                      int32_t *threads_solve);
+/* The same for the FP32 levels of the mixed-precision form (their own table;
+ * for mt = 64 the factor needs at least 128 threads). */
+int crsolve_tile_set_mixed(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc, int32_t threads,
+                           int32_t threads_solve);
+int crsolve_tile_get_mixed(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads,
+                           int32_t *threads_solve);
 
 /* Number of levels of the plan (floor(log2 N) + 1) and the level sizes; with
  * CRSOLVE_PLAN_ALG1, log2 N + 1 levels of N blocks each (2^l systems of N/2^l). */

@@ -88,6 +88,8 @@ SIGNATURES = {
     "crsolve_batch_destroy": (ctypes.c_int, [_P]),
     "crsolve_solve_noalloc": (ctypes.c_int, [_I64, _I32, _I32, _P, _P, _P, _P, ctypes.POINTER(CrsolveInfo), _P]),
     "crsolve_tile_get": (ctypes.c_int, [_I32] + [ctypes.POINTER(_I32)] * 5),
+    "crsolve_tile_set_mixed": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _I32]),
+    "crsolve_tile_get_mixed": (ctypes.c_int, [_I32] + [ctypes.POINTER(_I32)] * 5),
     "crsolve_peak_probe": (ctypes.c_int, [_I32] + [ctypes.POINTER(ctypes.c_double)] * 3 + [_P]),
     "crsolve_check_bounded_wait": (ctypes.c_int, [_I32, _P, _P]),
     "crsolve_debug_bounds": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64), _P]),

@@ -16,7 +16,8 @@ from . import _native as nat
 __all__ = ["Plan", "crsolve_plan_create", "crsolve_factor", "crsolve_solve", "crsolve_backward",
            "crsolve_info_get", "crsolve_solve_host", "crsolve_plan_levels",
            "crsolve_debug_level_system", "crsolve_timing_enable", "crsolve_timing_read",
-           "crsolve_launch_count", "crsolve_mixed_stats", "crsolve_tile_set", "crsolve_tile_get", "crsolve_solve_noalloc", "crsolve_peak_probe", "crsolve_residual", "solve", "CRSolveFn",
+           "crsolve_launch_count", "crsolve_mixed_stats", "crsolve_tile_set", "crsolve_tile_get", "crsolve_tile_set_mixed", "crsolve_tile_get_mixed",
+           "crsolve_solve_noalloc", "crsolve_peak_probe", "crsolve_residual", "solve", "CRSolveFn",
            "NotPositiveDefinite"]
 
 
@@ -289,6 +290,19 @@ def crsolve_tile_set(mt: int, nb_factor: int, nb_solve: int, kc: int, threads: i
                      threads_solve: int | None = None) -> None:
     nat.check(nat.load().crsolve_tile_set(mt, nb_factor, nb_solve, kc, threads,
                                           threads if threads_solve is None else threads_solve), "crsolve_tile_set")
+
+
+def crsolve_tile_set_mixed(mt: int, nb_factor: int, nb_solve: int, kc: int, threads: int,
+                           threads_solve: int | None = None) -> None:
+    nat.check(nat.load().crsolve_tile_set_mixed(mt, nb_factor, nb_solve, kc, threads,
+                                                threads if threads_solve is None else threads_solve),
+              "crsolve_tile_set_mixed")
+
+
+def crsolve_tile_get_mixed(mt: int):
+    v = [ctypes.c_int32() for _ in range(5)]
+    nat.check(nat.load().crsolve_tile_get_mixed(mt, *[ctypes.byref(x) for x in v]), "crsolve_tile_get_mixed")
+    return tuple(int(x.value) for x in v)
 
 
 def crsolve_tile_get(mt: int):

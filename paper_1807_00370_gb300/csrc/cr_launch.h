@@ -17,6 +17,7 @@ struct TileShape {
 
 TileShape tile_shape(int mt);
 bool set_tile_shape(int mt, const TileShape &ts, size_t smem_limit);
+bool set_tile_shape32(int mt, const TileShape &ts, size_t smem_limit);
 int pick_mt(int m);                                  // 4, 8, 16, 32, 64 or 0
 size_t factor_smem_bytes(int mt, int nb, int rsize = 8);           // rsize: 8 FP64, 4 FP32
 size_t solve_smem_bytes(int mt, int nb, int kc, int panels, int rsize = 8);

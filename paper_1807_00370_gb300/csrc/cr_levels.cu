@@ -111,7 +111,7 @@ TileShape tile_shape(int mt) {
 
 // FP32 levels of the mixed-precision form: narrower right-hand-side chunks at
 // MT >= 32 so that the staged Z still leaves room for two CTAs per SM.
-static const TileShape g_tiles32[5] = {
+static TileShape g_tiles32[5] = {
     {32, 32, 32, 256, 256}, {16, 16, 16, 256, 256}, {4, 8, 16, 256, 256}, {2, 2, 16, 256, 256},
     {1, 1, 16, 256, 256},
 };
@@ -119,6 +119,21 @@ static const TileShape g_tiles32[5] = {
 TileShape tile_shape32(int mt) {
     const int i = mt_slot(mt);
     return i < 0 ? TileShape{0, 0, 0, 0, 0} : g_tiles32[i];
+}
+
+bool set_tile_shape32(int mt, const TileShape &ts, size_t smem_limit) {
+    const int i = mt_slot(mt);
+    if (i < 0 || ts.nb_factor < 1 || ts.nb_solve < 1 || ts.kc_max < 1 || ts.threads < 32 ||
+        ts.threads > 256 || ts.threads % 32 || ts.threads_solve < 32 || ts.threads_solve > 256 ||
+        ts.threads_solve % 32)
+        return false;
+    // the tensor-core Schur product of MT = 64 reads TMEM with four warps
+    if (mt == 64 && ts.threads < 128) return false;
+    if (factor_smem_bytes(mt, ts.nb_factor, 4) > smem_limit ||
+        solve_smem_bytes(mt, ts.nb_solve, ts.kc_max, 3, 4) > smem_limit)
+        return false;
+    g_tiles32[i] = ts;
+    return true;
 }
 
 bool set_tile_shape(int mt, const TileShape &ts, size_t smem_limit) {

@@ -376,7 +376,8 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    uint32_t uses0 = 0, uses1 = 0;  // commits issued per buffer
+    uint32_t uses0 = 0, uses1 = 0;      // commits issued per buffer
+    uint32_t copies0 = 0, copies1 = 0;  // image copies issued per buffer (thread 0)
     bool ok = true;
     const int npass = (k + kRtNC - 1) / kRtNC;
 
@@ -406,6 +407,14 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
     int64_t j = blockIdx.x;
     int pass = 0;
     if (j < a.N) fetch(j, 0, 0, cur_a, cur_x);
+    if constexpr (kImg) {
+        // the first chunk's matrix slices (chunk g's copy goes to buffer g & 1)
+        if (tid == 0 && j < a.N) {
+            mbar_expect_tx(smem_u32(&fbar[0]), (uint32_t)kRtAStage);
+            bulk_g2s(smem_u32(base), a.img + j * 12 * (int64_t)kRtAStage, (uint32_t)kRtAStage, smem_u32(&fbar[0]));
+            copies0 = 1;
+        }
+    }
     while (j < a.N && ok) {
         const int col0 = pass * kRtNC;
         // the (row, pass) after this one: its first chunk is fetched during the last chunk
@@ -438,14 +447,6 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
                 break;
             }
             unsigned char *As = base + buf * kRtStage, *Bs = As + kRtAStage;
-            if constexpr (kImg) {
-                // the chunk's matrix slices, copied in while the x slices are cut
-                if (tid == 0) {
-                    mbar_expect_tx(smem_u32(&fbar[buf]), (uint32_t)kRtAStage);
-                    bulk_g2s(smem_u32(As), a.img + (j * 12 + q) * (int64_t)kRtAStage, (uint32_t)kRtAStage,
-                             smem_u32(&fbar[buf]));
-                }
-            }
             if (q + 1 < 12) fetch(j, col0, q + 1, nxt_a, nxt_x);
             else if (jn < a.N) fetch(jn, pn * kRtNC, 0, nxt_a, nxt_x);
             // matrix slices: 64 rows x 16 complex columns (see a_row / a_col
@@ -505,6 +506,23 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
                     }
                 }
                 tc_commit(smem_u32(&mbar[buf]));
+                if constexpr (kImg) {
+                    // the next chunk's matrix slices go into the other buffer as
+                    // soon as its previous MMAs (chunk g-1) are done, so the copy
+                    // has this chunk's MMAs and the next x slicing to land
+                    const int64_t jc = q + 1 < 12 ? j : jn;
+                    const int qc = q + 1 < 12 ? q + 1 : 0;
+                    if (jc < a.N) {
+                        const int ob = buf ^ 1;
+                        const uint32_t uo = ob ? uses1 : uses0;     // commits of the other buffer so far
+                        if (uo > 0 && !mbar_wait(smem_u32(&mbar[ob]), (uo - 1) & 1u, kRtWaitPolls)) *sAbort = 1;
+                        mbar_expect_tx(smem_u32(&fbar[ob]), (uint32_t)kRtAStage);
+                        bulk_g2s(smem_u32(base + ob * kRtStage), a.img + (jc * 12 + qc) * (int64_t)kRtAStage,
+                                 (uint32_t)kRtAStage, smem_u32(&fbar[ob]));
+                        if (ob) ++copies1;
+                        else ++copies0;
+                    }
+                }
             }
             if (buf) ++uses1;
             else ++uses0;
@@ -567,10 +585,10 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
         // let every committed MMA finish before tensor memory is released
         if (uses0 > 0) mbar_wait(smem_u32(&mbar[0]), (uses0 - 1) & 1u, kRtWaitPolls);
         if (uses1 > 0) mbar_wait(smem_u32(&mbar[1]), (uses1 - 1) & 1u, kRtWaitPolls);
-        if (kImg) {
-            // and every image copy (each use of a buffer was one copy)
-            if (uses0 > 0) mbar_wait(smem_u32(&fbar[0]), (uses0 - 1) & 1u, kRtWaitPolls);
-            if (uses1 > 0) mbar_wait(smem_u32(&fbar[1]), (uses1 - 1) & 1u, kRtWaitPolls);
+        if (kImg && tid == 0) {
+            // and every image copy thread 0 issued, consumed or not
+            if (copies0 > 0) mbar_wait(smem_u32(&fbar[0]), (copies0 - 1) & 1u, kRtWaitPolls);
+            if (copies1 > 0) mbar_wait(smem_u32(&fbar[1]), (copies1 - 1) & 1u, kRtWaitPolls);
         }
     }
     tc_fence_before();

@@ -1388,6 +1388,27 @@ int crsolve_tile_set(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc
                : CRSOLVE_EINVAL;
 }
 
+int crsolve_tile_set_mixed(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc, int32_t threads,
+                           int32_t threads_solve) {
+    int dev = 0, optin = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+        return CRSOLVE_ECUDA;
+    return crs::set_tile_shape32(mt, crs::TileShape{nb_factor, nb_solve, kc, threads, threads_solve}, (size_t)optin)
+               ? CRSOLVE_OK
+               : CRSOLVE_EINVAL;
+}
+
+int crsolve_tile_get_mixed(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads,
+                           int32_t *threads_solve) {
+    if (!nb_factor || !nb_solve || !kc || !threads || !threads_solve) return CRSOLVE_EINVAL;
+    const crs::TileShape ts = crs::tile_shape32(mt);
+    if (ts.threads == 0) return CRSOLVE_EINVAL;
+    *nb_factor = ts.nb_factor; *nb_solve = ts.nb_solve; *kc = ts.kc_max; *threads = ts.threads;
+    *threads_solve = ts.threads_solve;
+    return CRSOLVE_OK;
+}
+
 int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads,
                      int32_t *threads_solve) {
     if (!nb_factor || !nb_solve || !kc || !threads || !threads_solve) return CRSOLVE_EINVAL;
