@@ -1,12 +1,14 @@
-"""Tile autotuner of the batched form.
+"""Tile autotuner of the batched form and of the single-system plans.
 
-For every block-size class MT (4, 8, 16, 32, 64) present in a batch, it
-times the persistent batched kernel on a sample batch of that class and
-keeps the fastest (odd blocks per chunk in the factor step, odd blocks per
-chunk in the solve steps, right-hand-side columns per chunk).  Results are
-cached per GPU name and class in _build/tiles.json next to the library.
-The sample inputs come from torch's generator (their values do not matter
-for timing, only their shapes).
+Batched form: for every block-size class MT (4, 8, 16, 32, 64) present in a
+batch, it times the persistent batched kernel on a sample batch of that class
+and keeps the fastest (odd blocks per chunk in the factor step, odd blocks
+per chunk in the solve steps, right-hand-side columns per chunk).  Plans
+(plan_tiles): per class, width k and precision, a coordinate search over the
+five parameters of the plan kernels' tile table.  Results are cached per GPU
+name in _build/tiles.json next to the library.  The sample inputs come from
+torch's generator (their values do not matter for timing, only their shapes;
+they are diagonally dominant, so every sample factorises).
 """
 from __future__ import annotations
 
@@ -137,3 +139,107 @@ def tiles_for(ms, ks, device=None, use_cache: bool = True, verbose: bool = False
         with open(CACHE, "w") as f:
             json.dump(cache, f, indent=1)
     return out
+
+
+# ------------------------------------------------- single-system (plan) paths
+#
+# The plan kernels read a process-wide tile table per block-size class and
+# precision (crsolve_tile_set / crsolve_tile_set_mixed).  plan_tiles() picks a
+# shape for (class, k, precision) by timing factor + solve of a sample system
+# over the candidates (each parameter around the current shape, a coordinate
+# search), caches it per GPU name under that key, and with apply=True writes
+# it into the table for later launches of every plan of that class.
+
+PLAN_NB = (1, 2, 4, 8, 16, 32)
+PLAN_KC = (8, 16, 32)
+PLAN_THREADS = (128, 256)
+
+
+def _time_plan(N, m, k, precision, A, B, y, reps=3) -> float:
+    from .api import Plan, crsolve_factor, crsolve_solve
+    plan = Plan(N, m, k, precision=precision)
+    x = torch.empty_like(y)
+    crsolve_factor(plan, A, B)
+    crsolve_solve(plan, y, x)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        crsolve_factor(plan, A, B)
+        crsolve_solve(plan, y, x)
+    e1.record()
+    torch.cuda.synchronize()
+    plan.close()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_plan_class(m: int, k: int, precision: int = 0, n_blocks: int = 0, device=None, verbose: bool = False):
+    """Best (nb_factor, nb_solve, kc, threads, threads_solve) of class mt(m)
+    for width k and precision (0 FP64, 1 mixed: its FP32 levels' table) on a
+    sample system of n_blocks blocks (default: 2^20 / m^2, at least 2^12).
+    Restores the table it started from; returns (shape, timings)."""
+    from . import api
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    mt = _mt(m)
+    getter = api.crsolve_tile_get_mixed if precision else api.crsolve_tile_get
+    setter = api.crsolve_tile_set_mixed if precision else api.crsolve_tile_set
+    if n_blocks <= 0:
+        n_blocks = max(1 << 12, (1 << 20) // (m * m))
+    A, B, y = _sample_inputs(np.array([n_blocks]), np.array([m]), np.array([k]), device)
+    A = A.view(n_blocks, m, m)
+    B = B[:(n_blocks - 1) * m * m].view(n_blocks - 1, m, m)
+    y = y.view(n_blocks, m, k)
+    start = list(getter(mt))
+    best, timings = list(start), {}
+
+    def trial(shape):
+        key = ",".join(map(str, shape))
+        if key in timings:
+            return timings[key]
+        try:
+            setter(mt, *shape)
+        except Exception:  # noqa: BLE001 - out of range or too large for shared memory
+            timings[key] = None
+            return None
+        t = _time_plan(n_blocks, m, k, precision, A, B, y)
+        timings[key] = t
+        if verbose:
+            print(f"  mt={mt} k={k} prec={precision} {shape}: {t:.3f} ms")
+        return t
+
+    try:
+        t_best = trial(best)
+        for i, cands in enumerate((PLAN_NB, PLAN_NB, PLAN_KC, PLAN_THREADS, PLAN_THREADS)):
+            for v in cands:
+                shape = list(best)
+                shape[i] = v
+                t = trial(shape)
+                if t is not None and t < t_best:
+                    best, t_best = shape, t
+    finally:
+        setter(mt, *start)
+    return tuple(int(v) for v in best), {k_: v for k_, v in timings.items() if v is not None}
+
+
+def plan_tiles(m: int, k: int, precision: int = 0, device=None, use_cache: bool = True, apply: bool = True,
+               verbose: bool = False):
+    """The tuned tile shape of class mt(m) for width k and precision, from the
+    cache (key: GPU name, class, k rounded up to a power of two, precision)
+    or tuned now; with apply=True it is written into the process-wide table."""
+    from . import api
+    device = device or torch.device("cuda", torch.cuda.current_device())
+    name = torch.cuda.get_device_name(device)
+    kb = 1 << max(0, (int(k) - 1).bit_length())
+    key = f"{name}|plan|mt={_mt(m)}|k={kb}|prec={'mixed' if precision else 'fp64'}"
+    cache = load_cache() if use_cache else {}
+    if key not in cache:
+        best, table = tune_plan_class(m, kb, precision, device=device, verbose=verbose)
+        cache = load_cache()
+        cache[key] = {"tile": list(best), "m": int(m), "k": kb, "timings_ms": table}
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        with open(CACHE, "w") as f:
+            json.dump(cache, f, indent=1)
+    shape = tuple(cache[key]["tile"])
+    if apply:
+        (api.crsolve_tile_set_mixed if precision else api.crsolve_tile_set)(_mt(m), *shape)
+    return shape

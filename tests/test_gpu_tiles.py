@@ -145,3 +145,29 @@ def test_full_batch_with_autotuned_tiles_as_benchmarked(cuda_ok):
         nA = (Ah.abs().sum(2).max() + 2 * (bb.abs().sum(2).max() if len(bb) else 0)).item()
         worst = max(worst, (r.abs().amax() / (nA * xi.abs().amax())).item())
     assert worst <= 1e-14, (worst, b.tiles)
+
+
+@pytest.mark.parametrize("m,k,prec", [(8, 4, 0), (16, 8, 0), (64, 32, 1)])
+def test_plan_autotuner_choice_matches_oracle(cuda_ok, m, k, prec):
+    """plan_tiles tunes the plan kernels' tile table for (class, k, precision)
+    on a sample system, writes the choice into the table, and that table
+    solves a fresh system to the oracle's answer (FP64 at 1e-12, mixed at
+    the stated 1e-10); the table is restored afterwards."""
+    get = crs.crsolve_tile_get_mixed if prec else crs.crsolve_tile_get
+    put = crs.crsolve_tile_set_mixed if prec else crs.crsolve_tile_set
+    before = get(m)
+    try:
+        shape = autotune.plan_tiles(m, k, prec, use_cache=False, apply=True)
+        assert get(m) == shape
+        N = 777 if m < 64 else 129
+        A, B, y = synthetic.gen_system(N, m, k, seed=5 * m + k)
+        dA, dB, dy = to_dev(A, B, y)
+        plan = crs.Plan(N, m, k, precision=prec)
+        crs.crsolve_factor(plan, dA, dB)
+        x = crs.crsolve_solve(plan, dy).cpu().numpy()
+        xo, io = oracle.cr_solve(A, B, y)
+        assert crs.crsolve_info_get(plan) == io
+        assert rel_err(x, xo) <= (1e-10 if prec else TOL), shape
+    finally:
+        put(m, *before)
+    assert get(m) == before
