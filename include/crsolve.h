@@ -350,12 +350,17 @@ int crsolve_timing_read(crsolve_plan p, crsolve_kernel_time *out, int32_t cap, i
  * preconditioned conjugate gradients per right-hand-side column (A is
  * Hermitian positive definite) with the FP32 solve as preconditioner, the
  * CG variant of the mixed-precision iterative refinement of Carson and Higham
- * (SIAM J. Sci. Comput. 39, 2017); it stops when the estimated error
- * (observed contraction times the last relative correction) is below 1e-11, a
- * tenth of the stated bound 1e-10.  For m > 32 the FP64-accurate residuals
- * and products come from exact splitting on the tensor cores (see
- * crsolve_residual, method CRSOLVE_RESIDUAL_SPLIT) unless the plan was
- * created with CRSOLVE_PLAN_FP64_RESIDUAL.  In this mode crsolve_factor and
+ * (SIAM J. Sci. Comput. 39, 2017); it stops when the last relative
+ * correction is below 1e-11, a tenth of the stated bound 1e-10, or, late in
+ * the run (correction <= 1e-8, contraction <= 1e-2), when the observed
+ * contraction times the last correction is below 1e-12; when the first
+ * correction shows a condition number above about 1e3, the first stop is
+ * followed by one restart from the true residual.  For m > 32 the FP64-
+ * accurate residuals and products come from exact splitting on the tensor
+ * cores (see crsolve_residual, method CRSOLVE_RESIDUAL_SPLIT) unless the plan
+ * was created with CRSOLVE_PLAN_FP64_RESIDUAL, and the FP32 factorisation
+ * keeps L^{-1} in place of L, so that the FP32 sweeps are complex matrix
+ * products instead of triangular substitutions.  In this mode crsolve_factor and
  * crsolve_solve synchronise the stream, and A and B must stay valid and
  * unchanged until the plan is re-factored or destroyed (the residual reads
  * them).  A breakdown in the FP32 levels is re-decided by an FP64
@@ -369,6 +374,21 @@ int crsolve_timing_read(crsolve_plan p, crsolve_kernel_time *out, int32_t cap, i
  * contraction per step, and whether the FP64 path was used instead.
  */
 int crsolve_mixed_stats(crsolve_plan p, int32_t *iterations, double *delta, double *rho, int32_t *fp64_fallback);
+
+/*
+ * The preconditioner of the mixed-precision form alone: z = A~^{-1} r, one
+ * solve with the FP32 levels and the FP64 coarse levels of the factorisation
+ * (Sec. 2 eq. Formulas, the down and up sweeps, in FP32 on every level with
+ * more than 2 blocks), without refinement; for users who run their own
+ * Krylov iteration around it.  r and z: device [N][m][k] complex128, k <=
+ * kmax, 16-byte aligned, may be the same buffer (r is read first).  Enqueued
+ * on `stream`, no synchronisation.  The accuracy is that of FP32 arithmetic
+ * (about kappa * 2^-24 relative).  CRSOLVE_EUNSUPPORTED for plans other than
+ * CRSOLVE_MIXED, for plans without FP32 levels (N <= 2), and after an FP32
+ * breakdown (the plan then holds only the FP64 factorisation);
+ * CRSOLVE_ENOTFACTORED before crsolve_factor.
+ */
+int crsolve_mixed_precondition(crsolve_plan p, int32_t k, const crsolve_z *r, crsolve_z *z, void *stream);
 
 /*
  * crsolve_residual -- r = y - A x for the block-tridiagonal A of eq. Axb
@@ -447,7 +467,10 @@ int crsolve_tile_set(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc
 int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads,
                      int32_t *threads_solve);
 /* The same for the FP32 levels of the mixed-precision form (their own table;
- * for mt = 64 the factor needs at least 128 threads). */
+ * for mt = 64 the factor needs at least 128 threads, and the solve fields
+ * nb_solve, kc, threads_solve are stored but not used: that class keeps
+ * L^{-1} and solves with fixed-shape product kernels, one odd block and a
+ * column chunk of 8, 16 or 32 (by k) per work item). */
 int crsolve_tile_set_mixed(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc, int32_t threads,
                            int32_t threads_solve);
 int crsolve_tile_get_mixed(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads,

@@ -76,6 +76,7 @@ SIGNATURES = {
     "crsolve_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(_I64)]),
     "crsolve_mixed_stats": (ctypes.c_int, [_P, ctypes.POINTER(_I32), ctypes.POINTER(ctypes.c_double),
                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I32)]),
+    "crsolve_mixed_precondition": (ctypes.c_int, [_P, _I32, _P, _P, _P]),
     "crsolve_tile_set": (ctypes.c_int, [_I32, _I32, _I32, _I32, _I32, _I32]),
     "crsolve_batch_create": (ctypes.c_int, [_I32, _P, _P, _P, ctypes.POINTER(_P)]),
     "crsolve_batch_tile_set": (ctypes.c_int, [_P, _I32, _I32, _I32, _I32]),

@@ -16,7 +16,7 @@ from . import _native as nat
 __all__ = ["Plan", "crsolve_plan_create", "crsolve_factor", "crsolve_solve", "crsolve_backward",
            "crsolve_info_get", "crsolve_solve_host", "crsolve_plan_levels",
            "crsolve_debug_level_system", "crsolve_timing_enable", "crsolve_timing_read",
-           "crsolve_launch_count", "crsolve_mixed_stats", "crsolve_tile_set", "crsolve_tile_get", "crsolve_tile_set_mixed", "crsolve_tile_get_mixed",
+           "crsolve_launch_count", "crsolve_mixed_stats", "crsolve_mixed_precondition", "crsolve_tile_set", "crsolve_tile_get", "crsolve_tile_set_mixed", "crsolve_tile_get_mixed",
            "crsolve_solve_noalloc", "crsolve_peak_probe", "crsolve_residual", "solve", "CRSolveFn",
            "NotPositiveDefinite"]
 
@@ -153,6 +153,22 @@ def crsolve_solve(plan: Plan, y: torch.Tensor, x: torch.Tensor | None = None, st
     with torch.cuda.device(plan.device):
         nat.check(nat.load().crsolve_solve(plan.handle, k, _vp(y), _vp(x), _stream(stream)), "crsolve_solve")
     return x
+
+
+def crsolve_mixed_precondition(plan: Plan, r: torch.Tensor, z: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """z = A~^{-1} r with the FP32 factorisation of a factored CRSOLVE_MIXED plan
+    (no refinement); r, z: [N, m, k] complex128 on the plan's device."""
+    N, m = plan.N, plan.m
+    k = r.shape[-1] if r.dim() == 3 else -1
+    _need(r, (N, m, k), "r", plan.device)
+    if z is None:
+        z = torch.empty_like(r)
+    _need(z, (N, m, k), "z", plan.device)
+    plan.ensure_scratch()
+    with torch.cuda.device(plan.device):
+        nat.check(nat.load().crsolve_mixed_precondition(plan.handle, k, _vp(r), _vp(z), _stream(stream)),
+                  "crsolve_mixed_precondition")
+    return z
 
 
 def crsolve_backward(plan: Plan, x: torch.Tensor, gx: torch.Tensor, want_gA: bool = True,

@@ -207,9 +207,15 @@ def tune_plan_class(m: int, k: int, precision: int = 0, n_blocks: int = 0, devic
             print(f"  mt={mt} k={k} prec={precision} {shape}: {t:.3f} ms")
         return t
 
+    # The FP32 levels of class 64 solve with fixed-shape product kernels (one
+    # odd block per work item, chunk by k): only the factor fields matter there.
+    knobs = (PLAN_NB, PLAN_NB, PLAN_KC, PLAN_THREADS, PLAN_THREADS)
+    factor_only = {0, 3}
     try:
         t_best = trial(best)
-        for i, cands in enumerate((PLAN_NB, PLAN_NB, PLAN_KC, PLAN_THREADS, PLAN_THREADS)):
+        for i, cands in enumerate(knobs):
+            if precision and mt == 64 and i not in factor_only:
+                continue
             for v in cands:
                 shape = list(best)
                 shape[i] = v

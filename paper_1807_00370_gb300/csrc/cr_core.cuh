@@ -107,27 +107,42 @@ __device__ __forceinline__ void trsv_lower_h_col(const C *Lb, const R *ivb, C *c
 // are taken in blocks of 16: the diagonal block is solved per column (a
 // chain of <= 16 rows), then the rows below are updated in parallel, one
 // item per (block, row, column).  Column (b, col) starts at
-// base + b * bstride + col, with row stride ld.  Ends with __syncthreads().
-template <int MT, class R, class C>
+// base + b * bstride + col, with row stride ld.  With kUnit2, a second set of
+// ncols2 columns at base2 + b * bstride2 + j (row stride ld2) is solved in the
+// same passes; column j of it must start as the unit vector e_j, so its rows
+// above j are zero and stay zero and the items that would only add zeros
+// are skipped (ncols2 = m gives L^{-1}).  Ends with __syncthreads().
+template <int MT, class R, class C, bool kUnit2 = false>
 __device__ __forceinline__ void trsm_lower_cta(const C *sL, const R *sInv, C *base, int bstride, int ld, int nbh,
-                                               int ncols, int m) {
+                                               int ncols, int m, C *base2 = nullptr, int bstride2 = 0, int ld2 = 0,
+                                               int ncols2 = 0) {
     constexpr int TRI = Tri<MT>::n, BS = 16;
     const int NT = blockDim.x, tid = threadIdx.x;
+    const int ntot = kUnit2 ? ncols + ncols2 : ncols;
     for (int rb = 0; rb < m; rb += BS) {
         const int re = min(rb + BS, m);
         const int nbr = re - rb;
-        for (int e = tid; e < nbh * ncols; e += NT) {
-            const int b = e / ncols, col = e - b * ncols;
+        for (int e = tid; e < nbh * ntot; e += NT) {
+            const int b = e / ntot, col = e - b * ntot;
             const C *Lb = sL + b * TRI;
             const R *ivb = sInv + b * MT;
             C *z = base + b * bstride + col;
+            int ld_ = ld;
+            if constexpr (kUnit2) {
+                if (col >= ncols) {
+                    const int j = col - ncols;
+                    if (j >= re) continue;   // rows rb .. re-1 of e_j are zero
+                    z = base2 + b * bstride2 + j;
+                    ld_ = ld2;
+                }
+            }
             if constexpr (sizeof(R) == 4) {
                 // FP32 (latency-bound): the column's rows rb .. re-1 in
                 // registers, so the chain waits on FMAs, not on shared memory
                 C zr[BS];
 #pragma unroll
                 for (int i = 0; i < BS; ++i)
-                    if (i < nbr) zr[i] = z[(rb + i) * ld];
+                    if (i < nbr) zr[i] = z[(rb + i) * ld_];
 #pragma unroll
                 for (int i = 0; i < BS; ++i) {
                     if (i < nbr) {
@@ -140,26 +155,35 @@ __device__ __forceinline__ void trsm_lower_cta(const C *sL, const R *sInv, C *ba
                 }
 #pragma unroll
                 for (int i = 0; i < BS; ++i)
-                    if (i < nbr) z[(rb + i) * ld] = zr[i];
+                    if (i < nbr) z[(rb + i) * ld_] = zr[i];
             } else {
                 for (int r = rb; r < re; ++r) {
-                    C acc = z[r * ld];
-                    for (int s = rb; s < r; ++s) zmsub(acc, Lb[tri(r, s)], z[s * ld]);
-                    z[r * ld] = zscale(acc, ivb[r]);
+                    C acc = z[r * ld_];
+                    for (int s = rb; s < r; ++s) zmsub(acc, Lb[tri(r, s)], z[s * ld_]);
+                    z[r * ld_] = zscale(acc, ivb[r]);
                 }
             }
         }
         __syncthreads();
         if (re < m) {
-            const int nr = m - re, per = nr * ncols;
+            const int nr = m - re, per = nr * ntot;
             for (int e = tid; e < nbh * per; e += NT) {
-                const int b = e / per, rem = e - b * per, r = re + rem / ncols, col = rem - (r - re) * ncols;
+                const int b = e / per, rem = e - b * per, r = re + rem / ntot, col = rem - (r - re) * ntot;
                 const C *Lr = sL + b * TRI + tri(r, 0);
                 C *z = base + b * bstride + col;
-                C acc = z[r * ld];
+                int ld_ = ld;
+                if constexpr (kUnit2) {
+                    if (col >= ncols) {
+                        const int j = col - ncols;
+                        if (j >= re) continue;   // rows rb .. re-1 of this column are zero
+                        z = base2 + b * bstride2 + j;
+                        ld_ = ld2;
+                    }
+                }
+                C acc = z[r * ld_];
 #pragma unroll 4
-                for (int s = rb; s < re; ++s) zmsub(acc, Lr[s], z[s * ld]);
-                z[r * ld] = acc;
+                for (int s = rb; s < re; ++s) zmsub(acc, Lr[s], z[s * ld_]);
+                z[r * ld_] = acc;
             }
             __syncthreads();
         }
@@ -367,6 +391,20 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
     C *sV = sL + (size_t)nb * TRI;                                    // [nb][TRI] even block t0+b
     C *sZ = sV + (size_t)nb * TRI;                                    // [nb][MT][2MT] [P | Q]
     R *sInv = reinterpret_cast<R *>(sZ + (size_t)nb * MT * LDZ);  // [nb][MT]
+    // FP32 levels of class MT = 64 (the mixed form): the solves are products
+    // with L^{-1} (cr_solve32.cu), kept in place of L; [nb][MT][MT] after the
+    // tensor-core operand stages, starting as the identity
+    constexpr bool kLinv = std::is_same<R, float>::value && MT == 64;
+    C *sLi = nullptr;
+    if constexpr (kLinv) {
+        unsigned char *st = reinterpret_cast<unsigned char *>(
+            (reinterpret_cast<uintptr_t>(sInv + (size_t)nb * MT) + 1023) & ~(uintptr_t)1023);
+        sLi = reinterpret_cast<C *>(st + tc_stage_bytes(MT));
+        for (int e = tid; e < nbh * MT * MT; e += NT) {
+            const int rem = e % (MT * MT), r = rem / MT, c = rem - r * MT;
+            sLi[e] = zmk((r == c && r < m) ? R(1) : R(0), R(0));
+        }
+    }
 
     // stage the lower triangles of A_2t and A_2t+1, B_{2t-1} (P part) and
     // B_{2t}^H (Q part)
@@ -517,7 +555,9 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
     }
 
     // Z := L^{-1} Z, one item per (block, column); zero columns stay zero
-    if constexpr (MT >= 32) {
+    if constexpr (kLinv) {
+        trsm_lower_cta<MT, R, C, true>(sL, sInv, sZ, MT * LDZ, LDZ, nbh, m2, m, sLi, MT * MT, MT, m);
+    } else if constexpr (MT >= 32) {
         trsm_lower_cta<MT, R, C>(sL, sInv, sZ, MT * LDZ, LDZ, nbh, m2, m);
     } else {
         for (int e = tid; e < nbh * m2; e += NT) {
@@ -529,11 +569,17 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
         __syncthreads();
     }
 
-    // keep L, 1/diag(L) and Z for the solves
+    // keep L (L^{-1} for kLinv), 1/diag(L) and Z for the solves
     for (int e = tid; e < nbh * mm; e += NT) {
         const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        if (CRS_IN(a, kDbgL, (t0 + b) * mm + rem))
-            a.L[(t0 + b) * mm + rem] = (r >= c) ? sL[b * TRI + tri(r, c)] : zmk(R(0), R(0));
+        if (CRS_IN(a, kDbgL, (t0 + b) * mm + rem)) {
+            C v = zmk(R(0), R(0));
+            if (r >= c) {
+                if constexpr (kLinv) v = sLi[(b * MT + r) * MT + c];
+                else v = sL[b * TRI + tri(r, c)];
+            }
+            a.L[(t0 + b) * mm + rem] = v;
+        }
     }
     for (int e = tid; e < nbh * m; e += NT) {
         const int b = e / m, r = e - b * m;

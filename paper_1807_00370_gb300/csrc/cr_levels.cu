@@ -12,6 +12,13 @@ __global__ void __launch_bounds__(256) k_factor_odd(LevelArgsT<R> a) {
     factor_chunk<MT, R>(a, a.c_begin + blockIdx.x, smem_raw);
 }
 
+// The FP32 factor of class MT = 64 (tensor-core Schur product, L^{-1}): its
+// shared memory allows one CTA per SM, so the registers may be spent freely.
+__global__ void __launch_bounds__(256, 1) k_factor_odd_f32_64(LevelArgsT<float> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    factor_chunk<64, float>(a, a.c_begin + blockIdx.x, smem_raw);
+}
+
 template <class R>
 __global__ void __launch_bounds__(256) k_factor_fix(LevelArgsT<R> a) {
     factor_fix_items<R>(a, blockIdx.x * (int64_t)blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
@@ -129,8 +136,9 @@ bool set_tile_shape32(int mt, const TileShape &ts, size_t smem_limit) {
         return false;
     // the tensor-core Schur product of MT = 64 reads TMEM with four warps
     if (mt == 64 && ts.threads < 128) return false;
+    // (the solve fields are not used at MT = 64: see solve_nb32)
     if (factor_smem_bytes(mt, ts.nb_factor, 4) > smem_limit ||
-        solve_smem_bytes(mt, ts.nb_solve, ts.kc_max, 3, 4) > smem_limit)
+        (mt != 64 && solve_smem_bytes(mt, ts.nb_solve, ts.kc_max, 3, 4) > smem_limit))
         return false;
     g_tiles32[i] = ts;
     return true;
@@ -163,7 +171,10 @@ int pick_mt(int m) {
 size_t factor_smem_bytes(int mt, int nb, int rsize) {
     const size_t tri = (size_t)mt * (mt + 1) / 2, cs = 2 * (size_t)rsize;
     size_t b = (size_t)nb * ((2 * tri + 2 * (size_t)mt * mt) * cs + (size_t)mt * rsize);
-    if (rsize == 4 && mt == 64) b += 1024 + tc_stage_bytes(mt);   // tensor-core operand stages (1 KB aligned)
+    if (rsize == 4 && mt == 64) {
+        b += 1024 + tc_stage_bytes(mt);                 // tensor-core operand stages (1 KB aligned)
+        b += (size_t)nb * mt * mt * cs;                  // L^{-1} of every block
+    }
     return b;
 }
 
@@ -183,6 +194,10 @@ static cudaError_t prepare_mt_r(int smem_optin) {
     cudaError_t e;
     e = cudaFuncSetAttribute(k_factor_odd<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
     if (e != cudaSuccess) return e;
+    if constexpr (MT == 64 && sizeof(R) == 4) {
+        e = cudaFuncSetAttribute(k_factor_odd_f32_64, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaFuncSetAttribute(k_solve_down_odd<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_solve_up<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
@@ -205,7 +220,10 @@ cudaError_t prepare_kernels(int mt) {
         case 8: return prepare_mt<8>(optin);
         case 16: return prepare_mt<16>(optin);
         case 32: return prepare_mt<32>(optin);
-        case 64: return prepare_mt<64>(optin);
+        case 64: {
+            const cudaError_t e2 = prepare_mt<64>(optin);
+            return e2 != cudaSuccess ? e2 : prepare_solve_g32(optin);
+        }
         default: return cudaErrorInvalidValue;
     }
 }
@@ -237,8 +255,11 @@ int solve_kc(int mt, int k, int64_t no, int nsm) {
     return spread_kc(tile_shape(mt).kc_max, k, num_ctas(no, solve_nb(mt, no, nsm)), nsm);
 }
 int factor_nb32(int mt, int64_t no, int nsm) { return level_nb(tile_shape32(mt).nb_factor, no, nsm); }
-int solve_nb32(int mt, int64_t no, int nsm) { return level_nb(tile_shape32(mt).nb_solve, no, nsm); }
+// MT = 64: one odd block per work item of the persistent product kernels
+// (cr_solve32.cu), whose column chunk depends on k alone.
+int solve_nb32(int mt, int64_t no, int nsm) { return mt == 64 ? 1 : level_nb(tile_shape32(mt).nb_solve, no, nsm); }
 int solve_kc32(int mt, int k, int64_t no, int nsm) {
+    if (mt == 64) return solve_kc_g32(k);
     return spread_kc(tile_shape32(mt).kc_max, k, num_ctas(no, solve_nb32(mt, no, nsm)), nsm);
 }
 
@@ -260,7 +281,10 @@ template <int MT, class R>
 static cudaError_t factor_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const unsigned grid = odd_grid(a);
     const int th = sizeof(R) == 4 ? tile_shape32(MT).threads : tile_shape(MT).threads;
-    k_factor_odd<MT, R><<<grid, th, factor_smem_bytes(MT, a.nb, sizeof(R)), s>>>(a);
+    if constexpr (MT == 64 && sizeof(R) == 4)
+        k_factor_odd_f32_64<<<grid, th, factor_smem_bytes(MT, a.nb, sizeof(R)), s>>>(a);
+    else
+        k_factor_odd<MT, R><<<grid, th, factor_smem_bytes(MT, a.nb, sizeof(R)), s>>>(a);
     return cudaGetLastError();
 }
 
@@ -318,6 +342,7 @@ cudaError_t launch_solve_down_odd(int mt, const LevelArgsT<double> &a, cudaStrea
     CRS_DISPATCH(solve_down_odd_mt, double, mt, a, s)
 }
 cudaError_t launch_solve_down_odd(int mt, const LevelArgsT<float> &a, cudaStream_t s) {
+    if (mt == 64) return launch_solve_down_g32(a, s);   // L^{-1} form (cr_solve32.cu)
     CRS_DISPATCH(solve_down_odd_mt, float, mt, a, s)
 }
 cudaError_t launch_solve_down_fix(const LevelArgsT<double> &a, int nsm, cudaStream_t s) {
@@ -330,6 +355,7 @@ cudaError_t launch_solve_up(int mt, const LevelArgsT<double> &a, cudaStream_t s)
     CRS_DISPATCH(solve_up_mt, double, mt, a, s)
 }
 cudaError_t launch_solve_up(int mt, const LevelArgsT<float> &a, cudaStream_t s) {
+    if (mt == 64) return launch_solve_up_g32(a, s);
     CRS_DISPATCH(solve_up_mt, float, mt, a, s)
 }
 

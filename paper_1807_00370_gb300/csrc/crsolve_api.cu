@@ -1205,6 +1205,26 @@ int crsolve_solve(crsolve_plan p, int32_t k, const crsolve_z *y, crsolve_z *x, v
                     static_cast<cudaStream_t>(stream));
 }
 
+int crsolve_mixed_precondition(crsolve_plan p, int32_t k, const crsolve_z *r, crsolve_z *z, void *stream) {
+    NvtxRange nv("crsolve_mixed_precondition");
+    if (!p || !r || !z || k < 1) return CRSOLVE_EINVAL;
+    if (k > p->kmax) return CRSOLVE_EUNSUPPORTED;
+    if (!aligned16(r) || !aligned16(z)) return CRSOLVE_EINVAL;
+    if (!p->ws || (p->keep >= 0 && !p->scr)) return CRSOLVE_ENOMEM;
+    if (!p->factored) return CRSOLVE_ENOTFACTORED;
+    if (p->precision != CRSOLVE_MIXED || p->lT == 0 || p->fallback) return CRSOLVE_EUNSUPPORTED;
+    int rc = check_device(p);
+    if (rc) return rc;
+    if ((rc = ensure_prepared(p))) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // r is read (into the FP32 right-hand side) before z is written, so they may alias
+    if ((rc = mixed_correction(p, k, reinterpret_cast<const z2 *>(r), s))) return rc;
+    const crs::c2 *z32 = reinterpret_cast<const crs::c2 *>(p->map() + p->offX32);
+    return launch(p, CRSOLVE_K_CONVERT, 0, p->N, s, [&] {
+        return crs::launch_to_f64(z32, reinterpret_cast<z2 *>(z), p->N * (int64_t)p->m * k, p->nsm, s);
+    });
+}
+
 int crsolve_backward(crsolve_plan p, int32_t k, const crsolve_z *x, const crsolve_z *gx, crsolve_z *gy,
                      crsolve_z *gA, crsolve_z *gB, void *stream) {
     NvtxRange nv("crsolve_backward");

@@ -94,7 +94,7 @@ def main():
     check_plan(plan, "host buffers")
     n += 1
     # mixed precision: CUDA-core and tensor-core classes (FP32 levels, split residuals)
-    for N, m, k in [(300, 8, 4), (129, 64, 32), (77, 40, 3)]:
+    for N, m, k in [(300, 8, 4), (129, 64, 32), (77, 40, 3), (61, 57, 20), (65, 64, 40)]:
         A, B, y = synthetic.gen_system(N, m, k, seed=N + m)
         dA, dB, dy = dev(A, B, y)
         plan = crs.Plan(N, m, k, precision=nat.CRSOLVE_MIXED)

@@ -106,3 +106,41 @@ def test_plain_fp64_at_kappa_1e6(cuda_ok):
     x = crs.crsolve_solve(plan, dy).cpu().numpy()
     xo, _ = oracle.cr_solve(A, B, y)
     assert rel_err(x, xo) <= BOUND
+
+
+# The FP32 preconditioner alone (crsolve_mixed_precondition): one FP32 solve,
+# no refinement.  For the class 33 <= m <= 64 its sweeps are the L^{-1}
+# products of cr_solve32.cu: column chunks of 8 (k <= 8), 16 and 32, ragged
+# last chunks (k = 20, 40), odd m (8-byte copies of L^{-1}) and odd k (8-byte
+# copies of the right-hand sides), N from 3 (one FP32 level) up.  Bound: the
+# FP32 solve's forward error, at most c kappa u_32 with u_32 = 2^-24; these
+# synthetic systems have kappa < 1e2, so 1e-4 leaves c ~ 170.
+PRECOND_BOUND = 1e-4
+
+
+@pytest.mark.parametrize("N,m,k", [(3, 64, 32), (257, 64, 32), (77, 40, 3), (200, 57, 20), (129, 33, 1),
+                                   (300, 64, 40), (64, 48, 9), (1000, 16, 8), (513, 61, 16)])
+def test_mixed_preconditioner_matches_oracle(cuda_ok, N, m, k):
+    A, B, y = synthetic.gen_system(N, m, k, seed=7 * N + m + k)
+    dA, dB, dy = to_dev(A, B if N > 1 else None, y)
+    plan = crs.Plan(N, m, k, precision=nat.CRSOLVE_MIXED)
+    crs.crsolve_factor(plan, dA, dB)
+    z = crs.crsolve_mixed_precondition(plan, dy)
+    xo, io = oracle.cr_solve(A, B, y)
+    assert io["status"] == 0
+    err = rel_err(z.cpu().numpy(), xo)
+    assert err <= PRECOND_BOUND, err
+    # in place (r and z the same buffer) gives the same bits
+    dz = dy.clone()
+    crs.crsolve_mixed_precondition(plan, dz, dz)
+    assert torch.equal(dz, z)
+
+
+def test_mixed_preconditioner_rejects_fp64_plans(cuda_ok):
+    N, m, k = 64, 40, 4
+    A, B, y = synthetic.gen_system(N, m, k, seed=5)
+    dA, dB, dy = to_dev(A, B, y)
+    plan = crs.Plan(N, m, k)
+    crs.crsolve_factor(plan, dA, dB)
+    with pytest.raises(RuntimeError, match="unsupported"):
+        crs.crsolve_mixed_precondition(plan, dy)
