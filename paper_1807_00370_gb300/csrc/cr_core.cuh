@@ -251,76 +251,82 @@ __device__ __forceinline__ void trsm_lower_h_cta(const C *sL, const R *sInv, C *
 
 // ---------------------------------------------- FP32 Schur products (tcgen05)
 
-// Shared memory of the tensor-core Schur product: 1 KB for the mbarrier and
-// the TMEM address, then an A (2MT x KS) and a B (4MT x KS) operand stage for
-// each of the three TF32 pieces of the FP32 operands.
+// Shared memory of the tensor-core Schur product: 1 KB for two mbarriers and
+// the TMEM address, then two operand buffers (double buffering over the
+// K-stages), each holding the three TF32 pieces of one stage of X (2MT rows
+// x kTcKS K-columns of 32-bit elements).
 constexpr int kTcKS = 16;
 __host__ __device__ constexpr size_t tc_stage_bytes(int mt) {
-    return 1024 + 3 * ((size_t)(2 * mt) * kTcKS * 4 + (size_t)(4 * mt) * kTcKS * 4);
+    return 1024 + 2 * 3 * (size_t)(2 * mt) * kTcKS * 4;
 }
 
 // Lower triangle of Z^H Z for one block on the tensor cores (FP32 levels of
-// the mixed form, MT = 64).  With X = [Re Z; Im Z] and Y = [Im Z; -Re Z]
-// (2m x 2m real, rows s' = 0..2m-1), Re(Z^H Z) = X^T X and Im(Z^H Z) = X^T Y,
-// so D = X^T [X | Y] is one real product with M = 2MT = 128, N = 4MT = 256 and
-// K = 2m, accumulated in TMEM over K-stages of 16.  Every FP32 operand is
-// split exactly into three TF32 pieces x = x1 + x2 + x3 (11 significant bits
-// each), and the six products x1 y1, x1 y2, x2 y1, x1 y3, x2 y2, x3 y1 (smallest
-// first) are accumulated in FP32: the dropped terms are below 2^-33 of the
-// product, so the result has the accuracy of FP32 arithmetic, which the
-// iterative refinement needs (a two-piece split, 2^-22, costs refinement
-// steps).  Warps 0-3 then read D (row p = lane of TMEM) and route entry
-// (p, q), q <= p: P^H P to sW, Q^H Q subtracted from sV, Q^H P negated to the
-// next level's B.  Returns false if a wait gave up.
+// the mixed form, MT = 64).  With X = [Re Z; Im Z] (real, rows s' = 0..2m-1,
+// column p = column of Z), Re(Z^H Z) = X^T X and
+// Im(Z^H Z) = (Re Z)^T (Im Z) - (Im Z)^T (Re Z): three real products with
+// M = N = 2MT = 128 into three TMEM accumulators (the imaginary part as the
+// difference of the last two, formed when it is read).  X is stored once per
+// K-stage: rows s0..s0+7 of Re Z as K-columns 0..7 and the same rows of Im Z
+// as K-columns 8..15, so X^T X takes both halves and the cross products one
+// half each as A and the other as B.  Every FP32 operand is split exactly
+// into three TF32 pieces x = x1 + x2 + x3 (11 significant bits each), and
+// the six products x1 y1, x1 y2, x2 y1, x1 y3, x2 y2, x3 y1 (smallest first)
+// are accumulated in FP32: the dropped terms are below 2^-33 of the product,
+// so the result has the accuracy of FP32 arithmetic, which the iterative
+// refinement needs.  The stages alternate between two operand buffers: while
+// the MMAs of one stage run, the threads split the next stage into the other
+// buffer (an mbarrier per buffer, completed by the MMAs' commit, says when a
+// buffer may be refilled; uses0 / uses1 count their commits).  Warps 0-3 then read
+// the accumulators (row p = lane of TMEM) and route entry (p, q), q <= p:
+// P^H P to sW, Q^H Q subtracted from sV, Q^H P negated to the next level's B.
+// Returns false if a wait gave up.
 template <int MT>
-__device__ bool herk_tc_f32(const LevelArgsT<float> &a, int64_t t, const float2 *Zb, float2 *sWb, float2 *sVb,
-                            unsigned char *stage, int &phase) {
-    constexpr int M = 2 * MT, N = 4 * MT, KS = kTcKS;
+__device__ __forceinline__ bool herk_tc_f32(const LevelArgsT<float> &a, int64_t t, const float2 *Zb, float2 *sWb, float2 *sVb,
+                            unsigned char *stage, uint32_t &uses0, uint32_t &uses1, uint32_t &stage_count) {
+    constexpr int M = 2 * MT, KS = kTcKS, HS = KS / 2;
+    constexpr int PIECE = M * KS * 4;
     const int m = a.m, m2 = 2 * m, NT = blockDim.x, tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mm = m * m;
     uint64_t *mbar = reinterpret_cast<uint64_t *>(stage);
-    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(stage + 16);
-    unsigned char *Ap[3], *Bp[3];
-    for (int i = 0; i < 3; ++i) {
-        Ap[i] = stage + 1024 + i * (M * KS * 4);
-        Bp[i] = stage + 1024 + 3 * (M * KS * 4) + i * (N * KS * 4);
-    }
-    const uint32_t tmem = *tmem_slot;
-    constexpr uint32_t idesc = idesc_tf32(M, N);
+    const uint32_t tmem = *reinterpret_cast<uint32_t *>(stage + 16);
+    unsigned char *ops = stage + 1024;
+    constexpr uint32_t idesc = idesc_tf32(M, M);
     bool ok = true;
-    auto xval = [&](int sp, int i) -> float {
-        if (sp >= m2 || i >= m2) return 0.f;
-        return sp < m ? Zb[sp * 2 * MT + i].x : Zb[(sp - m) * 2 * MT + i].y;
-    };
-    auto yval = [&](int sp, int j) -> float {
-        if (sp >= m2 || j >= m2) return 0.f;
-        return sp < m ? Zb[sp * 2 * MT + j].y : -Zb[(sp - m) * 2 * MT + j].x;
-    };
     auto split3 = [](float v, uint32_t &p1, uint32_t &p2, uint32_t &p3) {
         p1 = cvt_tf32(v);
         const float r1 = v - __uint_as_float(p1);
         p2 = cvt_tf32(r1);
         p3 = cvt_tf32(r1 - __uint_as_float(p2));
     };
-    const int nst = (m2 + KS - 1) / KS;
+    const int nst = (m + HS - 1) / HS;
     for (int ks = 0; ks < nst; ++ks) {
-        for (int e = tid; e < M * KS; e += NT) {
-            const int kk = e / M, i = e - kk * M;
-            uint32_t p1, p2, p3;
-            split3(xval(ks * KS + kk, i), p1, p2, p3);
-            const int o = kmaj_off(i, kk, KS);
-            *reinterpret_cast<uint32_t *>(Ap[0] + o) = p1;
-            *reinterpret_cast<uint32_t *>(Ap[1] + o) = p2;
-            *reinterpret_cast<uint32_t *>(Ap[2] + o) = p3;
+        const int buf = (int)(stage_count & 1u);
+        const uint32_t ub = buf ? uses1 : uses0;
+        // the buffer's previous MMAs must have read it; a wait that gives up
+        // (in any thread) ends the product for the whole CTA
+        const bool got = ub == 0 || mbar_wait(smem_u32(&mbar[buf]), (ub - 1) & 1u, 1 << 24);
+        if (__syncthreads_or(!got)) {
+            ok = false;
+            break;
         }
-        for (int e = tid; e < N * KS; e += NT) {
-            const int kk = e / N, n = e - kk * N;
-            uint32_t p1, p2, p3;
-            split3(n < M ? xval(ks * KS + kk, n) : yval(ks * KS + kk, n - M), p1, p2, p3);
-            const int o = kmaj_off(n, kk, KS);
-            *reinterpret_cast<uint32_t *>(Bp[0] + o) = p1;
-            *reinterpret_cast<uint32_t *>(Bp[1] + o) = p2;
-            *reinterpret_cast<uint32_t *>(Bp[2] + o) = p3;
+        unsigned char *B0 = ops + buf * 3 * PIECE;
+        // item e: K-column kk = 4 kh + (e & 3) of the top half (Re Z row
+        // s = ks*HS + kk) and kk + HS of the bottom half (Im Z of the same
+        // row), operand row i = 8 ig + ((e >> 2) & 7); consecutive lanes
+        // write consecutive words of a core matrix
+        for (int e = tid; e < M * HS; e += NT) {
+            const int kk = ((e >> 5) & 1) * 4 + (e & 3), i = (e >> 6) * 8 + ((e >> 2) & 7);
+            const int sr = ks * HS + kk;
+            float2 z = make_float2(0.f, 0.f);
+            if (sr < m && i < m2) z = Zb[sr * 2 * MT + i];
+            uint32_t p[3];
+            split3(z.x, p[0], p[1], p[2]);
+            const int ot = kmaj_off(i, kk, KS), ob = kmaj_off(i, kk + HS, KS);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) *reinterpret_cast<uint32_t *>(B0 + c * PIECE + ot) = p[c];
+            split3(z.y, p[0], p[1], p[2]);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) *reinterpret_cast<uint32_t *>(B0 + c * PIECE + ob) = p[c];
         }
         fence_async_smem();
         tc_fence_before();
@@ -329,32 +335,48 @@ __device__ bool herk_tc_f32(const LevelArgsT<float> &a, int64_t t, const float2 
         if (tid == 0) {
             // (A piece, B piece), smallest terms first
             const int pa[6] = {2, 1, 0, 1, 0, 0}, pb[6] = {0, 1, 2, 0, 1, 0};
-            for (int pass = 0; pass < 6; ++pass)
-                for (int kq = 0; kq < KS / 8; ++kq) {
-                    const uint64_t ad = umma_desc(smem_u32(Ap[pa[pass]]) + kq * 256, 128, (KS / 4) * 128);
-                    const uint64_t bd = umma_desc(smem_u32(Bp[pb[pass]]) + kq * 256, 128, (KS / 4) * 128);
-                    mma_tf32(tmem, ad, bd, idesc, (ks > 0 || pass > 0 || kq > 0) ? 1u : 0u);
-                }
-            tc_commit(smem_u32(mbar));
+            const uint32_t b0 = smem_u32(B0);
+#pragma unroll
+            for (int pass = 0; pass < 6; ++pass) {
+                const uint32_t ab = b0 + pa[pass] * PIECE, bb = b0 + pb[pass] * PIECE;
+                const uint64_t at = umma_desc(ab, 128, (KS / 4) * 128), abot = umma_desc(ab + 256, 128, (KS / 4) * 128);
+                const uint64_t bt = umma_desc(bb, 128, (KS / 4) * 128), bbot = umma_desc(bb + 256, 128, (KS / 4) * 128);
+                const uint32_t first = (ks == 0 && pass == 0) ? 0u : 1u;
+                mma_tf32(tmem, at, bt, idesc, first);                 // Re: X^T X, top half
+                mma_tf32(tmem, abot, bbot, idesc, 1u);                //     and bottom half
+                mma_tf32(tmem + M, at, bbot, idesc, first);           // (Re Z)^T (Im Z)
+                mma_tf32(tmem + 2 * M, abot, bt, idesc, first);       // (Im Z)^T (Re Z)
+            }
+            tc_commit(smem_u32(&mbar[buf]));
         }
-        ok = mbar_wait(smem_u32(mbar), (uint32_t)phase, 1 << 24) && ok;
-        phase ^= 1;
-        tc_fence_after();
+        if (buf) ++uses1;
+        else ++uses0;
+        ++stage_count;
     }
+    // all MMAs of this block: the last commit tracks every earlier one
+    if (ok && stage_count > 0) {
+        const int lb = (int)((stage_count - 1) & 1u);
+        const bool got = mbar_wait(smem_u32(&mbar[lb]), ((lb ? uses1 : uses0) - 1) & 1u, 1 << 24);
+        if (__syncthreads_or(!got)) ok = false;
+    }
+    tc_fence_after();
     if (warp < 4) {
         const int p = warp * 32 + lane;
         const bool hasL = t >= 1, hasR = 2 * t + 1 < a.Nl;
         for (int c = 0; c < M / 32; ++c) {
             if (c * 32 > warp * 32 + 31) break;              // no entry q <= p in this column chunk
-            uint32_t vr[32], vi[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), vr);
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(M + c * 32), vi);
+            uint32_t vr[32], v1[32], v2[32];
+            const uint32_t lanes = (uint32_t)(warp * 32) << 16;
+            tmem_ld32(tmem + lanes + (uint32_t)(c * 32), vr);
+            tmem_ld32(tmem + lanes + (uint32_t)(M + c * 32), v1);
+            tmem_ld32(tmem + lanes + (uint32_t)(2 * M + c * 32), v2);
             if (!ok || p >= m2) continue;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
                 const int q = c * 32 + j;
                 if (q > p || q >= m2) continue;
-                const float dr = __uint_as_float(vr[j]), di = (q == p) ? 0.f : __uint_as_float(vi[j]);
+                const float dr = __uint_as_float(vr[j]);
+                const float di = (q == p) ? 0.f : __uint_as_float(v1[j]) - __uint_as_float(v2[j]);
                 if (p < m) {
                     if (hasL) sWb[tri(p, q)] = make_float2(dr, di);
                 } else if (q >= m) {
@@ -600,16 +622,21 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
         // FP32 levels of the mixed form: on the tensor cores (tcgen05, TF32 x 3)
         unsigned char *stage = reinterpret_cast<unsigned char *>(
             (reinterpret_cast<uintptr_t>(sInv + (size_t)nb * MT) + 1023) & ~(uintptr_t)1023);
-        if (tid == 0) mbar_init(smem_u32(stage), 1);
-        if (tid < 32) tmem_alloc(smem_u32(stage + 16), 2 * 2 * MT);
+        if (tid == 0) {
+            mbar_init(smem_u32(stage), 1);
+            mbar_init(smem_u32(stage + 8), 1);
+        }
+        // three accumulators of 2MT = 128 columns
+        if (tid < 32) tmem_alloc(smem_u32(stage + 16), 512);
         tc_fence_before();
         __syncthreads();
         tc_fence_after();
-        int phase = 0;
+        uint32_t uses0 = 0, uses1 = 0, stage_count = 0;
         bool ok = true;
-        for (int b = 0; b < nbh; ++b)
-            ok = herk_tc_f32<MT>(a, t0 + b, sZ + b * MT * LDZ, sW + b * TRI, sV + b * TRI, stage, phase) && ok;
-        if (tid < 32) tmem_dealloc(*reinterpret_cast<uint32_t *>(stage + 16), 2 * 2 * MT);
+        for (int b = 0; b < nbh && ok; ++b)   // ok is the same in every thread
+            ok = herk_tc_f32<MT>(a, t0 + b, sZ + b * MT * LDZ, sW + b * TRI, sV + b * TRI, stage, uses0, uses1,
+                                 stage_count);
+        if (tid < 32) tmem_dealloc(*reinterpret_cast<uint32_t *>(stage + 16), 512);
         if (!ok && tid == 0 && a.err) atomicExch(a.err, 1);
         __syncthreads();
     } else {
