@@ -46,8 +46,8 @@ def test_mixed_matches_oracle(cuda_ok, N, m, k):
         assert not st["fp64_fallback"] and st["iterations"] <= 4, st
 
 
-def test_mixed_breakdown_flags_equal_fp64(cuda_ok):
-    N, m = 512, 8
+@pytest.mark.parametrize("N,m", [(512, 8), (96, 40), (64, 64)])
+def test_mixed_breakdown_flags_equal_fp64(cuda_ok, N, m):
     for seed in range(20):
         A, B, y = synthetic.gen_system(N, m, 2, seed=seed)
         Ai = synthetic.make_indefinite(A)
