@@ -467,7 +467,7 @@ int crsolve_tile_set(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc
 int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads,
                      int32_t *threads_solve);
 /* The same for the FP32 levels of the mixed-precision form (their own table;
- * for mt = 64 the factor needs at least 128 threads, and the solve fields
+ * for mt = 64 the factor runs with exactly 256 threads, and the solve fields
  * nb_solve, kc, threads_solve are stored but not used: that class keeps
  * L^{-1} and solves with fixed-shape product kernels, one odd block and a
  * column chunk of 8, 16 or 32 (by k) per work item). */

@@ -249,6 +249,10 @@ __device__ __forceinline__ void trsm_lower_h_cta(const C *sL, const R *sInv, C *
     }
 }
 
+}  // namespace crs
+#include "cr_factor32.cuh"   // blocked FP32 factor of class MT = 64 (uses tri, trsm helpers above)
+namespace crs {
+
 // ---------------------------------------------- FP32 Schur products (tcgen05)
 
 // Shared memory of the tensor-core Schur product: 1 KB for two mbarriers and
@@ -413,19 +417,17 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
     C *sV = sL + (size_t)nb * TRI;                                    // [nb][TRI] even block t0+b
     C *sZ = sV + (size_t)nb * TRI;                                    // [nb][MT][2MT] [P | Q]
     R *sInv = reinterpret_cast<R *>(sZ + (size_t)nb * MT * LDZ);  // [nb][MT]
-    // FP32 levels of class MT = 64 (the mixed form): the solves are products
-    // with L^{-1} (cr_solve32.cu), kept in place of L; [nb][MT][MT] after the
-    // tensor-core operand stages, starting as the identity
+    // FP32 levels of class MT = 64 (the mixed form): the factorisation runs by
+    // 16 x 16 blocks (cr_factor32.cuh) and also forms L^{-1}, which is kept in
+    // place of L for the product form of the solves (cr_solve32.cu);
+    // [nb][MT][kF32LdE] after the tensor-core operand stages, zeroed here
     constexpr bool kLinv = std::is_same<R, float>::value && MT == 64;
     C *sLi = nullptr;
     if constexpr (kLinv) {
         unsigned char *st = reinterpret_cast<unsigned char *>(
             (reinterpret_cast<uintptr_t>(sInv + (size_t)nb * MT) + 1023) & ~(uintptr_t)1023);
         sLi = reinterpret_cast<C *>(st + tc_stage_bytes(MT));
-        for (int e = tid; e < nbh * MT * MT; e += NT) {
-            const int rem = e % (MT * MT), r = rem / MT, c = rem - r * MT;
-            sLi[e] = zmk((r == c && r < m) ? R(1) : R(0), R(0));
-        }
+        for (int e = tid; e < nbh * MT * kF32LdE; e += NT) sLi[e] = zmk(R(0), R(0));
     }
 
     // stage the lower triangles of A_2t and A_2t+1, B_{2t-1} (P part) and
@@ -491,104 +493,108 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
     }
     __syncthreads();
 
-    // Cholesky by panels of PW columns (one panel of m columns when MT < 32).
-    // Inside a panel, left-looking by columns: pass 1 of column c computes the
-    // pivots (one item per block, in warps of their own so that the sqrt path
-    // does not diverge from the off-diagonal path) and the unscaled entries
-    // below the pivot, summing only over the panel's earlier columns; pass 2
-    // scales them by 1 / pivot.  After a panel, the trailing lower triangle is
-    // updated in parallel (one item per entry), so the dependent chains of the
-    // column steps stay shorter than PW.
-    const int dpad = (nbh + 31) & ~31;
-    const int PW = (MT >= 32) ? 16 : m;
-    for (int kb = 0; kb < m; kb += PW) {
-        const int ke = min(kb + PW, m);
-        for (int c = kb; c < ke; ++c) {
-            const int below = m - c - 1;
-            for (int e = tid; e < dpad + nbh * below; e += NT) {
-                if (e < nbh) {
-                    const int b = e;
-                    C *Lb = sL + b * TRI;
-                    R d = Lb[tri(c, c)].x;
-                    if constexpr (MT >= 32 && sizeof(R) == 4) {
-                        // fixed trip count: the loads are issued ahead of the FMA chain
-                        const C *Lc = Lb + tri(c, kb);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (kb + j < c) {
-                                const C l = Lc[j];
+    if constexpr (kLinv) {
+        for (int b = 0; b < nbh; ++b)
+            chol_inv_z_f32<MT>(a, report_index(a, 2 * (t0 + b)), sL + b * TRI, sInv + b * MT, sLi + b * MT * kF32LdE,
+                               sZ + b * MT * LDZ);
+    } else {
+        // Cholesky by panels of PW columns (one panel of m columns when MT < 32).
+        // Inside a panel, left-looking by columns: pass 1 of column c computes the
+        // pivots (one item per block, in warps of their own so that the sqrt path
+        // does not diverge from the off-diagonal path) and the unscaled entries
+        // below the pivot, summing only over the panel's earlier columns; pass 2
+        // scales them by 1 / pivot.  After a panel, the trailing lower triangle is
+        // updated in parallel (one item per entry), so the dependent chains of the
+        // column steps stay shorter than PW.
+        const int dpad = (nbh + 31) & ~31;
+        const int PW = (MT >= 32) ? 16 : m;
+        for (int kb = 0; kb < m; kb += PW) {
+            const int ke = min(kb + PW, m);
+            for (int c = kb; c < ke; ++c) {
+                const int below = m - c - 1;
+                for (int e = tid; e < dpad + nbh * below; e += NT) {
+                    if (e < nbh) {
+                        const int b = e;
+                        C *Lb = sL + b * TRI;
+                        R d = Lb[tri(c, c)].x;
+                        if constexpr (MT >= 32 && sizeof(R) == 4) {
+                            // fixed trip count: the loads are issued ahead of the FMA chain
+                            const C *Lc = Lb + tri(c, kb);
+    #pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (kb + j < c) {
+                                    const C l = Lc[j];
+                                    d = fmx(-l.x, l.x, d);
+                                    d = fmx(-l.y, l.y, d);
+                                }
+                        } else {
+                            for (int s = kb; s < c; ++s) {
+                                const C l = Lb[tri(c, s)];
                                 d = fmx(-l.x, l.x, d);
                                 d = fmx(-l.y, l.y, d);
                             }
-                    } else {
-                        for (int s = kb; s < c; ++s) {
-                            const C l = Lb[tri(c, s)];
-                            d = fmx(-l.x, l.x, d);
-                            d = fmx(-l.y, l.y, d);
                         }
+                        if (!(d > R(0))) report_fail(a.status, a.level, report_index(a, 2 * (t0 + b)));
+                        const R iv = rsq(d);
+                        sInv[b * MT + c] = iv;
+                        Lb[tri(c, c)] = zmk(d * iv, R(0));
+                    } else if (e >= dpad) {
+                        const int e2 = e - dpad, b = e2 / below, r = c + 1 + (e2 - b * below);
+                        C *Lb = sL + b * TRI;
+                        C u = Lb[tri(r, c)];
+                        if constexpr (MT >= 32 && sizeof(R) == 4) {
+                            const C *Lr = Lb + tri(r, kb), *Lc = Lb + tri(c, kb);
+    #pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (kb + j < c) zmsub_cb(u, Lr[j], Lc[j]);
+                        } else {
+                            for (int s = kb; s < c; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(c, s)]);
+                        }
+                        Lb[tri(r, c)] = u;
                     }
-                    if (!(d > R(0))) report_fail(a.status, a.level, report_index(a, 2 * (t0 + b)));
-                    const R iv = rsq(d);
-                    sInv[b * MT + c] = iv;
-                    Lb[tri(c, c)] = zmk(d * iv, R(0));
-                } else if (e >= dpad) {
-                    const int e2 = e - dpad, b = e2 / below, r = c + 1 + (e2 - b * below);
+                }
+                __syncthreads();
+                for (int e = tid; e < nbh * below; e += NT) {
+                    const int b = e / below, r = c + 1 + (e - b * below);
+                    C *p = sL + b * TRI + tri(r, c);
+                    *p = zscale(*p, sInv[b * MT + c]);
+                }
+                __syncthreads();
+            }
+            if (ke < m) {
+                // A[r][q] -= sum_{s in panel} L[r][s] conj(L[q][s]) for ke <= q <= r < m
+                const int nr = m - ke, ntr = nr * (nr + 1) / 2;
+                for (int e = tid; e < nbh * ntr; e += NT) {
+                    const int b = e / ntr, f = e - b * ntr, rr = tri_row(f), qq = f - rr * (rr + 1) / 2;
+                    const int r = ke + rr, q = ke + qq;
                     C *Lb = sL + b * TRI;
-                    C u = Lb[tri(r, c)];
-                    if constexpr (MT >= 32 && sizeof(R) == 4) {
-                        const C *Lr = Lb + tri(r, kb), *Lc = Lb + tri(c, kb);
-#pragma unroll
+                    C u = Lb[tri(r, q)];
+                    if constexpr (sizeof(R) == 4) {
+                        const C *Lr = Lb + tri(r, kb), *Lq = Lb + tri(q, kb);
+    #pragma unroll
                         for (int j = 0; j < 16; ++j)
-                            if (kb + j < c) zmsub_cb(u, Lr[j], Lc[j]);
+                            if (kb + j < ke) zmsub_cb(u, Lr[j], Lq[j]);
                     } else {
-                        for (int s = kb; s < c; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(c, s)]);
+                        for (int s = kb; s < ke; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(q, s)]);
                     }
-                    Lb[tri(r, c)] = u;
+                    Lb[tri(r, q)] = u;
                 }
+                __syncthreads();
             }
-            __syncthreads();
-            for (int e = tid; e < nbh * below; e += NT) {
-                const int b = e / below, r = c + 1 + (e - b * below);
-                C *p = sL + b * TRI + tri(r, c);
-                *p = zscale(*p, sInv[b * MT + c]);
-            }
-            __syncthreads();
         }
-        if (ke < m) {
-            // A[r][q] -= sum_{s in panel} L[r][s] conj(L[q][s]) for ke <= q <= r < m
-            const int nr = m - ke, ntr = nr * (nr + 1) / 2;
-            for (int e = tid; e < nbh * ntr; e += NT) {
-                const int b = e / ntr, f = e - b * ntr, rr = tri_row(f), qq = f - rr * (rr + 1) / 2;
-                const int r = ke + rr, q = ke + qq;
-                C *Lb = sL + b * TRI;
-                C u = Lb[tri(r, q)];
-                if constexpr (sizeof(R) == 4) {
-                    const C *Lr = Lb + tri(r, kb), *Lq = Lb + tri(q, kb);
-#pragma unroll
-                    for (int j = 0; j < 16; ++j)
-                        if (kb + j < ke) zmsub_cb(u, Lr[j], Lq[j]);
-                } else {
-                    for (int s = kb; s < ke; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(q, s)]);
-                }
-                Lb[tri(r, q)] = u;
-            }
-            __syncthreads();
-        }
-    }
 
-    // Z := L^{-1} Z, one item per (block, column); zero columns stay zero
-    if constexpr (kLinv) {
-        trsm_lower_cta<MT, R, C, true>(sL, sInv, sZ, MT * LDZ, LDZ, nbh, m2, m, sLi, MT * MT, MT, m);
-    } else if constexpr (MT >= 32) {
-        trsm_lower_cta<MT, R, C>(sL, sInv, sZ, MT * LDZ, LDZ, nbh, m2, m);
-    } else {
-        for (int e = tid; e < nbh * m2; e += NT) {
-            const int b = e / m2, col = e - b * m2;
-            const int64_t pos = 2 * (t0 + b);
-            if (col < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
-            trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sZ + b * MT * LDZ + col, LDZ, m);
+        // Z := L^{-1} Z, one item per (block, column); zero columns stay zero
+        if constexpr (MT >= 32) {
+            trsm_lower_cta<MT, R, C>(sL, sInv, sZ, MT * LDZ, LDZ, nbh, m2, m);
+        } else {
+            for (int e = tid; e < nbh * m2; e += NT) {
+                const int b = e / m2, col = e - b * m2;
+                const int64_t pos = 2 * (t0 + b);
+                if (col < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
+                trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sZ + b * MT * LDZ + col, LDZ, m);
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 
     // keep L (L^{-1} for kLinv), 1/diag(L) and Z for the solves
@@ -597,7 +603,7 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
         if (CRS_IN(a, kDbgL, (t0 + b) * mm + rem)) {
             C v = zmk(R(0), R(0));
             if (r >= c) {
-                if constexpr (kLinv) v = sLi[(b * MT + r) * MT + c];
+                if constexpr (kLinv) v = sLi[(b * MT + r) * kF32LdE + c];
                 else v = sL[b * TRI + tri(r, c)];
             }
             a.L[(t0 + b) * mm + rem] = v;

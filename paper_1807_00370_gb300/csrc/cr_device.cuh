@@ -77,6 +77,20 @@ template <class C> __device__ __forceinline__ void zmsub_ca(C &acc, C a, C b) {
     acc.y = fmx(-a.x, b.y, acc.y);
     acc.y = fmx(a.y, b.x, acc.y);
 }
+// acc += a * b
+template <class C> __device__ __forceinline__ void zmac(C &acc, C a, C b) {
+    acc.x = fmx(a.x, b.x, acc.x);
+    acc.x = fmx(-a.y, b.y, acc.x);
+    acc.y = fmx(a.x, b.y, acc.y);
+    acc.y = fmx(a.y, b.x, acc.y);
+}
+// acc += a * conj(b)
+template <class C> __device__ __forceinline__ void zmac_cb(C &acc, C a, C b) {
+    acc.x = fmx(a.x, b.x, acc.x);
+    acc.x = fmx(a.y, b.y, acc.x);
+    acc.y = fmx(a.y, b.x, acc.y);
+    acc.y = fmx(-a.x, b.y, acc.y);
+}
 // acc += conj(a) * b
 template <class C> __device__ __forceinline__ void zmac_ca(C &acc, C a, C b) {
     acc.x = fmx(a.x, b.x, acc.x);

@@ -134,8 +134,9 @@ bool set_tile_shape32(int mt, const TileShape &ts, size_t smem_limit) {
         ts.threads > 256 || ts.threads % 32 || ts.threads_solve < 32 || ts.threads_solve > 256 ||
         ts.threads_solve % 32)
         return false;
-    // the tensor-core Schur product of MT = 64 reads TMEM with four warps
-    if (mt == 64 && ts.threads < 128) return false;
+    // the FP32 factor of MT = 64 (blocked, tensor-core Schur product) has
+    // its work split for exactly 256 threads
+    if (mt == 64 && ts.threads != 256) return false;
     // (the solve fields are not used at MT = 64: see solve_nb32)
     if (factor_smem_bytes(mt, ts.nb_factor, 4) > smem_limit ||
         (mt != 64 && solve_smem_bytes(mt, ts.nb_solve, ts.kc_max, 3, 4) > smem_limit))
@@ -173,7 +174,7 @@ size_t factor_smem_bytes(int mt, int nb, int rsize) {
     size_t b = (size_t)nb * ((2 * tri + 2 * (size_t)mt * mt) * cs + (size_t)mt * rsize);
     if (rsize == 4 && mt == 64) {
         b += 1024 + tc_stage_bytes(mt);                 // tensor-core operand stages (1 KB aligned)
-        b += (size_t)nb * mt * mt * cs;                  // L^{-1} of every block
+        b += (size_t)nb * mt * kF32LdE * cs;             // L^{-1} of every block (padded rows)
     }
     return b;
 }
