@@ -12,8 +12,8 @@
 //     1. one warp factors the diagonal block D = L_pp in registers (row
 //        16p + lane in lane; right-looking: pivot from lane c, column c
 //        scaled, rank-1 update of the rows below with the entries L[j][c]
-//        from lane j by shuffles), then inverts it: lane c solves column c of
-//        E_pp = D^{-1} by forward substitution;
+//        from lane j by shuffles) and, in the same steps, forms
+//        E_pp = D^{-1} row by row (forward substitution on the identity);
 //     2. the rows below take L_ip = A_ip E_pp^H;
 //     3. the trailing lower triangle is updated, A_ij -= L_ip L_jp^H;
 //   then the blocks of E below the diagonal, by distance d = i - j:
@@ -44,11 +44,21 @@ __device__ __forceinline__ void chol_inv_z_f32(const LevelArgsT<float> &a, int64
 
     for (int p = 0; p < nbk; ++p) {
         const int kb = 16 * p, w = min(16, m - kb);
-        // 1. diagonal block: factor, then invert (warp 0)
+        // 1. diagonal block (warp 0): D = L_pp and its inverse E_pp together.
+        // Lane r holds row r of D and row r of E_pp.  At step c lane c's pivot
+        // d = A_cc - sum |L_cs|^2 is final; its rows of D and E are scaled by
+        // 1 / sqrt(d), lanes r > c scale L[r][c]; then column c of D and row c
+        // of E (both from lane c's step) are shuffled to every lane, and lane
+        // r > c updates L[r][j] -= L[r][c] conj(L[j][c]) (j in (c, r]) and
+        // E[r][j] -= L[r][c] E[c][j] (j <= c): forward substitution on the
+        // identity, row by row, alongside the factorisation.
         if (warp == 0) {
-            C row[16];
+            C row[16], er[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) row[j] = (lane < w && j <= lane) ? Lb[tri(kb + lane, kb + j)] : zero;
+            for (int j = 0; j < 16; ++j) {
+                row[j] = (lane < w && j <= lane) ? Lb[tri(kb + lane, kb + j)] : zero;
+                er[j] = make_float2((lane < w && j == lane) ? 1.f : 0.f, 0.f);
+            }
 #pragma unroll
             for (int c = 0; c < 16; ++c) {
                 if (c < w) {   // the same in every lane
@@ -58,62 +68,68 @@ __device__ __forceinline__ void chol_inv_z_f32(const LevelArgsT<float> &a, int64
                     if (lane == c) {
                         row[c] = make_float2(d * iv, 0.f);
                         ivb[kb + c] = iv;
+#pragma unroll
+                        for (int j = 0; j <= c; ++j) er[j] = zscale(er[j], iv);
                     } else if (lane > c) {
                         row[c] = zscale(row[c], iv);
                     }
+                    // all shuffles of the step first, so that their latencies overlap
+                    C lj[16], ec[16];
 #pragma unroll
-                    for (int j = c + 1; j < 16; ++j) {
-                        if (j < w) {
-                            const C lj = make_float2(__shfl_sync(0xffffffffu, row[c].x, j),
-                                                     __shfl_sync(0xffffffffu, row[c].y, j));
-                            if (lane >= j) zmsub_cb(row[j], row[c], lj);   // L[r][j] -= L[r][c] conj(L[j][c])
-                        }
+                    for (int j = c + 1; j < 16; ++j)
+                        lj[j] = make_float2(__shfl_sync(0xffffffffu, row[c].x, j), __shfl_sync(0xffffffffu, row[c].y, j));
+#pragma unroll
+                    for (int j = 0; j <= c; ++j)
+                        ec[j] = make_float2(__shfl_sync(0xffffffffu, er[j].x, c), __shfl_sync(0xffffffffu, er[j].y, c));
+#pragma unroll
+                    for (int j = c + 1; j < 16; ++j)
+                        if (j < w && lane >= j) zmsub_cb(row[j], row[c], lj[j]);   // L[r][j] -= L[r][c] conj(L[j][c])
+                    if (lane > c && lane < w) {
+#pragma unroll
+                        for (int j = 0; j <= c; ++j) zmsub(er[j], row[c], ec[j]);   // E[r][j] -= L[r][c] E[c][j]
                     }
                 }
             }
             if (lane < w) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (j <= lane) Lb[tri(kb + lane, kb + j)] = row[j];
-            }
-            __syncwarp();
-            if (lane < w) {
-                // column c = lane of E_pp: e_r = (delta_rc - sum_{c<=j<r} D[r][j] e_j) / D[r][r]
-                const int c = lane;
-                C e[16];
-#pragma unroll
-                for (int r = 0; r < 16; ++r) {
-                    C acc = make_float2(r == c ? 1.f : 0.f, 0.f);
-                    if (r < w && r > c) {
-                        const C *Dr = Lb + tri(kb + r, kb);
-#pragma unroll
-                        for (int j = 0; j < r; ++j)
-                            if (j >= c) zmsub(acc, Dr[j], e[j]);
+                for (int j = 0; j < 16; ++j) {
+                    if (j <= lane) {
+                        Lb[tri(kb + lane, kb + j)] = row[j];
+                        E[(kb + lane) * LDE + kb + j] = er[j];
                     }
-                    e[r] = (r < w && r >= c) ? zscale(acc, ivb[kb + r]) : zero;
                 }
-#pragma unroll
-                for (int r = 0; r < 16; ++r)
-                    if (r < w) E[(kb + r) * LDE + kb + c] = e[r];
             }
         }
         __syncthreads();
-        // 2. rows below: L[r][kb + c] = sum_{j <= c} A[r][kb + j] conj(E_pp[c][j])
-        for (int r = kb + w + tid; r < m; r += NT) {
-            C x[16], y[16];
+        // 2. rows below: L[r][kb + c] = sum_{j <= c} A[r][kb + j] conj(E_pp[c][j]),
+        // four threads per row (columns g, g + 4, g + 8, g + 12), results kept
+        // in registers until every thread of the row has read it
+        {
+            const int nbel = m - kb - w;
+            const int r = kb + w + (tid >> 2), g = tid & 3;
+            const bool act = tid < 4 * nbel;
+            C y[4];
+            if (act) {
+                C x[16];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) x[j] = j < w ? Lb[tri(r, kb + j)] : zero;
+                for (int j = 0; j < 16; ++j) x[j] = j < w ? Lb[tri(r, kb + j)] : zero;
 #pragma unroll
-            for (int c = 0; c < 16; ++c) {
-                C acc = zero;
-                const C *Ec = E + (kb + c) * LDE + kb;
+                for (int q = 0; q < 4; ++q) {
+                    const int c = g + 4 * q;
+                    const C *Ec = E + (kb + c) * LDE + kb;
+                    C acc = zero;
 #pragma unroll
-                for (int j = 0; j <= c; ++j) zmac_cb(acc, x[j], Ec[j]);
-                y[c] = acc;
+                    for (int j = 0; j < 16; ++j)
+                        if (j <= c) zmac_cb(acc, x[j], Ec[j]);
+                    y[q] = acc;
+                }
             }
+            __syncthreads();
+            if (act) {
 #pragma unroll
-            for (int c = 0; c < 16; ++c)
-                if (c < w) Lb[tri(r, kb + c)] = y[c];
+                for (int q = 0; q < 4; ++q)
+                    if (g + 4 * q < w) Lb[tri(r, kb + g + 4 * q)] = y[q];
+            }
         }
         __syncthreads();
         // 3. trailing update: A[r][q] -= sum_{j in panel} L[r][j] conj(L[q][j]), kb + w <= q <= r < m
@@ -176,9 +192,13 @@ __device__ __forceinline__ void chol_inv_z_f32(const LevelArgsT<float> &a, int64
 
     // Z = E [B_l | B_r^H]: thread tile of 4 rows x 8 columns (16 row groups x
     // 16 column groups), s <= last row of the tile (E lower triangular); the
-    // products are kept in registers until every thread has read Zb
+    // products are kept in registers until every thread has read Zb.  Warp w
+    // takes rows 8 rb .. 8 rb + 7 with rb = w for w < 4 and 11 - w otherwise,
+    // so that warps w and w + 4 (one scheduler) share 9 of the 36 units of
+    // the triangle.
     {
-        const int cg = tid & 15, rg = tid >> 4;
+        const int wz = tid >> 5, rbz = wz < 4 ? wz : 11 - wz;
+        const int cg = tid & 15, rg = 2 * rbz + ((tid >> 4) & 1);
         C acc[4][8];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
