@@ -432,7 +432,9 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
 
     // stage the lower triangles of A_2t and A_2t+1, B_{2t-1} (P part) and
     // B_{2t}^H (Q part)
-    if constexpr (MT >= 32 && sizeof(R) == 4) {
+    if constexpr (kLinv) {
+        stage_f32_64<MT>(a, t0, nbh, sL, sV, sZ);
+    } else if constexpr (MT >= 32 && sizeof(R) == 4) {
         // FP32 large tiles (one or two CTAs per SM, latency-bound): the loads
         // of U iterations go out together
         // (into registers) before any store, so their latencies overlap

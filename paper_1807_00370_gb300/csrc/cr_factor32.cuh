@@ -27,6 +27,87 @@ namespace crs {
 
 constexpr int kF32LdE = 64 + 2;   // row of E in shared memory (complex), 16-byte padded
 
+__device__ __forceinline__ void f32_cp8(void *dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void f32_cp16(void *dst, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+                 : "memory");
+}
+
+// Staging of a chunk's blocks for the FP32 factor of class MT = 64: the
+// lower triangles of A_2t (-> sL) and A_2t+1 (-> sV, real diagonal) and
+// B_{2t-1} (-> the P columns of sZ) are plain copies and go by cp.async
+// (none of them passes through registers); B_{2t}^H (-> the Q columns of sZ)
+// is a transpose, loaded into registers with consecutive threads on
+// consecutive rows of B_{2t}, so that the transposed stores fall on
+// consecutive words.  Blocks without a left (right) neighbour get zero P (Q).
+// Ends with __syncthreads().
+template <int MT>
+__device__ __forceinline__ void stage_f32_64(const LevelArgsT<float> &a, int64_t t0, int nbh, float2 *sL, float2 *sV,
+                                             float2 *sZ) {
+    constexpr int TRI = MT * (MT + 1) / 2, LDZ = 2 * MT;
+    const int m = a.m, NT = blockDim.x, tid = threadIdx.x, nl = m * (m + 1) / 2;
+    const int64_t mm = (int64_t)m * m;
+    const float2 zero = make_float2(0.f, 0.f);
+    for (int b = 0; b < nbh; ++b) {
+        const int64_t t = t0 + b, pos = 2 * t;
+        for (int f = tid; f < nl; f += NT) {
+            const int r = tri_row(f), c = f - r * (r + 1) / 2;
+            const int64_t o = pos * mm + r * m + c;
+            if (CRS_IN(a, kDbgA, o)) f32_cp8(sL + b * TRI + f, a.A + o);
+            if (t < a.ne && CRS_IN(a, kDbgA, o + mm)) f32_cp8(sV + b * TRI + f, a.A + o + mm);
+        }
+        float2 *Zb = sZ + b * MT * LDZ;
+        if (pos >= 1) {
+            const int64_t o = (pos - 1) * mm;
+            if ((m & 1) == 0) {
+                const int h = m / 2;
+                for (int e = tid; e < m * h; e += NT) {
+                    const int r = e / h, g = e - r * h;
+                    if (CRS_IN(a, kDbgB, o + r * m + 2 * g) && CRS_IN(a, kDbgB, o + r * m + 2 * g + 1))
+                        f32_cp16(Zb + r * LDZ + 2 * g, a.B + o + r * m + 2 * g);
+                }
+            } else {
+                for (int e = tid; e < m * m; e += NT) {
+                    const int r = e / m, c = e - r * m;
+                    if (CRS_IN(a, kDbgB, o + e)) f32_cp8(Zb + r * LDZ + c, a.B + o + e);
+                }
+            }
+        } else {
+            for (int e = tid; e < m * m; e += NT) Zb[(e / m) * LDZ + e % m] = zero;
+        }
+        if (pos + 1 < a.Nl) {
+            const int64_t o = pos * mm;
+            const int ncq = (m + 3) / 4;
+            for (int e = tid; e < m * ncq; e += NT) {
+                const int r = e % m, cq = e / m;   // consecutive threads: consecutive rows r
+                float2 v[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int c = 4 * cq + i;
+                    v[i] = (c < m && CRS_IN(a, kDbgB, o + r * m + c)) ? __ldg(a.B + o + r * m + c) : zero;
+                }
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const int c = 4 * cq + i;
+                    if (c < m) Zb[c * LDZ + m + r] = zconj(v[i]);
+                }
+            }
+        } else {
+            for (int e = tid; e < m * m; e += NT) Zb[(e % m) * LDZ + m + e / m] = zero;
+        }
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    for (int e = tid; e < nbh * m; e += NT) {   // the diagonal of A_2t+1 is real
+        const int b = e / m, r = e - b * m;
+        if (t0 + b < a.ne) sV[b * TRI + tri(r, r)].y = 0.f;
+    }
+    __syncthreads();
+}
+
 // One block, run by the whole CTA.  Lb: packed lower triangle of A (in: the
 // odd diagonal block; out: L); ivb[MT]: 1 / diag(L); E: [MT][kF32LdE], all
 // zero on entry (out: L^{-1}, zero above the diagonal); Zb: [MT][2MT] (in:
