@@ -600,25 +600,56 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
     }
 
     // keep L (L^{-1} for kLinv), 1/diag(L) and Z for the solves
-    for (int e = tid; e < nbh * mm; e += NT) {
-        const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
-        if (CRS_IN(a, kDbgL, (t0 + b) * mm + rem)) {
-            C v = zmk(R(0), R(0));
-            if (r >= c) {
-                if constexpr (kLinv) v = sLi[(b * MT + r) * kF32LdE + c];
-                else v = sL[b * TRI + tri(r, c)];
+    bool bulk_l = false;
+    if constexpr (kLinv) {
+        // Z and (for even m) the rows of L^{-1} leave shared memory by bulk
+        // asynchronous copies, which run under the Schur product below (it
+        // reads sZ and writes neither region); waited for at the end
+        bulk_l = (m & 1) == 0;
+        fence_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            for (int b = 0; b < nbh; ++b) {
+                const int64_t t = t0 + b, oz = t * 2 * (int64_t)mm, ol = t * (int64_t)mm;
+                if (m == MT) {
+                    if (CRS_IN(a, kDbgZ, oz) && CRS_IN(a, kDbgZ, oz + 2 * mm - 1))
+                        bulk_s2g(a.Z + oz, sZ + b * MT * LDZ, (uint32_t)(2 * mm * sizeof(C)));
+                } else {
+                    for (int r = 0; r < m; ++r)
+                        if (CRS_IN(a, kDbgZ, oz + r * m2) && CRS_IN(a, kDbgZ, oz + r * m2 + m2 - 1))
+                            bulk_s2g(a.Z + oz + r * m2, sZ + (b * MT + r) * LDZ, (uint32_t)(m2 * sizeof(C)));
+                }
+                if (bulk_l)
+                    for (int r = 0; r < m; ++r)
+                        if (CRS_IN(a, kDbgL, ol + r * m) && CRS_IN(a, kDbgL, ol + r * m + m - 1))
+                            bulk_s2g(a.L + ol + r * m, sLi + (b * MT + r) * kF32LdE, (uint32_t)(m * sizeof(C)));
             }
-            a.L[(t0 + b) * mm + rem] = v;
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+        }
+    }
+    if (!bulk_l) {
+        for (int e = tid; e < nbh * mm; e += NT) {
+            const int b = e / mm, rem = e - b * mm, r = rem / m, c = rem - r * m;
+            if (CRS_IN(a, kDbgL, (t0 + b) * mm + rem)) {
+                C v = zmk(R(0), R(0));
+                if (r >= c) {
+                    if constexpr (kLinv) v = sLi[(b * MT + r) * kF32LdE + c];
+                    else v = sL[b * TRI + tri(r, c)];
+                }
+                a.L[(t0 + b) * mm + rem] = v;
+            }
         }
     }
     for (int e = tid; e < nbh * m; e += NT) {
         const int b = e / m, r = e - b * m;
         if (CRS_IN(a, kDbgInv, (t0 + b) * m + r)) a.inv[(t0 + b) * m + r] = sInv[b * MT + r];
     }
-    for (int e = tid; e < nbh * m * m2; e += NT) {
-        const int b = e / (m * m2), rem = e - b * (m * m2), r = rem / m2, c = rem - r * m2;
-        if (CRS_IN(a, kDbgZ, (t0 + b) * (int64_t)(m * m2) + rem))
-            a.Z[(t0 + b) * (int64_t)(m * m2) + rem] = sZ[(b * MT + r) * LDZ + c];
+    if constexpr (!kLinv) {
+        for (int e = tid; e < nbh * m * m2; e += NT) {
+            const int b = e / (m * m2), rem = e - b * (m * m2), r = rem / m2, c = rem - r * m2;
+            if (CRS_IN(a, kDbgZ, (t0 + b) * (int64_t)(m * m2) + rem))
+                a.Z[(t0 + b) * (int64_t)(m * m2) + rem] = sZ[(b * MT + r) * LDZ + c];
+        }
     }
     __syncthreads();
 
@@ -731,6 +762,11 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
         if (b + 1 < nbh) v = zsub(v, sW[(b + 1) * TRI + f]);
         if (CRS_IN(a, kDbgAn, j * mm + r * m + c)) a.An[j * mm + r * m + c] = v;
         if (r != c && CRS_IN(a, kDbgAn, j * mm + c * m + r)) a.An[j * mm + c * m + r] = zconj(v);
+    }
+    // the bulk stores of L^{-1} and Z have read shared memory and written
+    // global memory before the CTA ends (the hardware wait of the issuing thread)
+    if constexpr (kLinv) {
+        if (tid == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
 }
 
