@@ -50,14 +50,18 @@
 //     refinement with such a residual is not limited to kappa * u_FP64
 //     (Carson and Higham's extra-precise residual).
 //
-// Data flow per CTA (persistent over block rows, one CTA per SM): 16 warps cut
-// a K-chunk of 32 into slices in shared memory (double-buffered, K-major, no
+// Data flow per CTA (persistent over block rows, one CTA per SM).  With the
+// matrix slices precomputed once per factorisation (an image in the
+// shared-memory layout, CRSOLVE_RESIDUAL_SPLIT_IMAGE, the mixed form's
+// method): k_residual_ws, warp-specialised, streams the images through a
+// four-stage ring (see there).  Without: k_residual_tc, where 16 warps cut a
+// K-chunk of 32 into slices in shared memory (double-buffered, K-major, no
 // swizzle) while one thread issues the MMAs of the previous chunk
 // (tcgen05.mma kind::f16, BF16 inputs, FP32 accumulation in tensor memory)
 // and commits them to the chunk buffer's mbarrier; after the last chunk all
-// warps read the nine accumulators back (tcgen05.ld) and write r.  Every
+// warps read the twelve accumulators back (tcgen05.ld) and write r.  Every
 // mbarrier wait is bounded; on a timeout the kernel records the error, waits
-// (bounded) for its MMAs, frees tensor memory and returns.
+// (bounded) for its MMAs and copies, frees tensor memory and returns.
 #include "crsolve.h"
 #include "cr_launch.h"
 #include "cr_tc.cuh"
@@ -302,23 +306,6 @@ __device__ __forceinline__ void slice_matrix_entry(z2 v, int E, int i, int sl, u
     }
 }
 
-// Precomputed matrix slices: image (j, q) (block row j, K-chunk q) holds the
-// kRtAStage bytes that the product would cut into shared memory for that
-// chunk.  One CTA of kRtThreads per image, grid-stride over the 12 N images.
-__global__ void __launch_bounds__(kRtThreads) k_matrix_image(ResidTcArgs a, unsigned char *img) {
-    const int m = a.m;
-    for (int64_t g = blockIdx.x; g < a.N * 12; g += gridDim.x) {
-        const int64_t j = g / 12;
-        const int q = (int)(g - j * 12), b = q >> 2, s0 = (q & 3) * 16;
-        unsigned char *dst = img + g * (int64_t)kRtAStage;
-        for (int e = threadIdx.x; e < 64 * 16; e += kRtThreads) {
-            const int i = a_row(e), sl = a_col(e);
-            const int E = i < m ? a.erow[j * m + i] : kExpZero;
-            slice_matrix_entry(coupling(a, j, b, i, s0 + sl), E, i, sl, dst);
-        }
-    }
-}
-
 __global__ void __launch_bounds__(256) k_row_exponents(ResidTcArgs a) {
     const int m = a.m;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < a.N * m; e += (int64_t)gridDim.x * blockDim.x) {
@@ -348,12 +335,333 @@ __global__ void __launch_bounds__(256) k_col_exponents(ResidTcArgs a) {
     }
 }
 
-template <bool kImg>
+// ------------------------------------------------ image path, warp-specialised
+//
+// With the matrix slices precomputed (an image per block row and K-chunk of
+// 16, in the shared-memory layout), the residual is a stream of bulk copies
+// into tensor-core products.  Roles, with mbarrier hand-offs instead of CTA
+// barriers, so that copies, slicing, products and the epilogue of different
+// chunks and block rows overlap:
+//   warp 0 (one thread)   copies each chunk's image and the chunk's window
+//                         of x (8 rows x 32 columns, one bulk copy per row)
+//                         into a ring of kWsStages stages (full[s]: all the
+//                         bytes have landed);
+//   warps 2..7            cut the x window of each chunk into slices in the
+//                         stage (xfull[s]: all 192 threads have arrived); the
+//                         stage's full phase also tells them that its slices
+//                         of the chunk kWsStages earlier have been consumed;
+//   warp 1 (one thread)   issues the chunk's MMAs once both have arrived and
+//                         commits them to empty[s] (the stage may be refilled)
+//                         and, after a pass's last chunk, to accfull;
+//   warps 8..15           read the accumulators of a finished pass, write r,
+//                         and arrive on accempty, which the next pass's first
+//                         MMA waits for (tensor memory holds one pass).
+// Every wait is bounded and also ends when another role has given up
+// (sAbort); the roles then stop, wait (bounded) for what they issued, and
+// the kernel reports the error.
+constexpr int kWsKC = 16;                                  // real K per chunk (8 complex columns)
+constexpr int kWsChunks = 3 * 2 * 64 / kWsKC;              // 24 chunks per pass
+constexpr int kWsASlice = kRtM * kWsKC * 2;                // 4096 bytes per matrix slice
+constexpr int kWsAStage = kRtNSA * kWsASlice;              // 40960 bytes of matrix slices
+constexpr int kWsBStage = kRtNSX * kRtNC * kWsKC * 2;      // 9216 bytes of x slices
+constexpr int kWsXStage = 8 * kRtNC * 16;                  // 4096 bytes: the raw x window (complex128)
+constexpr int kWsStage = kWsAStage + kWsBStage + kWsXStage;
+constexpr int kWsStages = 4;
+constexpr int kWsSlicers = 192, kWsEpi = 256;
+static_assert(kWsChunks * kWsAStage == 12 * kRtAStage, "image bytes per block row");
+
+// Byte offset of element (r, k) of a K-major, unswizzled tile of 16-bit
+// elements 16 columns wide: core matrices of 8 rows x 8 elements, the two
+// K-adjacent cores 128 bytes apart, 8-row groups 256 bytes apart.
+__device__ __forceinline__ int kmajw(int r, int k) {
+    return (r >> 3) * 256 + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+// The ten slices of matrix entry v (row i, complex column sl of a chunk, row
+// exponent E) into the image tiles at dst, in the 16-wide layout.
+__device__ __forceinline__ void slice_matrix_entry_w(z2 v, int E, int i, int sl, unsigned char *dst) {
+    const unsigned long long qr = fixq<60>(v.x, E), qi = fixq<60>(v.y, E);
+    const uint32_t sr = dsign(v.x), si = dsign(v.y);
+    const uint32_t baser = 0x4B000000u | sr, basei = 0x4B000000u | si;
+    const float offr = __uint_as_float(0xCB000000u ^ sr), offi = __uint_as_float(0xCB000000u ^ si);
+    const int o_re = kmajw(i, 2 * sl), o_im = kmajw(i + 64, 2 * sl);
+#pragma unroll
+    for (int n = 0; n < kRtNSA; ++n) {
+        const int sh = 54 - 6 * n;
+        const uint32_t mr = (uint32_t)(qr >> sh) & 63u, mi = (uint32_t)(qi >> sh) & 63u;
+        const uint32_t fr = f32_int(mr, baser, offr), fi = f32_int(mi, basei, offi);
+        unsigned char *An = dst + n * kWsASlice;
+        *reinterpret_cast<uint32_t *>(An + o_re) = bf16_pair(fr, fi ^ 0x80000000u);
+        *reinterpret_cast<uint32_t *>(An + o_im) = bf16_pair(fi, fr);
+    }
+}
+
+// Image (j, q) (block row j, chunk q = 8 b + c8: complex columns 8 c8 .. +7
+// of block b of the coupling row): kWsAStage bytes.  Entry e of a chunk: row
+// i = 8 (e >> 6) + ((e >> 2) & 7), column sl = 4 ((e >> 5) & 1) + (e & 3), so
+// that a warp's 32 words are one contiguous 128-byte piece.
+__global__ void __launch_bounds__(kRtThreads) k_matrix_image(ResidTcArgs a, unsigned char *img) {
+    const int m = a.m;
+    for (int64_t g = blockIdx.x; g < a.N * kWsChunks; g += gridDim.x) {
+        const int64_t j = g / kWsChunks;
+        const int q = (int)(g - j * kWsChunks), b = q >> 3, s0 = (q & 7) * 8;
+        unsigned char *dst = img + g * (int64_t)kWsAStage;
+        for (int e = threadIdx.x; e < 64 * 8; e += kRtThreads) {
+            const int i = (e >> 6) * 8 + ((e >> 2) & 7), sl = ((e >> 5) & 1) * 4 + (e & 3);
+            const int E = i < m ? a.erow[j * m + i] : kExpZero;
+            slice_matrix_entry_w(coupling(a, j, b, i, s0 + sl), E, i, sl, dst);
+        }
+    }
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t mbar, uint32_t parity) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(mbar), "r"(parity));
+    return done != 0;
+}
+
+// Bounded wait that also gives up when another role has set *abort.
+__device__ __forceinline__ bool wait_or_abort(uint32_t mbar, uint32_t parity, const volatile int *abort) {
+    const long long t0 = clock64();
+    for (int it = 0; it < kRtWaitPolls; ++it) {
+        if (mbar_test(mbar, parity)) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > 4000000000ll) break;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+__global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = reinterpret_cast<uint64_t *>(base + kWsStages * kWsStage);
+    uint64_t *xfull = full + kWsStages, *empty = xfull + kWsStages;
+    uint64_t *accfull = empty + kWsStages, *accempty = accfull + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accempty + 1);
+    volatile int *sAbort = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int *sEr = reinterpret_cast<int *>(tmem_slot + 4);          // [2][64]
+    int *sEc = sEr + 128;                                        // [2][32]
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m = a.m, k = a.k;
+    const int64_t mk = (int64_t)m * k;
+    const int npass = (k + kRtNC - 1) / kRtNC;
+    const int64_t rows = a.N > blockIdx.x ? (a.N - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t passes = rows * npass, total = passes * kWsChunks;
+
+    if (tid == 0) {
+        for (int s = 0; s < kWsStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&xfull[s]), kWsSlicers);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(accfull), 1);
+        mbar_init(smem_u32(accempty), kWsEpi);
+        *sAbort = 0;
+    }
+    if (warp == 0) tmem_alloc(smem_u32(tmem_slot), kRtTmemCols);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    auto stage = [&](int s) { return base + s * kWsStage; };
+    auto row_of = [&](int64_t P) { return blockIdx.x + (P / npass) * (int64_t)gridDim.x; };
+
+    if (warp == 0) {
+        // producer: chunk images into the ring
+        if (lane == 0) {
+            int64_t G = 0;
+            for (; G < total; ++G) {
+                const int st = (int)(G % kWsStages);
+                const uint32_t use = (uint32_t)(G / kWsStages);
+                if (use > 0 && !wait_or_abort(smem_u32(&empty[st]), (use - 1) & 1u, sAbort)) break;
+                const int64_t P = G / kWsChunks, j = row_of(P);
+                const int c = (int)(G % kWsChunks), col0 = (int)(P % npass) * kRtNC;
+                // the x window: rows s0 .. s0+7 of x_{j-1+b}, columns col0 .. col0+31
+                const int b = c >> 3, s0 = (c & 7) * 8, nc = min(kRtNC, k - col0);
+                const int64_t jb = j - 1 + b;
+                const bool xin = jb >= 0 && jb < a.N;
+                const int nr = xin ? max(0, min(8, m - s0)) : 0;
+                uint32_t rowmask = 0;   // rows whose copy is issued (all of them outside bounds-checked builds)
+                for (int r = 0; r < nr; ++r) {
+                    const int64_t o = jb * mk + (int64_t)(s0 + r) * k + col0;
+                    if (rin(a, kDbgResid, o) && rin(a, kDbgResid, o + nc - 1)) rowmask |= 1u << r;
+                }
+                mbar_expect_tx(smem_u32(&full[st]), (uint32_t)(kWsAStage + __popc(rowmask) * nc * 16));
+                bulk_g2s(smem_u32(stage(st)), a.img + (j * kWsChunks + c) * (int64_t)kWsAStage, (uint32_t)kWsAStage,
+                         smem_u32(&full[st]));
+                for (int r = 0; r < nr; ++r)
+                    if (rowmask >> r & 1u)
+                        bulk_g2s(smem_u32(stage(st) + kWsAStage + kWsBStage + r * kRtNC * 16),
+                                 a.x + jb * mk + (int64_t)(s0 + r) * k + col0, (uint32_t)(nc * 16), smem_u32(&full[st]));
+            }
+            if (G < total) {
+                *sAbort = 1;
+                // the copies issued but not consumed must land before the CTA ends
+                for (int64_t g = (G > kWsStages ? G - kWsStages : 0); g < G; ++g)
+                    mbar_wait(smem_u32(&full[g % kWsStages]), (uint32_t)(g / kWsStages) & 1u, kRtWaitPolls);
+            }
+        }
+    } else if (warp == 1) {
+        // MMA issue
+        if (lane == 0) {
+            int64_t G = 0;
+            bool ok = true;
+            for (; G < total && ok; ++G) {
+                const int st = (int)(G % kWsStages);
+                const uint32_t use = (uint32_t)(G / kWsStages);
+                const int64_t P = G / kWsChunks;
+                const int c = (int)(G % kWsChunks);
+                if (c == 0 && P > 0 && !wait_or_abort(smem_u32(accempty), (uint32_t)(P - 1) & 1u, sAbort)) break;
+                if (!wait_or_abort(smem_u32(&full[st]), use & 1u, sAbort) ||
+                    !wait_or_abort(smem_u32(&xfull[st]), use & 1u, sAbort)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a0 = smem_u32(stage(st)), b0 = a0 + kWsAStage;
+                const uint32_t acc = c == 0 ? 0u : 1u;
+                const uint64_t bd = umma_desc(b0, 128, 256), bd8 = umma_desc(b0 + 8 * (kRtNC / 8) * 256, 128, 256);
+                for (int i = 0; i < kRtNSA; ++i) {
+                    const uint64_t ad = umma_desc(a0 + i * kWsASlice, 128, 256);
+                    const int jmax = min(kRtNSX - 1, kRtND - 1 - i);
+                    if (jmax == kRtNSX - 1) {
+                        mma_bf16(tmem + i * kRtNC, ad, bd, idesc_bf16(kRtM, 256), i == 0 ? acc : 1u);
+                        mma_bf16(tmem + (i + 8) * kRtNC, ad, bd8, idesc_bf16(kRtM, kRtNC), acc);
+                    } else {
+                        mma_bf16(tmem + i * kRtNC, ad, bd, idesc_bf16(kRtM, (jmax + 1) * kRtNC), 1u);
+                    }
+                }
+                tc_commit(smem_u32(&empty[st]));
+                if (c == kWsChunks - 1) tc_commit(smem_u32(accfull));
+            }
+            if (G < total) {
+                *sAbort = 1;
+                // the MMAs committed so far must finish before tensor memory is released
+                if (G > 0) {
+                    const int64_t g = G - 1;
+                    mbar_wait(smem_u32(&empty[g % kWsStages]), (uint32_t)(g / kWsStages) & 1u, kRtWaitPolls);
+                }
+            }
+        }
+    } else if (warp < 8) {
+        // x slicers: 192 threads, 256 entries (8 complex rows x 32 columns) per chunk
+        const int sid = tid - 64;
+        for (int64_t G = 0; G < total; ++G) {
+            const int st = (int)(G % kWsStages);
+            const uint32_t use = (uint32_t)(G / kWsStages);
+            if (!wait_or_abort(smem_u32(&full[st]), use & 1u, sAbort)) {
+                *sAbort = 1;
+                break;
+            }
+            const int64_t P = G / kWsChunks, j = row_of(P);
+            const int c = (int)(G % kWsChunks), col0 = (int)(P % npass) * kRtNC, slot = (int)(P & 1);
+            if (c == 0) {
+                // the pass's exponents (its slot was last read by the epilogue of
+                // pass P - 2, which ended before any MMA of pass P - 1)
+                if (sid < 64) sEr[slot * 64 + sid] = sid < m ? a.erow[j * m + sid] : kExpZero;
+                if (sid >= 64 && sid < 64 + kRtNC) {
+                    const int cc = sid - 64, col = col0 + cc;
+                    int F = kExpZero;
+                    if (col < k) {
+                        F = a.ecol[j * k + col];
+                        if (j > 0) F = max(F, a.ecol[(j - 1) * k + col]);
+                        if (j + 1 < a.N) F = max(F, a.ecol[(j + 1) * k + col]);
+                    }
+                    sEc[slot * 32 + cc] = F;
+                }
+                asm volatile("bar.sync 1, %0;" ::"n"(kWsSlicers) : "memory");
+            }
+            unsigned char *Bs = stage(st) + kWsAStage;
+            const z2 *Xw = reinterpret_cast<const z2 *>(stage(st) + kWsAStage + kWsBStage);
+            const int b = c >> 3, s0 = (c & 7) * 8;
+            const int64_t jb = j - 1 + b;
+            for (int e = sid; e < 8 * kRtNC; e += kWsSlicers) {
+                const int sl = ((e >> 7) << 2) | (e & 3), cc = (((e >> 5) & 3) << 3) | ((e >> 2) & 7);
+                const int s = s0 + sl, col = col0 + cc;
+                z2 v = zmk(0.0, 0.0);
+                if (s < m && col < k && jb >= 0 && jb < a.N) v = Xw[sl * kRtNC + cc];
+                const int F = sEc[slot * 32 + cc];
+                const unsigned long long qr = fixq<54>(v.x, F), qi = fixq<54>(v.y, F);
+                const uint32_t sr = dsign(v.x), si = dsign(v.y);
+                const uint32_t baser = 0x4B000000u | sr, basei = 0x4B000000u | si;
+                const float offr = __uint_as_float(0xCB000000u ^ sr), offi = __uint_as_float(0xCB000000u ^ si);
+#pragma unroll
+                for (int n = 0; n < kRtNSX; ++n) {
+                    const int sh = 48 - 6 * n;
+                    const uint32_t mr = (uint32_t)(qr >> sh) & 63u, mi = (uint32_t)(qi >> sh) & 63u;
+                    *reinterpret_cast<uint32_t *>(Bs + kmajw(n * kRtNC + cc, 2 * sl)) =
+                        bf16_pair(f32_int(mr, baser, offr), f32_int(mi, basei, offi));
+                }
+            }
+            fence_async_smem();
+            mbar_arrive(smem_u32(&xfull[st]));
+        }
+    } else {
+        // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns 16 ((w - 8) / 4) .. +15
+        const int p = (warp & 3) * 32 + lane, i = p & 63, part = p >> 6, half = (warp - 8) >> 2;
+        for (int64_t P = 0; P < passes; ++P) {
+            if (!wait_or_abort(smem_u32(accfull), (uint32_t)P & 1u, sAbort)) {
+                *sAbort = 1;
+                break;
+            }
+            tc_fence_after();
+            const int64_t j = row_of(P);
+            const int col0 = (int)(P % npass) * kRtNC, slot = (int)(P & 1);
+            const int Er = sEr[slot * 64 + i];
+            for (int g = 0; g < 4; ++g) {
+                const int cb = half * 16 + g * 4;
+                uint32_t acc[kRtND][4];
+#pragma unroll
+                for (int d = 0; d < kRtND; ++d)
+                    tmem_ld4(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(d * kRtNC + cb), acc[d]);
+                tmem_wait_ld();
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) {
+                    const int c = cb + cc, col = col0 + c;
+                    if (i >= m || col >= k) continue;
+                    const int F = sEc[slot * 32 + c];
+                    // T = sum_d acc_d 2^(6 (11 - d)), exact (|T| < 2^91)
+                    __int128 T = 0;
+#pragma unroll
+                    for (int d = 0; d < kRtND; ++d) T = T * 64 + (__int128)__float2int_rn(__uint_as_float(acc[d][cc]));
+                    const int64_t ro = (j * m + i) * (int64_t)k + col;
+                    if (!rin(a, kDbgResid, ro)) continue;
+                    double *dst = &a.r[ro].x + part;
+                    const double yv = a.y ? (&a.y[ro].x)[part] : 0.0;
+                    double rv;
+                    if (Er == kExpNonFinite || F == kExpNonFinite) {
+                        rv = __longlong_as_double(0x7FF8000000000000ll);
+                    } else if (Er == kExpZero || F == kExpZero) {
+                        rv = yv;
+                    } else if (!resid_exact(yv, T, Er + F - 76, rv)) {
+                        rv = fma(-(double)T, pow2(Er + F - 76), yv);
+                    }
+                    *dst = rv;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(accempty));
+        }
+    }
+    __syncthreads();
+    if (*sAbort && tid == 0 && a.err) atomicExch(a.err, 1);
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(tmem, kRtTmemCols);
+}
+
+// Without an image: every chunk's matrix slices are cut in the kernel (method
+// CRSOLVE_RESIDUAL_SPLIT).
 __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(base + 2 * kRtStage);   // [2] MMAs of a buffer done
-    uint64_t *fbar = mbar + 2;                                           // [2] image copy into a buffer done
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(base + 2 * kRtStage + 32);
     int *sEr = reinterpret_cast<int *>(base + 2 * kRtStage + 64);        // [64]
     int *sEc = sEr + 64;                                                  // [32]
@@ -361,13 +669,11 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int m = a.m, k = a.k;
-    const int64_t mm = (int64_t)m * m, mk = (int64_t)m * k;
+    const int64_t mk = (int64_t)m * k;
 
     if (tid == 0) {
         mbar_init(smem_u32(&mbar[0]), 1);
         mbar_init(smem_u32(&mbar[1]), 1);
-        mbar_init(smem_u32(&fbar[0]), 1);
-        mbar_init(smem_u32(&fbar[1]), 1);
         *sAbort = 0;
     }
     if (warp == 0) tmem_alloc(smem_u32(tmem_slot), kRtTmemCols);
@@ -377,7 +683,6 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
     const uint32_t tmem = *tmem_slot;
 
     uint32_t uses0 = 0, uses1 = 0;      // commits issued per buffer
-    uint32_t copies0 = 0, copies1 = 0;  // image copies issued per buffer (thread 0)
     bool ok = true;
     const int npass = (k + kRtNC - 1) / kRtNC;
 
@@ -391,12 +696,10 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
     z2 cur_a[kAPer], nxt_a[kAPer], cur_x, nxt_x;
     auto fetch = [&](int64_t jj, int c0, int q, z2 (&va)[kAPer], z2 &vx) {
         const int b = q >> 2, s0 = (q & 3) * 16;
-        if constexpr (!kImg) {
 #pragma unroll
-            for (int u = 0; u < kAPer; ++u) {
-                const int e = tid + u * kRtThreads;
-                va[u] = coupling(a, jj, b, a_row(e), s0 + a_col(e));
-            }
+        for (int u = 0; u < kAPer; ++u) {
+            const int e = tid + u * kRtThreads;
+            va[u] = coupling(a, jj, b, a_row(e), s0 + a_col(e));
         }
         const int s = s0 + x_row(tid), col = c0 + x_col(tid);
         const int64_t jb = jj - 1 + b;
@@ -407,14 +710,6 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
     int64_t j = blockIdx.x;
     int pass = 0;
     if (j < a.N) fetch(j, 0, 0, cur_a, cur_x);
-    if constexpr (kImg) {
-        // the first chunk's matrix slices (chunk g's copy goes to buffer g & 1)
-        if (tid == 0 && j < a.N) {
-            mbar_expect_tx(smem_u32(&fbar[0]), (uint32_t)kRtAStage);
-            bulk_g2s(smem_u32(base), a.img + j * 12 * (int64_t)kRtAStage, (uint32_t)kRtAStage, smem_u32(&fbar[0]));
-            copies0 = 1;
-        }
-    }
     while (j < a.N && ok) {
         const int col0 = pass * kRtNC;
         // the (row, pass) after this one: its first chunk is fetched during the last chunk
@@ -451,12 +746,10 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
             else if (jn < a.N) fetch(jn, pn * kRtNC, 0, nxt_a, nxt_x);
             // matrix slices: 64 rows x 16 complex columns (see a_row / a_col
             // for the bank-conflict-free map)
-            if constexpr (!kImg) {
 #pragma unroll
-                for (int u = 0; u < kAPer; ++u) {
-                    const int e = tid + u * kRtThreads, i = a_row(e), sl = a_col(e);
-                    slice_matrix_entry(cur_a[u], sEr[i], i, sl, As);
-                }
+            for (int u = 0; u < kAPer; ++u) {
+                const int e = tid + u * kRtThreads, i = a_row(e), sl = a_col(e);
+                slice_matrix_entry(cur_a[u], sEr[i], i, sl, As);
             }
             // x slices: 16 complex rows x 32 columns
             {
@@ -483,9 +776,6 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
             __syncthreads();
             tc_fence_after();
             if (tid == 0) {
-                if constexpr (kImg) {
-                    if (!mbar_wait(smem_u32(&fbar[buf]), ub & 1u, kRtWaitPolls)) *sAbort = 1;
-                }
                 const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
                 for (int t = 0; t < kRtKC / 16; ++t) {
                     // the first products of a pass start the accumulators
@@ -506,23 +796,6 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
                     }
                 }
                 tc_commit(smem_u32(&mbar[buf]));
-                if constexpr (kImg) {
-                    // the next chunk's matrix slices go into the other buffer as
-                    // soon as its previous MMAs (chunk g-1) are done, so the copy
-                    // has this chunk's MMAs and the next x slicing to land
-                    const int64_t jc = q + 1 < 12 ? j : jn;
-                    const int qc = q + 1 < 12 ? q + 1 : 0;
-                    if (jc < a.N) {
-                        const int ob = buf ^ 1;
-                        const uint32_t uo = ob ? uses1 : uses0;     // commits of the other buffer so far
-                        if (uo > 0 && !mbar_wait(smem_u32(&mbar[ob]), (uo - 1) & 1u, kRtWaitPolls)) *sAbort = 1;
-                        mbar_expect_tx(smem_u32(&fbar[ob]), (uint32_t)kRtAStage);
-                        bulk_g2s(smem_u32(base + ob * kRtStage), a.img + (jc * 12 + qc) * (int64_t)kRtAStage,
-                                 (uint32_t)kRtAStage, smem_u32(&fbar[ob]));
-                        if (ob) ++copies1;
-                        else ++copies0;
-                    }
-                }
             }
             if (buf) ++uses1;
             else ++uses0;
@@ -585,11 +858,6 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
         // let every committed MMA finish before tensor memory is released
         if (uses0 > 0) mbar_wait(smem_u32(&mbar[0]), (uses0 - 1) & 1u, kRtWaitPolls);
         if (uses1 > 0) mbar_wait(smem_u32(&mbar[1]), (uses1 - 1) & 1u, kRtWaitPolls);
-        if (kImg && tid == 0) {
-            // and every image copy thread 0 issued, consumed or not
-            if (copies0 > 0) mbar_wait(smem_u32(&fbar[0]), (copies0 - 1) & 1u, kRtWaitPolls);
-            if (copies1 > 0) mbar_wait(smem_u32(&fbar[1]), (copies1 - 1) & 1u, kRtWaitPolls);
-        }
     }
     tc_fence_before();
     __syncthreads();
@@ -600,11 +868,12 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_tc(ResidTcArgs a) {
 }  // namespace
 
 size_t residual_tc_smem_bytes() { return 2 * (size_t)kRtStage + 1024 + 1024; }
+static size_t residual_ws_smem_bytes() { return kWsStages * (size_t)kWsStage + 1024 + 1024; }
 
-size_t residual_image_bytes(int64_t N) { return (size_t)N * 12 * (size_t)kRtAStage; }
+size_t residual_image_bytes(int64_t N) { return (size_t)N * kWsChunks * (size_t)kWsAStage; }
 
 cudaError_t launch_matrix_image(const ResidTcArgs &a, unsigned char *img, int nsm, cudaStream_t s) {
-    int64_t g = a.N * 12;
+    int64_t g = a.N * kWsChunks;
     if (g > (int64_t)nsm * 8) g = (int64_t)nsm * 8;
     k_matrix_image<<<(unsigned)g, kRtThreads, 0, s>>>(a, img);
     return cudaGetLastError();
@@ -628,13 +897,14 @@ cudaError_t launch_residual_tc(const ResidTcArgs &a, int nsm, cudaStream_t s) {
     const size_t smem = residual_tc_smem_bytes();
     const int64_t grid = a.N < nsm ? a.N : nsm;
     if (a.img) {
-        e = cudaFuncSetAttribute(k_residual_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const size_t wsm = residual_ws_smem_bytes();
+        e = cudaFuncSetAttribute(k_residual_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wsm);
         if (e != cudaSuccess) return e;
-        k_residual_tc<true><<<(unsigned)grid, kRtThreads, smem, s>>>(a);
+        k_residual_ws<<<(unsigned)grid, kRtThreads, wsm, s>>>(a);
     } else {
-        e = cudaFuncSetAttribute(k_residual_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_residual_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
-        k_residual_tc<false><<<(unsigned)grid, kRtThreads, smem, s>>>(a);
+        k_residual_tc<<<(unsigned)grid, kRtThreads, smem, s>>>(a);
     }
     return cudaGetLastError();
 }

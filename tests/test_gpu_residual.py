@@ -56,7 +56,7 @@ def _check(A, B, x, y, rows=None):
     rows = list(range(N)) if rows is None else rows
     ref = residual_dd(A, B, x, y, rows)
     bs, bf = _bounds(A, B, x, y, rows)
-    for method, bound in (("split", bs), ("fp64", bf)):
+    for method, bound in (("split", bs), ("split_image", bs), ("fp64", bf)):
         r = _gpu(A, B, x, y, method)[rows]
         for part in (np.real, np.imag):
             err = np.abs(part(r) - part(ref))
@@ -128,7 +128,7 @@ def test_zero_and_non_finite_inputs(cuda_ok):
     assert not bad.any()
 
 
-@pytest.mark.parametrize("N,m,k", [(5, 64, 32), (160, 64, 33), (7, 40, 5)])
+@pytest.mark.parametrize("N,m,k", [(5, 64, 32), (160, 64, 33), (7, 40, 5), (1, 64, 32), (2, 33, 65), (305, 64, 32)])
 def test_precomputed_matrix_slices_give_the_same_bits(cuda_ok, N, m, k):
     """"split_image" (matrix slices written once to the workspace and copied
     in by bulk copies, as the mixed form does) equals "split" bit for bit."""
