@@ -342,14 +342,15 @@ __global__ void __launch_bounds__(256) k_col_exponents(ResidTcArgs a) {
 // into tensor-core products.  Roles, with mbarrier hand-offs instead of CTA
 // barriers, so that copies, slicing, products and the epilogue of different
 // chunks and block rows overlap:
-//   warp 0 (one thread)   copies each chunk's image and the chunk's window
-//                         of x (8 rows x 32 columns, one bulk copy per row)
-//                         into a ring of kWsStages stages (full[s]: all the
-//                         bytes have landed);
+//   warp 0 (one thread)   copies each chunk's window of x (8 rows x 32
+//                         columns, one bulk copy per row; xr[s]) and then its
+//                         image (full[s]) into a ring of kWsStages stages;
 //   warps 2..7            cut the x window of each chunk into slices in the
-//                         stage (xfull[s]: all 192 threads have arrived); the
-//                         stage's full phase also tells them that its slices
-//                         of the chunk kWsStages earlier have been consumed;
+//                         stage as soon as it has landed, while the image is
+//                         still arriving (xfull[s]: all 192 threads have
+//                         arrived); the phase of xr[s] also tells them that
+//                         the stage's slices of the chunk kWsStages earlier
+//                         have been consumed (the producer waited for that);
 //   warp 1 (one thread)   issues the chunk's MMAs once both have arrived and
 //                         commits them to empty[s] (the stage may be refilled)
 //                         and, after a pass's last chunk, to accfull;
@@ -442,7 +443,8 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
     unsigned char *base = reinterpret_cast<unsigned char *>(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint64_t *full = reinterpret_cast<uint64_t *>(base + kWsStages * kWsStage);
     uint64_t *xfull = full + kWsStages, *empty = xfull + kWsStages;
-    uint64_t *accfull = empty + kWsStages, *accempty = accfull + 1;
+    uint64_t *xr = empty + kWsStages;                     // [S] the x window of a stage has landed
+    uint64_t *accfull = xr + kWsStages, *accempty = accfull + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(accempty + 1);
     volatile int *sAbort = reinterpret_cast<volatile int *>(tmem_slot + 1);
     int *sEr = reinterpret_cast<int *>(tmem_slot + 4);          // [2][64]
@@ -460,6 +462,7 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&xfull[s]), kWsSlicers);
             mbar_init(smem_u32(&empty[s]), 1);
+            mbar_init(smem_u32(&xr[s]), 1);
         }
         mbar_init(smem_u32(accfull), 1);
         mbar_init(smem_u32(accempty), kWsEpi);
@@ -493,19 +496,24 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
                     const int64_t o = jb * mk + (int64_t)(s0 + r) * k + col0;
                     if (rin(a, kDbgResid, o) && rin(a, kDbgResid, o + nc - 1)) rowmask |= 1u << r;
                 }
-                mbar_expect_tx(smem_u32(&full[st]), (uint32_t)(kWsAStage + __popc(rowmask) * nc * 16));
-                bulk_g2s(smem_u32(stage(st)), a.img + (j * kWsChunks + c) * (int64_t)kWsAStage, (uint32_t)kWsAStage,
-                         smem_u32(&full[st]));
+                // the x window first, on its own barrier, so that the slicers can
+                // cut it while the image is still on its way
+                mbar_expect_tx(smem_u32(&xr[st]), (uint32_t)(__popc(rowmask) * nc * 16));
                 for (int r = 0; r < nr; ++r)
                     if (rowmask >> r & 1u)
                         bulk_g2s(smem_u32(stage(st) + kWsAStage + kWsBStage + r * kRtNC * 16),
-                                 a.x + jb * mk + (int64_t)(s0 + r) * k + col0, (uint32_t)(nc * 16), smem_u32(&full[st]));
+                                 a.x + jb * mk + (int64_t)(s0 + r) * k + col0, (uint32_t)(nc * 16), smem_u32(&xr[st]));
+                mbar_expect_tx(smem_u32(&full[st]), (uint32_t)kWsAStage);
+                bulk_g2s(smem_u32(stage(st)), a.img + (j * kWsChunks + c) * (int64_t)kWsAStage, (uint32_t)kWsAStage,
+                         smem_u32(&full[st]));
             }
             if (G < total) {
                 *sAbort = 1;
                 // the copies issued but not consumed must land before the CTA ends
-                for (int64_t g = (G > kWsStages ? G - kWsStages : 0); g < G; ++g)
+                for (int64_t g = (G > kWsStages ? G - kWsStages : 0); g < G; ++g) {
+                    mbar_wait(smem_u32(&xr[g % kWsStages]), (uint32_t)(g / kWsStages) & 1u, kRtWaitPolls);
                     mbar_wait(smem_u32(&full[g % kWsStages]), (uint32_t)(g / kWsStages) & 1u, kRtWaitPolls);
+                }
             }
         }
     } else if (warp == 1) {
@@ -556,7 +564,7 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
         for (int64_t G = 0; G < total; ++G) {
             const int st = (int)(G % kWsStages);
             const uint32_t use = (uint32_t)(G / kWsStages);
-            if (!wait_or_abort(smem_u32(&full[st]), use & 1u, sAbort)) {
+            if (!wait_or_abort(smem_u32(&xr[st]), use & 1u, sAbort)) {
                 *sAbort = 1;
                 break;
             }
@@ -606,16 +614,32 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
     } else {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns 16 ((w - 8) / 4) .. +15
         const int p = (warp & 3) * 32 + lane, i = p & 63, part = p >> 6, half = (warp - 8) >> 2;
+        // y of the thread's 4 columns of group g (y does not depend on the
+        // products, so it is loaded ahead: group 0 before the accumulators are
+        // ready, group g + 1 while group g is combined)
+        auto load_y = [&](int64_t j, int col0, int g, double (&yv)[4]) {
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) {
+                const int col = col0 + half * 16 + g * 4 + cc;
+                const int64_t ro = (j * m + i) * (int64_t)k + col;
+                yv[cc] = (a.y && i < m && col < k && rin(a, kDbgResid, ro))
+                             ? __ldg(reinterpret_cast<const double *>(a.y + ro) + part)
+                             : 0.0;
+            }
+        };
         for (int64_t P = 0; P < passes; ++P) {
+            const int64_t j = row_of(P);
+            const int col0 = (int)(P % npass) * kRtNC, slot = (int)(P & 1);
+            double ycur[4], ynxt[4];
+            load_y(j, col0, 0, ycur);
             if (!wait_or_abort(smem_u32(accfull), (uint32_t)P & 1u, sAbort)) {
                 *sAbort = 1;
                 break;
             }
             tc_fence_after();
-            const int64_t j = row_of(P);
-            const int col0 = (int)(P % npass) * kRtNC, slot = (int)(P & 1);
             const int Er = sEr[slot * 64 + i];
             for (int g = 0; g < 4; ++g) {
+                if (g + 1 < 4) load_y(j, col0, g + 1, ynxt);
                 const int cb = half * 16 + g * 4;
                 uint32_t acc[kRtND][4];
 #pragma unroll
@@ -634,7 +658,7 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
                     const int64_t ro = (j * m + i) * (int64_t)k + col;
                     if (!rin(a, kDbgResid, ro)) continue;
                     double *dst = &a.r[ro].x + part;
-                    const double yv = a.y ? (&a.y[ro].x)[part] : 0.0;
+                    const double yv = ycur[cc];
                     double rv;
                     if (Er == kExpNonFinite || F == kExpNonFinite) {
                         rv = __longlong_as_double(0x7FF8000000000000ll);
@@ -645,6 +669,8 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
                     }
                     *dst = rv;
                 }
+#pragma unroll
+                for (int cc = 0; cc < 4; ++cc) ycur[cc] = ynxt[cc];
             }
             tc_fence_before();
             mbar_arrive(smem_u32(accempty));
