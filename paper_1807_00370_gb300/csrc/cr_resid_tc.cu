@@ -158,6 +158,15 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
+// 16 consecutive columns of the calling warp's 32 TMEM lanes.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+                 "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                   "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+                 : "r"(taddr));
+}
+
 // 4 consecutive columns of the calling warp's 32 TMEM lanes.
 __device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&v)[4]) {
     asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
@@ -614,9 +623,7 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
     } else {
         // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31, columns 16 ((w - 8) / 4) .. +15
         const int p = (warp & 3) * 32 + lane, i = p & 63, part = p >> 6, half = (warp - 8) >> 2;
-        // y of the thread's 4 columns of group g (y does not depend on the
-        // products, so it is loaded ahead: group 0 before the accumulators are
-        // ready, group g + 1 while group g is combined)
+        // y of the thread's 4 columns of group g
         auto load_y = [&](int64_t j, int col0, int g, double (&yv)[4]) {
 #pragma unroll
             for (int cc = 0; cc < 4; ++cc) {
@@ -630,31 +637,45 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
         for (int64_t P = 0; P < passes; ++P) {
             const int64_t j = row_of(P);
             const int col0 = (int)(P % npass) * kRtNC, slot = (int)(P & 1);
-            double ycur[4], ynxt[4];
-            load_y(j, col0, 0, ycur);
             if (!wait_or_abort(smem_u32(accfull), (uint32_t)P & 1u, sAbort)) {
                 *sAbort = 1;
                 break;
             }
             tc_fence_after();
-            const int Er = sEr[slot * 64 + i];
-            for (int g = 0; g < 4; ++g) {
-                if (g + 1 < 4) load_y(j, col0, g + 1, ynxt);
-                const int cb = half * 16 + g * 4;
-                uint32_t acc[kRtND][4];
+            // The thread's 16 columns: T = sum_d acc_d 2^(6 (11 - d)), exact
+            // (|T| < 2^91), as hi 2^36 + lo with hi = sum_{d<6} acc_d 2^(6 (5 - d))
+            // and lo the rest (each below 2^55 in magnitude, so 64-bit), read
+            // one diagonal (16 columns) at a time; tensor memory is released
+            // right after, so that the next pass's products run while y - A x
+            // is formed.
+            long long hi[16], lo[16];
 #pragma unroll
-                for (int d = 0; d < kRtND; ++d)
-                    tmem_ld4(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(d * kRtNC + cb), acc[d]);
+            for (int q = 0; q < 16; ++q) hi[q] = lo[q] = 0;
+#pragma unroll
+            for (int d = 0; d < kRtND; ++d) {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(d * kRtNC + half * 16), v);
                 tmem_wait_ld();
 #pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const long long x = __float2int_rn(__uint_as_float(v[q]));
+                    if (d < 6) hi[q] = hi[q] * 64 + x;
+                    else lo[q] = lo[q] * 64 + x;
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(accempty));
+            const int Er = sEr[slot * 64 + i];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                double ycur[4];
+                load_y(j, col0, g, ycur);
+#pragma unroll
                 for (int cc = 0; cc < 4; ++cc) {
-                    const int c = cb + cc, col = col0 + c;
+                    const int q = g * 4 + cc, c = half * 16 + q, col = col0 + c;
                     if (i >= m || col >= k) continue;
                     const int F = sEc[slot * 32 + c];
-                    // T = sum_d acc_d 2^(6 (11 - d)), exact (|T| < 2^91)
-                    __int128 T = 0;
-#pragma unroll
-                    for (int d = 0; d < kRtND; ++d) T = T * 64 + (__int128)__float2int_rn(__uint_as_float(acc[d][cc]));
+                    const __int128 T = (__int128)hi[q] * ((__int128)1 << 36) + (__int128)lo[q];
                     const int64_t ro = (j * m + i) * (int64_t)k + col;
                     if (!rin(a, kDbgResid, ro)) continue;
                     double *dst = &a.r[ro].x + part;
@@ -669,11 +690,7 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
                     }
                     *dst = rv;
                 }
-#pragma unroll
-                for (int cc = 0; cc < 4; ++cc) ycur[cc] = ynxt[cc];
             }
-            tc_fence_before();
-            mbar_arrive(smem_u32(accempty));
         }
     }
     __syncthreads();
