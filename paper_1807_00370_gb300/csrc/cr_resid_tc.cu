@@ -609,10 +609,14 @@ __global__ void __launch_bounds__(kRtThreads, 1) k_residual_ws(ResidTcArgs a) {
                 const uint32_t sr = dsign(v.x), si = dsign(v.y);
                 const uint32_t baser = 0x4B000000u | sr, basei = 0x4B000000u | si;
                 const float offr = __uint_as_float(0xCB000000u ^ sr), offi = __uint_as_float(0xCB000000u ^ si);
+                // the 54-bit integers as 30 high and 24 low bits: slices 0..4 from
+                // the high word, 5..8 from the low one, each one 32-bit shift
+                const uint32_t hr = (uint32_t)(qr >> 24), lr = (uint32_t)qr & 0xFFFFFFu;
+                const uint32_t hi_ = (uint32_t)(qi >> 24), li = (uint32_t)qi & 0xFFFFFFu;
 #pragma unroll
                 for (int n = 0; n < kRtNSX; ++n) {
-                    const int sh = 48 - 6 * n;
-                    const uint32_t mr = (uint32_t)(qr >> sh) & 63u, mi = (uint32_t)(qi >> sh) & 63u;
+                    const int sh = n < 5 ? 24 - 6 * n : 18 - 6 * (n - 5);
+                    const uint32_t mr = ((n < 5 ? hr : lr) >> sh) & 63u, mi = ((n < 5 ? hi_ : li) >> sh) & 63u;
                     *reinterpret_cast<uint32_t *>(Bs + kmajw(n * kRtNC + cc, 2 * sl)) =
                         bf16_pair(f32_int(mr, baser, offr), f32_int(mi, basei, offi));
                 }

@@ -137,6 +137,7 @@ __device__ __forceinline__ void gemm_rows(c2 (&acc)[RP][GTile<KC>::RC], const c2
         }
         ++s;
     }
+#pragma unroll 2
     for (; s + 1 < s1; s += 2) {
         c2 v0[RC], v1[RC];
         load_vec<KC>(V, s, cg, v0);
@@ -170,7 +171,7 @@ template <int KC, int RP>
 __device__ __forceinline__ void gemm_cols_h(c2 (&acc)[RP][GTile<KC>::RC], const c2 *Mb, int ldm, int p0, const c2 *V,
                                             int cg, int s0, int s1) {
     constexpr int RC = GTile<KC>::RC;
-#pragma unroll 2
+#pragma unroll 4
     for (int s = s0; s < s1; ++s) {
         c2 v[RC], a[RP];
         load_vec<KC>(V, s, cg, v);
