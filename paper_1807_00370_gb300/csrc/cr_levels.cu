@@ -41,6 +41,18 @@ __global__ void __launch_bounds__(256) k_solve_up(LevelArgsT<R> a) {
     solve_up_chunk<MT, R>(a, a.c_begin + blockIdx.x, blockIdx.y, smem_raw);
 }
 
+// The FP64 sweeps of class 16 at the default 128 threads, with registers
+// capped so that five CTAs fit on an SM (16 warps otherwise): more warps to
+// cover the loads at the start of each chunk.
+__global__ void __launch_bounds__(128, 5) k_solve_down_odd_16c(LevelArgsT<double> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    solve_down_chunk<16, double>(a, a.c_begin + blockIdx.x, blockIdx.y, smem_raw);
+}
+__global__ void __launch_bounds__(128, 5) k_solve_up_16c(LevelArgsT<double> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    solve_up_chunk<16, double>(a, a.c_begin + blockIdx.x, blockIdx.y, smem_raw);
+}
+
 // ------------------------------------------------------------------ adjoint
 
 // gA_j = -1/2 (gy_j x_j^H + x_j gy_j^H) (lower, mirrored), and
@@ -199,6 +211,12 @@ static cudaError_t prepare_mt_r(int smem_optin) {
         e = cudaFuncSetAttribute(k_factor_odd_f32_64, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
         if (e != cudaSuccess) return e;
     }
+    if constexpr (MT == 16 && sizeof(R) == 8) {
+        e = cudaFuncSetAttribute(k_solve_down_odd_16c, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_solve_up_16c, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaFuncSetAttribute(k_solve_down_odd<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_solve_up<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
@@ -293,6 +311,12 @@ template <int MT, class R>
 static cudaError_t solve_down_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const dim3 grid(odd_grid(a), (unsigned)((a.k + a.kc - 1) / a.kc));
     const int th = sizeof(R) == 4 ? tile_shape32(MT).threads_solve : tile_shape(MT).threads_solve;
+    if constexpr (MT == 16 && sizeof(R) == 8) {
+        if (th == 128) {
+            k_solve_down_odd_16c<<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     k_solve_down_odd<MT, R><<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
     return cudaGetLastError();
 }
@@ -301,6 +325,12 @@ template <int MT, class R>
 static cudaError_t solve_up_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const dim3 grid(odd_grid(a), (unsigned)((a.k + a.kc - 1) / a.kc));
     const int th = sizeof(R) == 4 ? tile_shape32(MT).threads_solve : tile_shape(MT).threads_solve;
+    if constexpr (MT == 16 && sizeof(R) == 8) {
+        if (th == 128) {
+            k_solve_up_16c<<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     k_solve_up<MT, R><<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
     return cudaGetLastError();
 }

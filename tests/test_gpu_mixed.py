@@ -144,3 +144,19 @@ def test_mixed_preconditioner_rejects_fp64_plans(cuda_ok):
     crs.crsolve_factor(plan, dA, dB)
     with pytest.raises(RuntimeError, match="unsupported"):
         crs.crsolve_mixed_precondition(plan, dy)
+
+
+def test_mixed_full_size_at_kappa_1e6(cuda_ok):
+    """The precision workload at its full size (N = 2^14, m = 64, k = 32) and
+    the hardest conditioning (κ ≈ 1e6), as the benchmark runs it: the refined
+    solution against the oracle on the whole system, within the stated 1e-10,
+    with no FP64 handover."""
+    case, shift = _kappa_case("mixed_N2p14_m64_k32", 1e6)
+    A, B, y = synthetic.gen_system(case["N"], case["m"], case["k"], case["seed"], shift=shift)
+    x, info, st = _mixed(A, B, y)
+    xo, io = oracle.cr_solve(A, B, y)
+    assert info == io and info["status"] == 0
+    err = rel_err(x, xo)
+    print(f"N=2^14 m=64 k=32 kappa~1e6: rel err vs oracle {err:.2e}, stats {st}")
+    assert err <= BOUND, (err, st)
+    assert not st["fp64_fallback"], st
