@@ -280,9 +280,12 @@ __host__ __device__ constexpr size_t tc_stage_bytes(int mt) {
 // refinement needs.  The stages alternate between two operand buffers: while
 // the MMAs of one stage run, the threads split the next stage into the other
 // buffer (an mbarrier per buffer, completed by the MMAs' commit, says when a
-// buffer may be refilled; uses0 / uses1 count their commits).  Warps 0-3 then read
-// the accumulators (row p = lane of TMEM) and route entry (p, q), q <= p:
-// P^H P to sW, Q^H Q subtracted from sV, Q^H P negated to the next level's B.
+// buffer may be refilled; uses0 / uses1 count their commits).  All eight warps
+// then read the accumulators (row p = lane of TMEM, two warps per lane group,
+// column chunks split between them) and route the entries: P^H P (q <= p < m)
+// to sW, Q^H Q (m <= q <= p) subtracted from sV, and the next level's B =
+// -Q^H P from the upper triangle (p < m <= q), where consecutive lanes hold
+// consecutive entries of a row of B.
 // Returns false if a wait gave up.
 template <int MT>
 __device__ __forceinline__ bool herk_tc_f32(const LevelArgsT<float> &a, int64_t t, const float2 *Zb, float2 *sWb, float2 *sVb,
@@ -364,33 +367,44 @@ __device__ __forceinline__ bool herk_tc_f32(const LevelArgsT<float> &a, int64_t 
         if (__syncthreads_or(!got)) ok = false;
     }
     tc_fence_after();
-    if (warp < 4) {
-        const int p = warp * 32 + lane;
+    // Epilogue by all 8 warps: warp w reads TMEM lanes 32 (w % 4) .. +31 (rows
+    // p) and the column chunks c of parity w / 4.  Row p < m gives P^H P (q <= p,
+    // q < m) and, from the upper triangle, the next level's B: for q in
+    // [m, 2m), B_next[q - m][p] = -(Q^H P)[q - m][p] = -conj(Z^H Z)[p][q], so that
+    // consecutive lanes write consecutive entries; row p >= m gives Q^H Q
+    // (m <= q <= p).
+    if (warp < 8) {
+        const int g = warp & 3, h = warp >> 2, p = g * 32 + lane;
         const bool hasL = t >= 1, hasR = 2 * t + 1 < a.Nl;
-        for (int c = 0; c < M / 32; ++c) {
-            if (c * 32 > warp * 32 + 31) break;              // no entry q <= p in this column chunk
+        const int rlo = g * 32, rhi = g * 32 + 31;
+        for (int c = h; c < M / 32; c += 2) {
+            const int clo = c * 32, chi = c * 32 + 31;
+            const bool needP = rlo < m && clo < m && clo <= rhi;
+            const bool needB = rlo < m && chi >= m && clo < m2;
+            const bool needQ = rhi >= m && rlo < m2 && chi >= m && clo <= rhi;
+            if (!(needP || needB || needQ)) continue;   // the same in every lane of the warp
             uint32_t vr[32], v1[32], v2[32];
-            const uint32_t lanes = (uint32_t)(warp * 32) << 16;
-            tmem_ld32(tmem + lanes + (uint32_t)(c * 32), vr);
-            tmem_ld32(tmem + lanes + (uint32_t)(M + c * 32), v1);
-            tmem_ld32(tmem + lanes + (uint32_t)(2 * M + c * 32), v2);
+            const uint32_t lanes = (uint32_t)(g * 32) << 16;
+            tmem_ld32(tmem + lanes + (uint32_t)clo, vr);
+            tmem_ld32(tmem + lanes + (uint32_t)(M + clo), v1);
+            tmem_ld32(tmem + lanes + (uint32_t)(2 * M + clo), v2);
             if (!ok || p >= m2) continue;
 #pragma unroll
             for (int j = 0; j < 32; ++j) {
-                const int q = c * 32 + j;
-                if (q > p || q >= m2) continue;
+                const int q = clo + j;
+                if (q >= m2) continue;
                 const float dr = __uint_as_float(vr[j]);
                 const float di = (q == p) ? 0.f : __uint_as_float(v1[j]) - __uint_as_float(v2[j]);
                 if (p < m) {
-                    if (hasL) sWb[tri(p, q)] = make_float2(dr, di);
-                } else if (q >= m) {
-                    if (hasR) {
-                        float2 &v = sVb[tri(p - m, q - m)];
-                        v.x -= dr;
-                        v.y -= di;
+                    if (q <= p) {
+                        if (hasL) sWb[tri(p, q)] = make_float2(dr, di);
+                    } else if (q >= m && hasL && hasR && CRS_IN(a, kDbgBn, (t - 1) * mm + (q - m) * m + p)) {
+                        a.Bn[(t - 1) * mm + (q - m) * m + p] = make_float2(-dr, di);
                     }
-                } else if (hasL && hasR && CRS_IN(a, kDbgBn, (t - 1) * mm + (p - m) * m + q)) {
-                    a.Bn[(t - 1) * mm + (p - m) * m + q] = make_float2(-dr, -di);
+                } else if (q >= m && q <= p && hasR) {
+                    float2 &v = sVb[tri(p - m, q - m)];
+                    v.x -= dr;
+                    v.y -= di;
                 }
             }
         }
