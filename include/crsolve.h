@@ -470,7 +470,8 @@ int crsolve_tile_get(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t 
  * for mt = 64 the factor runs with exactly 256 threads, and the solve fields
  * nb_solve, kc, threads_solve are stored but not used: that class keeps
  * L^{-1} and solves with fixed-shape product kernels, one odd block and a
- * column chunk of 8, 16 or 32 (by k) per work item). */
+ * column chunk of 8, 16 or 32 per work item: by k, narrower on levels with
+ * fewer odd blocks than SMs). */
 int crsolve_tile_set_mixed(int32_t mt, int32_t nb_factor, int32_t nb_solve, int32_t kc, int32_t threads,
                            int32_t threads_solve);
 int crsolve_tile_get_mixed(int32_t mt, int32_t *nb_factor, int32_t *nb_solve, int32_t *kc, int32_t *threads,

@@ -54,8 +54,9 @@ cudaError_t launch_solve_up(int mt, const LevelArgsT<double> &a, cudaStream_t s)
 cudaError_t launch_solve_up(int mt, const LevelArgsT<float> &a, cudaStream_t s);
 // FP32 levels of class MT = 64 (cr_solve32.cu): the factor keeps L^{-1} in
 // place of L and both sweeps run as complex products in persistent CTAs, one
-// odd block and solve_kc_g32(k) columns per work item (a.nb = 1, a.kc =
-// solve_kc_g32(a.k)); launch_solve_down_odd / launch_solve_up route there.
+// odd block and a.kc columns per work item (a.nb = 1; a.kc = 8, 16 or 32:
+// solve_kc_g32(a.k), narrowed by solve_kc32 on levels with few odd blocks);
+// launch_solve_down_odd / launch_solve_up route there.
 int solve_kc_g32(int k);
 cudaError_t prepare_solve_g32(int smem_optin);
 cudaError_t launch_solve_down_g32(const LevelArgsT<float> &a, cudaStream_t s);

@@ -278,7 +278,13 @@ int factor_nb32(int mt, int64_t no, int nsm) { return level_nb(tile_shape32(mt).
 // (cr_solve32.cu), whose column chunk depends on k alone.
 int solve_nb32(int mt, int64_t no, int nsm) { return mt == 64 ? 1 : level_nb(tile_shape32(mt).nb_solve, no, nsm); }
 int solve_kc32(int mt, int k, int64_t no, int nsm) {
-    if (mt == 64) return solve_kc_g32(k);
+    if (mt == 64) {
+        // levels with fewer work items than SMs: narrower column chunks, so
+        // that the items of a level spread over more SMs
+        int kc = solve_kc_g32(k);
+        while (kc > 8 && no * ((k + kc - 1) / kc) < nsm) kc /= 2;
+        return kc;
+    }
     return spread_kc(tile_shape32(mt).kc_max, k, num_ctas(no, solve_nb32(mt, no, nsm)), nsm);
 }
 

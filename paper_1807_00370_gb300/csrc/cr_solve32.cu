@@ -521,7 +521,7 @@ cudaError_t prepare_solve_g32(int optin) {
 }
 
 cudaError_t launch_solve_down_g32(const LevelArgsT<float> &a, cudaStream_t s) {
-    if (a.m > kGMT || a.m < 1 || a.nb != 1 || a.kc != solve_kc_g32(a.k)) return cudaErrorInvalidValue;
+    if (a.m > kGMT || a.m < 1 || a.nb != 1 || (a.kc != 8 && a.kc != 16 && a.kc != 32)) return cudaErrorInvalidValue;
     switch (a.kc) {
         case 8: return down_g32<8>(a, s);
         case 16: return down_g32<16>(a, s);
@@ -530,7 +530,7 @@ cudaError_t launch_solve_down_g32(const LevelArgsT<float> &a, cudaStream_t s) {
 }
 
 cudaError_t launch_solve_up_g32(const LevelArgsT<float> &a, cudaStream_t s) {
-    if (a.m > kGMT || a.m < 1 || a.nb != 1 || a.kc != solve_kc_g32(a.k)) return cudaErrorInvalidValue;
+    if (a.m > kGMT || a.m < 1 || a.nb != 1 || (a.kc != 8 && a.kc != 16 && a.kc != 32)) return cudaErrorInvalidValue;
     switch (a.kc) {
         case 8: return up_g32<8>(a, s);
         case 16: return up_g32<16>(a, s);
