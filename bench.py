@@ -60,9 +60,9 @@ FP64_PEAK_GFLOPS = FP64_FMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ / 1e3
 # odd blocks: 538,057,472 + 624,746,752 bytes), valid only while the sources
 # of the kernel's device code are the ones captured (their SHA-256 below).
 # Otherwise the line reports null.
-TRAFFIC_CAPTURE = {"bytes_per_odd_block": (537881344 + 624315904) / (1 << 17),
+TRAFFIC_CAPTURE = {"bytes_per_odd_block": (538565888 + 624200704) / (1 << 17),
                    "sources": ("paper_1807_00370_gb300/csrc/cr_core.cuh", "paper_1807_00370_gb300/csrc/cr_device.cuh"),
-                   "sha256": "ff90e7e79e5261ffd616a6d7a3ff9443d83ba2782d97b86387ca2a580fc582d9"}
+                   "sha256": "3ec9e59d89e9eeaee92964322e2b0cef5e89043d31790d4eadb3d12c05f5f54f"}
 
 
 def captured_traffic_per_odd_block():
