@@ -57,7 +57,7 @@ FP64_FMA_PER_CLK_SM, N_SM, SM_MAX_MHZ = 2, 152, 2070.0
 FP64_PEAK_GFLOPS = FP64_FMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ / 1e3
 # DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum
 # + dram__bytes_write.sum of k_factor_odd<8, double>, level 0 of N = 2^18, 2^17
-# odd blocks: 538,057,472 + 624,746,752 bytes), valid only while the sources
+# odd blocks: 538,565,888 + 624,200,704 bytes), valid only while the sources
 # of the kernel's device code are the ones captured (their SHA-256 below).
 # Otherwise the line reports null.
 TRAFFIC_CAPTURE = {"bytes_per_odd_block": (538565888 + 624200704) / (1 << 17),
@@ -190,6 +190,25 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sms) if sms else None,
                 "sm_max_mhz": max(maxs) if maxs else None,
                 "reasons": sorted(reasons), "samples": len(sms)}
+
+
+def kernel_breakdown(crs, plan, step, steps: int, stream):
+    """Per-kernel CUDA-event times over `steps` more steps, with an event pair
+    around every launch of the plan.  The pairs cost about 2 us per launch
+    (0.6 ms of a 21 ms adjoint step), so the step time itself comes from a
+    run without them; this run gives the kernels' shares and durations.
+    Returns the records [(kind, level, units, ms)] and this run's step time."""
+    import torch
+    crs.crsolve_timing_enable(plan, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    recs = crs.crsolve_timing_read(plan)
+    crs.crsolve_timing_enable(plan, False)
+    return recs, e0.elapsed_time(e1) / steps
 
 
 def reduce_over_ranks(ms: float, units: int, device="cpu"):
@@ -504,16 +523,15 @@ def measure_adjoint(steps: int, warmup: int, with_oracle: bool = True, keep_leve
         step()
     torch.cuda.synchronize()
     launches0 = crs.crsolve_launch_count(plan)
-    crs.crsolve_timing_enable(plan, True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(steps):
         grads = step()
     e1.record(stream)
     torch.cuda.synchronize()
-    recs = crs.crsolve_timing_read(plan)
-    crs.crsolve_timing_enable(plan, False)
     ms_step = e0.elapsed_time(e1) / steps
+    launches = crs.crsolve_launch_count(plan) - launches0
+    recs, ms_step_ev = kernel_breakdown(crs, plan, step, steps, stream)
     adj_ms = sum(r[3] for r in recs if r[0] == "adjoint_outer") / steps
     flops = N * (flops_per_block_row(m, k) + flops_solve_per_odd_block(m, k) + adjoint_flops_per_row(m, k))
     peak_tf = FP64_PEAK_GFLOPS / 1e3
@@ -522,7 +540,8 @@ def measure_adjoint(steps: int, warmup: int, with_oracle: bool = True, keep_leve
         by[kind] = by.get(kind, 0.0) + kms / steps
     out = {
         "metric": "block-rows/s", "value": N / (ms_step * 1e-3), "unit": "block-rows/s",
-        "ms_per_step": ms_step, "steps": steps, "warmup": max(warmup, 3),
+        "ms_per_step": ms_step, "ms_per_step_with_kernel_events": ms_step_ev, "steps": steps,
+        "warmup": max(warmup, 3),
         "config": {"workload": ADJ_WORKLOAD, "N": N, "m": m, "k": k, "seed": ADJ_SEED},
         "roofline": {"bound": "alu", "kernel": "whole forward + backward step",
                      "achieved": flops / (ms_step * 1e-3) / 1e12, "peak": peak_tf, "unit": "TFLOP/s",
@@ -530,7 +549,7 @@ def measure_adjoint(steps: int, warmup: int, with_oracle: bool = True, keep_leve
                      "adjoint_outer_frac": (N * adjoint_flops_per_row(m, k) / (adj_ms * 1e-3) / 1e12 / peak_tf)
                      if adj_ms else None},
         "kernels": {kk: {"ms_per_step": v} for kk, v in by.items()},
-        "gpu_launches": crs.crsolve_launch_count(plan) - launches0,
+        "gpu_launches": launches,
     }
     if with_oracle:
         import oracle
@@ -622,23 +641,25 @@ def measure_mixed(steps: int, warmup: int, log2n: int = 14, with_oracle: bool = 
                 crs.crsolve_factor(plan, dA, dB)
                 crs.crsolve_solve(plan, dy, x)
             torch.cuda.synchronize()
-            crs.crsolve_timing_enable(plan, True)
             launches0 = crs.crsolve_launch_count(plan)
+
+            def step():
+                crs.crsolve_factor(plan, dA, dB)
+                crs.crsolve_solve(plan, dy, x)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             for _ in range(steps):
-                crs.crsolve_factor(plan, dA, dB)
-                crs.crsolve_solve(plan, dy, x)
+                step()
             e1.record(stream)
             torch.cuda.synchronize()
+            launches = (crs.crsolve_launch_count(plan) - launches0) // steps
+            stats = crs.crsolve_mixed_stats(plan) if prec == nat.CRSOLVE_MIXED else None
+            recs, _ = kernel_breakdown(crs, plan, step, steps, stream)
             by = {}
-            for kind, _, _, kms in crs.crsolve_timing_read(plan):
+            for kind, _, _, kms in recs:
                 by[kind] = round(by.get(kind, 0.0) + kms / steps, 3)
-            crs.crsolve_timing_enable(plan, False)
             res[pname] = {"ms": e0.elapsed_time(e1) / steps, "x": x, "kernels_ms": by,
-                          "launches": (crs.crsolve_launch_count(plan) - launches0) // steps,
-                          "info": crs.crsolve_info_get(plan),
-                          "stats": crs.crsolve_mixed_stats(plan) if prec == nat.CRSOLVE_MIXED else None}
+                          "launches": launches, "info": crs.crsolve_info_get(plan), "stats": stats}
             plan.close()
         err = float((torch.linalg.norm(res["mixed"]["x"] - res["fp64"]["x"]) / torch.linalg.norm(res["fp64"]["x"])).item())
         run = {"kappa": float(kap), "shift": shifts["shifts"][kap], "mixed_ms": res["mixed"]["ms"],
@@ -761,7 +782,6 @@ def run_alg1(args):
     sampler.start()
     time.sleep(1.0)
     launches0 = crs.crsolve_launch_count(plan)
-    crs.crsolve_timing_enable(plan, True)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -772,14 +792,13 @@ def run_alg1(args):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    sampler.mark(False)
     if ws > 1:
         torch.distributed.barrier()
-    clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    recs = crs.crsolve_timing_read(plan)
-    crs.crsolve_timing_enable(plan, False)
     launches = crs.crsolve_launch_count(plan) - launches0
+    recs, _ = kernel_breakdown(crs, plan, step, args.steps, stream)
+    sampler.mark(False)
+    clocks = sampler.stop()
     ms, total_units = reduce_over_ranks(ms, N * args.steps, dev)
     ms_step = ms / args.steps
     value = total_units / (ms * 1e-3)
@@ -990,7 +1009,6 @@ def main():
     sampler.start()
     time.sleep(1.0)
     launches0 = crs.crsolve_launch_count(plan)
-    crs.crsolve_timing_enable(plan, True)
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -1001,14 +1019,13 @@ def main():
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    sampler.mark(False)
     if ws > 1:
         torch.distributed.barrier()
-    clocks = sampler.stop()
     ms = e0.elapsed_time(e1)
-    recs = crs.crsolve_timing_read(plan)
-    crs.crsolve_timing_enable(plan, False)
     launches = crs.crsolve_launch_count(plan) - launches0
+    recs, ms_step_ev = kernel_breakdown(crs, plan, step, args.steps, stream)
+    sampler.mark(False)
+    clocks = sampler.stop()
     ms, total_units = reduce_over_ranks(ms, N_BLOCKS * args.steps, dev)
 
     # per-kernel breakdown and the dominant kernel's roofline (FP64 pipe)
@@ -1087,12 +1104,15 @@ def main():
         line = {
             "metric": "block-rows/s", "value": value, "unit": "block-rows/s", "n_gpus": ws,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms_step,
+            "ms_per_step_with_kernel_events": ms_step_ev,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128 (f64)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "N": N_BLOCKS, "m": M, "k": K_RHS, "seed": SEED,
                        "l2": "inputs larger than L2 (A alone 1 GiB), no flush", "parallelism":
                        f"{ws} independent system(s), one per GPU"},
-            "roofline": {"bound": "alu", "kernel": "k_factor_odd<8>, all levels",
+            "roofline": {"bound": "alu", "kernel": "k_factor_odd<8> (and its coarse-level form "
+                                                  "k_factor_odd_wide<8>), all levels; per-launch CUDA events "
+                                                  "over a second run of the same steps",
                          "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                          "frac": (achieved / peak_tf) if achieved else None,
                          "traffic": (traffic_blk * (fac["units"] / max(fac["launches"], 1))) if traffic_blk else None,

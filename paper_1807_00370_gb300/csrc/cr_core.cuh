@@ -72,6 +72,8 @@ __device__ __forceinline__ void trsv_lower_col(const C *Lb, const R *ivb, C *col
 }
 
 // z := L^{-H} z for one column z (shared memory, stride ld); L packed lower.
+// Row r subtracts the terms of rows s = m-1 down to r+1, the order in which
+// trsv_lower_h_wide produces them.
 template <int MT, class R, class C>
 __device__ __forceinline__ void trsv_lower_h_col(const C *Lb, const R *ivb, C *col, int ld, int m) {
     if constexpr (MT <= 16) {
@@ -84,7 +86,7 @@ __device__ __forceinline__ void trsv_lower_h_col(const C *Lb, const R *ivb, C *c
             if (r < m) {
                 C acc = z[r];
 #pragma unroll
-                for (int s = r + 1; s < MT; ++s)
+                for (int s = MT - 1; s > r; --s)
                     if (s < m) zmsub_ca(acc, Lb[tri(s, r)], z[s]);
                 z[r] = zscale(acc, ivb[r]);
             }
@@ -95,9 +97,128 @@ __device__ __forceinline__ void trsv_lower_h_col(const C *Lb, const R *ivb, C *c
     } else {
         for (int r = m - 1; r >= 0; --r) {
             C acc = col[r * ld];
-            for (int s = r + 1; s < m; ++s) zmsub_ca(acc, Lb[tri(s, r)], col[s * ld]);
+            for (int s = m - 1; s > r; --s) zmsub_ca(acc, Lb[tri(s, r)], col[s * ld]);
             col[r * ld] = zscale(acc, ivb[r]);
         }
+    }
+}
+
+// Chunks with few columns to solve (the coarse levels, one or two odd blocks
+// per CTA): a column per thread leaves most of the CTA idle while one warp
+// runs a dependent chain of m(m-1)/2 complex FMAs per column, and on GB300 a
+// warp's FP64 instruction holds its sub-partition's FP64 pipe for about 64
+// cycles (2 DFMA per clock per SM), so that chain takes ~15 us at m = 16.
+// The wide forms below take the same operations in the same order (results
+// bit-identical to the column-per-thread forms) but spread each step over
+// (block, row, column) items: row s is final, then every row below it is
+// updated in parallel, and the next row is scaled by the item that finishes
+// it, so a step costs one barrier.
+
+// Z := L^{-1} Z for columns c < ncols of blocks b < nbh (column (b, c) at
+// base + b * bstride + c, row stride ld); skip(b, c) marks columns that stay
+// zero.  Same operations and order as trsv_lower_col.  Ends with
+// __syncthreads().
+template <int MT, class R, class C, class Skip>
+__device__ __forceinline__ void trsv_lower_wide(const C *sL, const R *sInv, C *base, int bstride, int ld, int nbh,
+                                                int ncols, int m, Skip skip) {
+    constexpr int TRI = Tri<MT>::n;
+    const int NT = blockDim.x, tid = threadIdx.x, nc = nbh * ncols;
+    for (int e = tid; e < nc; e += NT) {
+        const int b = e / ncols, c = e - b * ncols;
+        if (skip(b, c)) continue;
+        C *p = base + b * bstride + c;
+        *p = zscale(*p, sInv[b * MT]);
+    }
+    __syncthreads();
+    for (int s = 0; s + 1 < m; ++s) {
+        const int nr = m - 1 - s, per_b = nr * ncols;
+        for (int e = tid; e < nbh * per_b; e += NT) {
+            const int b = e / per_b, rem = e - b * per_b, r = s + 1 + rem / ncols, c = rem % ncols;
+            if (skip(b, c)) continue;
+            C *col = base + b * bstride + c;
+            C acc = col[r * ld];
+            zmsub(acc, sL[b * TRI + tri(r, s)], col[s * ld]);
+            if (r == s + 1) acc = zscale(acc, sInv[b * MT + r]);
+            col[r * ld] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// Z := L^{-H} Z for columns c < ncols of blocks b < nbh (layout as in
+// trsv_lower_wide).  Same operations and order as trsv_lower_h_col.  Ends
+// with __syncthreads().
+template <int MT, class R, class C>
+__device__ __forceinline__ void trsv_lower_h_wide(const C *sL, const R *sInv, C *base, int bstride, int ld, int nbh,
+                                                  int ncols, int m) {
+    constexpr int TRI = Tri<MT>::n;
+    const int NT = blockDim.x, tid = threadIdx.x, nc = nbh * ncols;
+    for (int e = tid; e < nc; e += NT) {
+        const int b = e / ncols, c = e - b * ncols;
+        C *p = base + b * bstride + c + (m - 1) * ld;
+        *p = zscale(*p, sInv[b * MT + m - 1]);
+    }
+    __syncthreads();
+    for (int s = m - 1; s >= 1; --s) {
+        const int per_b = s * ncols;   // rows 0 .. s-1
+        for (int e = tid; e < nbh * per_b; e += NT) {
+            const int b = e / per_b, rem = e - b * per_b, r = rem / ncols, c = rem % ncols;
+            C *col = base + b * bstride + c;
+            C acc = col[r * ld];
+            zmsub_ca(acc, sL[b * TRI + tri(s, r)], col[s * ld]);
+            if (r == s - 1) acc = zscale(acc, sInv[b * MT + r]);
+            col[r * ld] = acc;
+        }
+        __syncthreads();
+    }
+}
+
+// Right-looking Cholesky A_b = L_b L_b^H of the blocks b < nbh of a chunk
+// (packed lower in sL, 1 / diag(L) to sInv) with the breakdown test of
+// factor_chunk: the same operations in the same order as its left-looking
+// column steps (entry (r, q) subtracts L_rs conj(L_qs) for s = 0 .. q-1 in
+// turn, the pivot d = A_qq - sum |L_qs|^2 by two real FMAs per term), so L is
+// bit-identical.  Per column: scale the column below the pivot, then update
+// the trailing triangle in parallel; the item that finishes the next
+// diagonal entry takes its pivot.  Ends with __syncthreads().
+template <int MT, class R, class C>
+__device__ __forceinline__ void chol_lower_wide(const LevelArgsT<R> &a, int64_t t0, C *sL, R *sInv, int nbh, int m) {
+    constexpr int TRI = Tri<MT>::n;
+    const int NT = blockDim.x, tid = threadIdx.x;
+    auto pivot = [&](int b, int c, R d) {
+        if (!(d > R(0))) report_fail(a.status, a.level, report_index(a, 2 * (t0 + b)));
+        const R iv = rsq(d);
+        sInv[b * MT + c] = iv;
+        sL[b * TRI + tri(c, c)] = zmk(d * iv, R(0));
+    };
+    for (int b = tid; b < nbh; b += NT) pivot(b, 0, sL[b * TRI].x);
+    __syncthreads();
+    for (int c = 0; c + 1 < m; ++c) {
+        const int below = m - 1 - c, ntr = below * (below + 1) / 2;
+        for (int e = tid; e < nbh * below; e += NT) {
+            const int b = e / below, r = c + 1 + (e - b * below);
+            C *p = sL + b * TRI + tri(r, c);
+            *p = zscale(*p, sInv[b * MT + c]);
+        }
+        __syncthreads();
+        for (int e = tid; e < nbh * ntr; e += NT) {
+            const int b = e / ntr, f = e - b * ntr, rr = tri_row(f), qq = f - rr * (rr + 1) / 2;
+            const int r = c + 1 + rr, q = c + 1 + qq;
+            C *Lb = sL + b * TRI;
+            const C lr = Lb[tri(r, c)];
+            if (r == q) {
+                R d = Lb[tri(r, r)].x;
+                d = fmx(-lr.x, lr.x, d);
+                d = fmx(-lr.y, lr.y, d);
+                if (r == c + 1) pivot(b, r, d);
+                else Lb[tri(r, r)].x = d;
+            } else {
+                C u = Lb[tri(r, q)];
+                zmsub_cb(u, lr, Lb[tri(q, c)]);
+                Lb[tri(r, q)] = u;
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -419,7 +540,7 @@ __device__ __forceinline__ bool herk_tc_f32(const LevelArgsT<float> &a, int64_t 
 
 // One chunk of nb odd blocks (chunk index `chunk`) of a factor level, run by
 // the whole CTA.  Uses the CTA's shared memory from smem_raw.
-template <int MT, class R>
+template <int MT, class R, bool kWide = false>
 __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chunk, unsigned char *smem_raw) {
     using C = cplx_t<R>;
     constexpr int LDZ = 2 * MT, TRI = Tri<MT>::n;
@@ -514,102 +635,111 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
             chol_inv_z_f32<MT>(a, report_index(a, 2 * (t0 + b)), sL + b * TRI, sInv + b * MT, sLi + b * MT * kF32LdE,
                                sZ + b * MT * LDZ);
     } else {
-        // Cholesky by panels of PW columns (one panel of m columns when MT < 32).
-        // Inside a panel, left-looking by columns: pass 1 of column c computes the
-        // pivots (one item per block, in warps of their own so that the sqrt path
-        // does not diverge from the off-diagonal path) and the unscaled entries
-        // below the pivot, summing only over the panel's earlier columns; pass 2
-        // scales them by 1 / pivot.  After a panel, the trailing lower triangle is
-        // updated in parallel (one item per entry), so the dependent chains of the
-        // column steps stay shorter than PW.
-        const int dpad = (nbh + 31) & ~31;
-        const int PW = (MT >= 32) ? 16 : m;
-        for (int kb = 0; kb < m; kb += PW) {
-            const int ke = min(kb + PW, m);
-            for (int c = kb; c < ke; ++c) {
-                const int below = m - c - 1;
-                for (int e = tid; e < dpad + nbh * below; e += NT) {
-                    if (e < nbh) {
-                        const int b = e;
-                        C *Lb = sL + b * TRI;
-                        R d = Lb[tri(c, c)].x;
-                        if constexpr (MT >= 32 && sizeof(R) == 4) {
-                            // fixed trip count: the loads are issued ahead of the FMA chain
-                            const C *Lc = Lb + tri(c, kb);
-    #pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                if (kb + j < c) {
-                                    const C l = Lc[j];
+        if constexpr (MT < 32 && kWide) {
+            chol_lower_wide<MT, R, C>(a, t0, sL, sInv, nbh, m);
+            // zero columns stay zero, as below
+            trsv_lower_wide<MT, R, C>(sL, sInv, sZ, MT * LDZ, LDZ, nbh, m2, m, [&](int b, int col) {
+                const int64_t pos = 2 * (t0 + b);
+                return col < m ? (pos == 0) : (pos + 1 >= a.Nl);
+            });
+        } else {
+            // Cholesky by panels of PW columns (one panel of m columns when MT < 32).
+            // Inside a panel, left-looking by columns: pass 1 of column c computes the
+            // pivots (one item per block, in warps of their own so that the sqrt path
+            // does not diverge from the off-diagonal path) and the unscaled entries
+            // below the pivot, summing only over the panel's earlier columns; pass 2
+            // scales them by 1 / pivot.  After a panel, the trailing lower triangle is
+            // updated in parallel (one item per entry), so the dependent chains of the
+            // column steps stay shorter than PW.
+            const int dpad = (nbh + 31) & ~31;
+            const int PW = (MT >= 32) ? 16 : m;
+            for (int kb = 0; kb < m; kb += PW) {
+                const int ke = min(kb + PW, m);
+                for (int c = kb; c < ke; ++c) {
+                    const int below = m - c - 1;
+                    for (int e = tid; e < dpad + nbh * below; e += NT) {
+                        if (e < nbh) {
+                            const int b = e;
+                            C *Lb = sL + b * TRI;
+                            R d = Lb[tri(c, c)].x;
+                            if constexpr (MT >= 32 && sizeof(R) == 4) {
+                                // fixed trip count: the loads are issued ahead of the FMA chain
+                                const C *Lc = Lb + tri(c, kb);
+        #pragma unroll
+                                for (int j = 0; j < 16; ++j)
+                                    if (kb + j < c) {
+                                        const C l = Lc[j];
+                                        d = fmx(-l.x, l.x, d);
+                                        d = fmx(-l.y, l.y, d);
+                                    }
+                            } else {
+                                for (int s = kb; s < c; ++s) {
+                                    const C l = Lb[tri(c, s)];
                                     d = fmx(-l.x, l.x, d);
                                     d = fmx(-l.y, l.y, d);
                                 }
-                        } else {
-                            for (int s = kb; s < c; ++s) {
-                                const C l = Lb[tri(c, s)];
-                                d = fmx(-l.x, l.x, d);
-                                d = fmx(-l.y, l.y, d);
                             }
+                            if (!(d > R(0))) report_fail(a.status, a.level, report_index(a, 2 * (t0 + b)));
+                            const R iv = rsq(d);
+                            sInv[b * MT + c] = iv;
+                            Lb[tri(c, c)] = zmk(d * iv, R(0));
+                        } else if (e >= dpad) {
+                            const int e2 = e - dpad, b = e2 / below, r = c + 1 + (e2 - b * below);
+                            C *Lb = sL + b * TRI;
+                            C u = Lb[tri(r, c)];
+                            if constexpr (MT >= 32 && sizeof(R) == 4) {
+                                const C *Lr = Lb + tri(r, kb), *Lc = Lb + tri(c, kb);
+        #pragma unroll
+                                for (int j = 0; j < 16; ++j)
+                                    if (kb + j < c) zmsub_cb(u, Lr[j], Lc[j]);
+                            } else {
+                                for (int s = kb; s < c; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(c, s)]);
+                            }
+                            Lb[tri(r, c)] = u;
                         }
-                        if (!(d > R(0))) report_fail(a.status, a.level, report_index(a, 2 * (t0 + b)));
-                        const R iv = rsq(d);
-                        sInv[b * MT + c] = iv;
-                        Lb[tri(c, c)] = zmk(d * iv, R(0));
-                    } else if (e >= dpad) {
-                        const int e2 = e - dpad, b = e2 / below, r = c + 1 + (e2 - b * below);
+                    }
+                    __syncthreads();
+                    for (int e = tid; e < nbh * below; e += NT) {
+                        const int b = e / below, r = c + 1 + (e - b * below);
+                        C *p = sL + b * TRI + tri(r, c);
+                        *p = zscale(*p, sInv[b * MT + c]);
+                    }
+                    __syncthreads();
+                }
+                if (ke < m) {
+                    // A[r][q] -= sum_{s in panel} L[r][s] conj(L[q][s]) for ke <= q <= r < m
+                    const int nr = m - ke, ntr = nr * (nr + 1) / 2;
+                    for (int e = tid; e < nbh * ntr; e += NT) {
+                        const int b = e / ntr, f = e - b * ntr, rr = tri_row(f), qq = f - rr * (rr + 1) / 2;
+                        const int r = ke + rr, q = ke + qq;
                         C *Lb = sL + b * TRI;
-                        C u = Lb[tri(r, c)];
-                        if constexpr (MT >= 32 && sizeof(R) == 4) {
-                            const C *Lr = Lb + tri(r, kb), *Lc = Lb + tri(c, kb);
-    #pragma unroll
+                        C u = Lb[tri(r, q)];
+                        if constexpr (sizeof(R) == 4) {
+                            const C *Lr = Lb + tri(r, kb), *Lq = Lb + tri(q, kb);
+        #pragma unroll
                             for (int j = 0; j < 16; ++j)
-                                if (kb + j < c) zmsub_cb(u, Lr[j], Lc[j]);
+                                if (kb + j < ke) zmsub_cb(u, Lr[j], Lq[j]);
                         } else {
-                            for (int s = kb; s < c; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(c, s)]);
+                            for (int s = kb; s < ke; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(q, s)]);
                         }
-                        Lb[tri(r, c)] = u;
+                        Lb[tri(r, q)] = u;
                     }
+                    __syncthreads();
                 }
-                __syncthreads();
-                for (int e = tid; e < nbh * below; e += NT) {
-                    const int b = e / below, r = c + 1 + (e - b * below);
-                    C *p = sL + b * TRI + tri(r, c);
-                    *p = zscale(*p, sInv[b * MT + c]);
-                }
-                __syncthreads();
             }
-            if (ke < m) {
-                // A[r][q] -= sum_{s in panel} L[r][s] conj(L[q][s]) for ke <= q <= r < m
-                const int nr = m - ke, ntr = nr * (nr + 1) / 2;
-                for (int e = tid; e < nbh * ntr; e += NT) {
-                    const int b = e / ntr, f = e - b * ntr, rr = tri_row(f), qq = f - rr * (rr + 1) / 2;
-                    const int r = ke + rr, q = ke + qq;
-                    C *Lb = sL + b * TRI;
-                    C u = Lb[tri(r, q)];
-                    if constexpr (sizeof(R) == 4) {
-                        const C *Lr = Lb + tri(r, kb), *Lq = Lb + tri(q, kb);
-    #pragma unroll
-                        for (int j = 0; j < 16; ++j)
-                            if (kb + j < ke) zmsub_cb(u, Lr[j], Lq[j]);
-                    } else {
-                        for (int s = kb; s < ke; ++s) zmsub_cb(u, Lb[tri(r, s)], Lb[tri(q, s)]);
-                    }
-                    Lb[tri(r, q)] = u;
-                }
-                __syncthreads();
-            }
-        }
 
-        // Z := L^{-1} Z, one item per (block, column); zero columns stay zero
-        if constexpr (MT >= 32) {
-            trsm_lower_cta<MT, R, C>(sL, sInv, sZ, MT * LDZ, LDZ, nbh, m2, m);
-        } else {
-            for (int e = tid; e < nbh * m2; e += NT) {
-                const int b = e / m2, col = e - b * m2;
-                const int64_t pos = 2 * (t0 + b);
-                if (col < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
-                trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sZ + b * MT * LDZ + col, LDZ, m);
+            // Z := L^{-1} Z, one item per (block, column); zero columns stay zero
+            if constexpr (MT >= 32) {
+                trsm_lower_cta<MT, R, C>(sL, sInv, sZ, MT * LDZ, LDZ, nbh, m2, m);
+            } else {
+                for (int e = tid; e < nbh * m2; e += NT) {
+                    const int b = e / m2, col = e - b * m2;
+                    const int64_t pos = 2 * (t0 + b);
+                    if (col < m ? (pos == 0) : (pos + 1 >= a.Nl)) continue;
+                    trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sZ + b * MT * LDZ + col, LDZ, m);
+                }
+                __syncthreads();
             }
-            __syncthreads();
         }
     }
 
@@ -816,7 +946,7 @@ __device__ __forceinline__ void factor_fix_items(const LevelArgsT<R> &a, int64_t
 
 // One chunk of nb odd blocks and right-hand-side columns [cchunk*kc, +kc)
 // of a down-sweep level, run by the whole CTA.
-template <int MT, class R>
+template <int MT, class R, bool kWide = false>
 __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t chunk, int cchunk,
                                                  unsigned char *smem_raw) {
     using C = cplx_t<R>;
@@ -863,11 +993,15 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t
     if constexpr (MT >= 32) {
         trsm_lower_cta<MT, R, C>(sL, sInv, sR, MT * kc, kc, nbh, kw, m);
     } else {
-        for (int e = tid; e < nbh * kw; e += NT) {
-            const int b = e / kw, c = e - b * kw;
-            trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sR + b * MT * kc + c, kc, m);
+        if constexpr (kWide) {
+            trsv_lower_wide<MT, R, C>(sL, sInv, sR, MT * kc, kc, nbh, kw, m, [](int, int) { return false; });
+        } else {
+            for (int e = tid; e < nbh * kw; e += NT) {
+                const int b = e / kw, c = e - b * kw;
+                trsv_lower_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sR + b * MT * kc + c, kc, m);
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 
     for (int e = tid; e < nbh * m * kw; e += NT) {
@@ -974,7 +1108,7 @@ __device__ __forceinline__ void solve_down_fix_items(const LevelArgsT<R> &a, int
 
 // One chunk of nb odd blocks and right-hand-side columns [cchunk*kc, +kc)
 // of an up-sweep level, run by the whole CTA.
-template <int MT, class R>
+template <int MT, class R, bool kWide = false>
 __device__ __forceinline__ void solve_up_chunk(const LevelArgsT<R> &a, int64_t chunk, int cchunk,
                                                unsigned char *smem_raw) {
     using C = cplx_t<R>;
@@ -1085,11 +1219,15 @@ __device__ __forceinline__ void solve_up_chunk(const LevelArgsT<R> &a, int64_t c
     if constexpr (MT >= 32) {
         trsm_lower_h_cta<MT, R, C>(sL, sInv, sW, MT * kc, kc, nbh, kw, m);
     } else {
-        for (int e = tid; e < nbh * kw; e += NT) {
-            const int b = e / kw, c = e - b * kw;
-            trsv_lower_h_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sW + b * MT * kc + c, kc, m);
+        if constexpr (kWide) {
+            trsv_lower_h_wide<MT, R, C>(sL, sInv, sW, MT * kc, kc, nbh, kw, m);
+        } else {
+            for (int e = tid; e < nbh * kw; e += NT) {
+                const int b = e / kw, c = e - b * kw;
+                trsv_lower_h_col<MT, R, C>(sL + b * TRI, sInv + b * MT, sW + b * MT * kc + c, kc, m);
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
     for (int e = tid; e < nbh * m * kw; e += NT) {
         const int b = e / (m * kw), rem = e - b * (m * kw), r = rem / kw, c = rem - r * kw;

@@ -53,6 +53,26 @@ __global__ void __launch_bounds__(128, 5) k_solve_up_16c(LevelArgsT<double> a) {
     solve_up_chunk<16, double>(a, a.c_begin + blockIdx.x, blockIdx.y, smem_raw);
 }
 
+// The wide forms of the class MT < 32 (right-looking Cholesky, substitutions
+// by (block, row, column) items; see trsv_lower_wide) for the coarse levels.
+// Separate instances, so that the column-per-thread kernels keep their
+// register allocation.
+template <int MT, class R>
+__global__ void __launch_bounds__(256) k_factor_odd_wide(LevelArgsT<R> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    factor_chunk<MT, R, true>(a, a.c_begin + blockIdx.x, smem_raw);
+}
+template <int MT, class R>
+__global__ void __launch_bounds__(256) k_solve_down_odd_wide(LevelArgsT<R> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    solve_down_chunk<MT, R, true>(a, a.c_begin + blockIdx.x, blockIdx.y, smem_raw);
+}
+template <int MT, class R>
+__global__ void __launch_bounds__(256) k_solve_up_wide(LevelArgsT<R> a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    solve_up_chunk<MT, R, true>(a, a.c_begin + blockIdx.x, blockIdx.y, smem_raw);
+}
+
 // ------------------------------------------------------------------ adjoint
 
 // gA_j = -1/2 (gy_j x_j^H + x_j gy_j^H) (lower, mirrored), and
@@ -217,6 +237,15 @@ static cudaError_t prepare_mt_r(int smem_optin) {
         e = cudaFuncSetAttribute(k_solve_up_16c, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
         if (e != cudaSuccess) return e;
     }
+    if constexpr (MT < 32) {
+        e = cudaFuncSetAttribute(k_factor_odd_wide<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_solve_down_odd_wide<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 smem_optin);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_solve_up_wide<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
+        if (e != cudaSuccess) return e;
+    }
     e = cudaFuncSetAttribute(k_solve_down_odd<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_solve_up<MT, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
@@ -302,14 +331,40 @@ static unsigned grid_1d(int64_t items, int nsm) {
     return (unsigned)g;
 }
 
+// The wide kernels of the class MT < 32 serve the levels that the tile was
+// narrowed for (fewer blocks or columns per CTA than the tile's: the coarse
+// levels, about two CTAs per SM) when a CTA holds at most kWideCols
+// substitution columns, i.e. when a column per thread would keep at most two
+// warps of the CTA busy.  Their results are bit-identical.
+constexpr int kWideCols = 64;
+
+template <int MT, class R>
+static bool factor_wide(const LevelArgsT<R> &a) {
+    const TileShape ts = sizeof(R) == 4 ? tile_shape32(MT) : tile_shape(MT);
+    return MT < 32 && a.nb < ts.nb_factor && a.nb * 2 * a.m <= kWideCols;
+}
+
+template <int MT, class R>
+static bool solve_wide(const LevelArgsT<R> &a) {
+    const TileShape ts = sizeof(R) == 4 ? tile_shape32(MT) : tile_shape(MT);
+    const bool narrowed = a.nb < ts.nb_solve || a.kc < (a.k < ts.kc_max ? a.k : ts.kc_max);
+    return MT < 32 && narrowed && a.nb * a.kc <= kWideCols;
+}
+
 template <int MT, class R>
 static cudaError_t factor_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const unsigned grid = odd_grid(a);
     const int th = sizeof(R) == 4 ? tile_shape32(MT).threads : tile_shape(MT).threads;
-    if constexpr (MT == 64 && sizeof(R) == 4)
+    if constexpr (MT == 64 && sizeof(R) == 4) {
         k_factor_odd_f32_64<<<grid, th, factor_smem_bytes(MT, a.nb, sizeof(R)), s>>>(a);
-    else
+    } else if constexpr (MT < 32) {
+        if (factor_wide<MT, R>(a))
+            k_factor_odd_wide<MT, R><<<grid, th, factor_smem_bytes(MT, a.nb, sizeof(R)), s>>>(a);
+        else
+            k_factor_odd<MT, R><<<grid, th, factor_smem_bytes(MT, a.nb, sizeof(R)), s>>>(a);
+    } else {
         k_factor_odd<MT, R><<<grid, th, factor_smem_bytes(MT, a.nb, sizeof(R)), s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -317,6 +372,12 @@ template <int MT, class R>
 static cudaError_t solve_down_odd_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const dim3 grid(odd_grid(a), (unsigned)((a.k + a.kc - 1) / a.kc));
     const int th = sizeof(R) == 4 ? tile_shape32(MT).threads_solve : tile_shape(MT).threads_solve;
+    if constexpr (MT < 32) {
+        if (solve_wide<MT, R>(a)) {
+            k_solve_down_odd_wide<MT, R><<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (MT == 16 && sizeof(R) == 8) {
         if (th == 128) {
             k_solve_down_odd_16c<<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
@@ -331,6 +392,12 @@ template <int MT, class R>
 static cudaError_t solve_up_mt(const LevelArgsT<R> &a, cudaStream_t s) {
     const dim3 grid(odd_grid(a), (unsigned)((a.k + a.kc - 1) / a.kc));
     const int th = sizeof(R) == 4 ? tile_shape32(MT).threads_solve : tile_shape(MT).threads_solve;
+    if constexpr (MT < 32) {
+        if (solve_wide<MT, R>(a)) {
+            k_solve_up_wide<MT, R><<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
+            return cudaGetLastError();
+        }
+    }
     if constexpr (MT == 16 && sizeof(R) == 8) {
         if (th == 128) {
             k_solve_up_16c<<<grid, th, solve_smem_bytes(MT, a.nb, a.kc, 3, sizeof(R)), s>>>(a);
