@@ -538,6 +538,53 @@ __device__ __forceinline__ bool herk_tc_f32(const LevelArgsT<float> &a, int64_t 
 
 // ------------------------------------------------------------ factor: odd
 
+// Entry f of the lower triangle of the boundary block of boundary c.  With
+// kL2 the two halves are read through L2 (one of them was written by another
+// CTA of the same launch).
+template <class R, bool kL2 = false>
+__device__ __forceinline__ void factor_fix_entry(const LevelArgsT<R> &a, int64_t c, int f) {
+    using C = cplx_t<R>;
+    const int m = a.m, mm = m * m;
+    const int p = tri_row(f), q = f - p * (p + 1) / 2;
+    const int64_t j = c * a.nb - 1;
+    if (!CRS_IN(a, kDbgAn, j * mm + p * m + q) || !CRS_IN(a, kDbgAn, j * mm + q * m + p) ||
+        !CRS_IN(a, kDbgWbd, c * mm + p * m + q))
+        return;
+    const C *pa = a.An + j * mm + p * m + q, *pw = a.Wbd + c * mm + p * m + q;
+    C v = kL2 ? zsub(__ldcg(pa), __ldcg(pw)) : zsub(*pa, *pw);
+    if (p == q) v.y = R(0);
+    a.An[j * mm + p * m + q] = v;
+    if (p != q) a.An[j * mm + q * m + p] = zconj(v);
+}
+
+// Completion of the chunk-boundary even blocks inside the odd-block kernels
+// (a.bd_count set).  The even block on the boundary between chunks c-1 and
+// c gets one half from each of the two CTAs: chunk c-1 leaves it without
+// its right neighbour's term, chunk c leaves that term (in Wbd or cbd).
+// Each CTA, once its stores are out, counts itself in at its boundaries; the
+// second to arrive completes the block with the fix-up kernels' subtraction
+// (same result) and resets the counter for the next launch.  No CTA waits
+// for another.  Called by every thread of the CTA; returns bit 0 when this
+// CTA completes its left boundary (c = chunk), bit 1 its right one (chunk + 1).
+__device__ __forceinline__ int bd_arrive(unsigned *cnt, int64_t chunk, int64_t ncta) {
+    __threadfence();   // this thread's stores, before the CTA's arrival
+    __syncthreads();
+    int second = 0;
+    if (threadIdx.x == 0) {
+        if (chunk >= 1 && atomicAdd(cnt + chunk, 1u) == 1u) {
+            cnt[chunk] = 0u;
+            second |= 1;
+        }
+        if (chunk + 1 < ncta && atomicAdd(cnt + chunk + 1, 1u) == 1u) {
+            cnt[chunk + 1] = 0u;
+            second |= 2;
+        }
+        __threadfence();   // the other CTA's stores, before this CTA reads them
+    }
+    const int left = __syncthreads_or(second & 1), right = __syncthreads_or(second & 2);
+    return (left ? 1 : 0) | (right ? 2 : 0);
+}
+
 // One chunk of nb odd blocks (chunk index `chunk`) of a factor level, run by
 // the whole CTA.  Uses the CTA's shared memory from smem_raw.
 template <int MT, class R, bool kWide = false>
@@ -907,6 +954,11 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
         if (CRS_IN(a, kDbgAn, j * mm + r * m + c)) a.An[j * mm + r * m + c] = v;
         if (r != c && CRS_IN(a, kDbgAn, j * mm + c * m + r)) a.An[j * mm + c * m + r] = zconj(v);
     }
+    if (a.bd_count) {
+        const int sec = bd_arrive(a.bd_count, chunk, crs_num_ctas(a.no, a.nb));
+        for (int e = tid; e < ((sec & 1) ? nl : 0); e += NT) factor_fix_entry<R, true>(a, chunk, e);
+        for (int e = tid; e < ((sec & 2) ? nl : 0); e += NT) factor_fix_entry<R, true>(a, chunk + 1, e);
+    }
     // the bulk stores of L^{-1} and Z have read shared memory and written
     // global memory before the CTA ends (the hardware wait of the issuing thread)
     if constexpr (kLinv) {
@@ -921,28 +973,28 @@ __device__ __forceinline__ void factor_chunk(const LevelArgsT<R> &a, int64_t chu
 // c_begin .. c_begin + c_count - 1 (chunks c-1 and c must both be done).
 template <class R>
 __device__ __forceinline__ void factor_fix_items(const LevelArgsT<R> &a, int64_t first, int64_t stride) {
-    using C = cplx_t<R>;
-    const int m = a.m, mm = m * m, nl = m * (m + 1) / 2;
+    const int nl = a.m * (a.m + 1) / 2;
     // boundaries c_first .. c_first + nbd - 1 (c_count = 0: all, 1 .. ncta - 1)
     const int64_t ncta = crs_num_ctas(a.no, a.nb);
     const int64_t c_first = a.c_count > 0 ? a.c_begin : 1, nbd = a.c_count > 0 ? a.c_count : ncta - 1;
     const int64_t total = nbd * nl;
     for (int64_t e = first; e < total; e += stride) {
         const int64_t c = c_first + e / nl;
-        const int f = (int)(e - (c - c_first) * nl);
-        const int p = tri_row(f), q = f - p * (p + 1) / 2;
-        const int64_t j = c * a.nb - 1;
-        if (!CRS_IN(a, kDbgAn, j * mm + p * m + q) || !CRS_IN(a, kDbgAn, j * mm + q * m + p) ||
-            !CRS_IN(a, kDbgWbd, c * mm + p * m + q))
-            continue;
-        C v = zsub(a.An[j * mm + p * m + q], a.Wbd[c * mm + p * m + q]);
-        if (p == q) v.y = R(0);
-        a.An[j * mm + p * m + q] = v;
-        if (p != q) a.An[j * mm + q * m + p] = zconj(v);
+        factor_fix_entry<R>(a, c, (int)(e - (c - c_first) * nl));
     }
 }
 
 // ------------------------------------------------------------- solve: down
+
+// Entry rem (= row * k + column) of the boundary right-hand side of
+// boundary c; kL2 as in factor_fix_entry.
+template <class R, bool kL2 = false>
+__device__ __forceinline__ void solve_down_fix_entry(const LevelArgsT<R> &a, int64_t c, int64_t rem) {
+    const int64_t mk = (int64_t)a.m * a.k, j = c * a.nb - 1;
+    if (!CRS_IN(a, kDbgYn, j * mk + rem) || !CRS_IN(a, kDbgCbd, c * mk + rem)) return;
+    const auto *py = a.yn + j * mk + rem, *pc = a.cbd + c * mk + rem;
+    a.yn[j * mk + rem] = kL2 ? zsub(__ldcg(py), __ldcg(pc)) : zsub(*py, *pc);
+}
 
 // One chunk of nb odd blocks and right-hand-side columns [cchunk*kc, +kc)
 // of a down-sweep level, run by the whole CTA.
@@ -1091,6 +1143,15 @@ __device__ __forceinline__ void solve_down_chunk(const LevelArgsT<R> &a, int64_t
         if (b + 1 < nbh) v = zsub(v, sW[((b + 1) * MT + r) * kc + c]);
         if (CRS_IN(a, kDbgYn, j * mk + r * k + c0 + c)) a.yn[j * mk + r * k + c0 + c] = v;
     }
+    if (a.bd_count) {
+        // counters of this right-hand-side chunk: [cchunk][boundary]
+        const int64_t ncta = crs_num_ctas(a.no, a.nb);
+        const int sec = bd_arrive(a.bd_count + cchunk * ncta, chunk, ncta);
+        for (int e = tid; e < ((sec & 1) ? m * kw : 0); e += NT)
+            solve_down_fix_entry<R, true>(a, chunk, (e / kw) * k + c0 + e % kw);
+        for (int e = tid; e < ((sec & 2) ? m * kw : 0); e += NT)
+            solve_down_fix_entry<R, true>(a, chunk + 1, (e / kw) * k + c0 + e % kw);
+    }
 }
 
 // Even block j = c * nb - 1 on a chunk boundary: subtract P^H r of odd block c * nb.
@@ -1098,9 +1159,8 @@ template <class R>
 __device__ __forceinline__ void solve_down_fix_items(const LevelArgsT<R> &a, int64_t first, int64_t stride) {
     const int64_t mk = (int64_t)a.m * a.k, ncta = crs_num_ctas(a.no, a.nb), total = (ncta - 1) * mk;
     for (int64_t e = first; e < total; e += stride) {
-        const int64_t c = 1 + e / mk, rem = e - (c - 1) * mk, j = c * a.nb - 1;
-        if (CRS_IN(a, kDbgYn, j * mk + rem) && CRS_IN(a, kDbgCbd, c * mk + rem))
-            a.yn[j * mk + rem] = zsub(a.yn[j * mk + rem], a.cbd[c * mk + rem]);
+        const int64_t c = 1 + e / mk;
+        solve_down_fix_entry<R>(a, c, e - (c - 1) * mk);
     }
 }
 

@@ -123,6 +123,9 @@ struct LevelArgsT {
     int m, k, nb, kc, level;
     int inline_fix;     // 1: one CTA runs the chunks of the level in order and completes each
                         // chunk-boundary even block itself (no Wbd / cbd, no fix-up pass)
+    unsigned *bd_count; // nullable: one arrival counter per chunk boundary (per right-hand-side
+                        // chunk in the down sweep), zero on entry; the second CTA to arrive at a
+                        // boundary completes its even block (see bd_arrive), no fix-up pass
     const C *A;         // [Nl][m][m] level system (lower triangle read)
     const C *B;         // [Nl-1][m][m]
     C *L;               // [no][m][m]  Cholesky factors (lower, upper zero)

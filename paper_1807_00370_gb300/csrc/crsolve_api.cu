@@ -53,6 +53,10 @@ struct crsolve_plan_s {
     uint32_t flags = 0;
     std::vector<LevelPlan> lev;
     size_t offStatus = 0, offDbg = 0, offWbd = 0, offCbd = 0;
+    // arrival counters of the chunk boundaries (bd_arrive): one per CTA of the
+    // largest level and right-hand-side column, bdc_cap of them (0: none)
+    size_t offBdc = 0;
+    int64_t bdc_cap = 0;
     size_t offSA = 0, offSB = 0, offSY = 0, offSX = 0;
     size_t total = 0;
     char *ws = nullptr;
@@ -366,17 +370,47 @@ int alg1_solve(crsolve_plan_s *p, int k, const z2 *y, z2 *x, cudaStream_t s) {
     return CRSOLVE_OK;
 }
 
-// Factor levels [l0, nlev): odd-block kernel and CTA-boundary fix-up per level.
+// CTA-boundary completion inside the odd-block kernels (bd_arrive) pays on
+// the coarse levels, where a fix-up launch costs more than the level's
+// work; on the fine levels the fence and atomics at the end of every one of
+// their many short CTAs cost about as much as the fix-up kernel (measured:
+// k_solve_down_odd +0.16 ms per step at N = 2^20, m = 8), so launches of
+// more than kBdMaxCtasPerSm CTAs per SM keep the fix-up kernel.
+constexpr int64_t kBdMaxCtasPerSm = 4;
+bool fuse_boundaries(const crsolve_plan_s *p, int64_t ctas) { return ctas <= kBdMaxCtasPerSm * p->nsm; }
+
+// Arrival counters for launches that need `need` of them (zeroed on the
+// stream), or nullptr when the plan's region is too small (the levels then
+// take the fix-up kernels).
+unsigned *boundary_counters(crsolve_plan_s *p, int64_t need, cudaStream_t s, int *rc) {
+    *rc = CRSOLVE_OK;
+    if (need < 1 || need > p->bdc_cap) return nullptr;
+    unsigned *cnt = reinterpret_cast<unsigned *>(p->map() + p->offBdc);
+    if (cudaMemsetAsync(cnt, 0, (size_t)need * sizeof(unsigned), s) != cudaSuccess) *rc = CRSOLVE_ECUDA;
+    return cnt;
+}
+
+// Factor levels [l0, nlev): the odd-block kernel per level, which also
+// completes the CTA-boundary even blocks (bd_arrive), or else a fix-up
+// kernel after it.
 int factor_levels(crsolve_plan_s *p, int l0, const z2 *A, const z2 *B, cudaStream_t s) {
     int rc;
+    int64_t need = 0;
+    for (int l = l0; l < (int)p->lev.size(); ++l) {
+        const int64_t ctas = crs::num_ctas(p->lev[l].no, crs::factor_nb(p->mt, p->lev[l].no, p->nsm));
+        if (fuse_boundaries(p, ctas)) need = std::max(need, ctas);
+    }
+    unsigned *cnt = boundary_counters(p, need, s, &rc);
+    if (rc) return rc;
     for (int l = l0; l < (int)p->lev.size(); ++l) {
         NvtxRange nv("factor", l);
         crs::LevelArgs a = level_args(p, l, A, B);
         a.nb = crs::factor_nb(p->mt, a.no, p->nsm);
+        a.bd_count = fuse_boundaries(p, crs::num_ctas(a.no, a.nb)) ? cnt : nullptr;
         if ((rc = launch(p, CRSOLVE_K_FACTOR_ODD, l, a.no, s,
                          [&] { return crs::launch_factor_odd(p->mt, a, s); })))
             return rc;
-        if (crs::num_ctas(a.no, a.nb) > 1 &&
+        if (!a.bd_count && crs::num_ctas(a.no, a.nb) > 1 &&
             (rc = launch(p, CRSOLVE_K_FACTOR_FIX, l, crs::num_ctas(a.no, a.nb) - 1, s,
                          [&] { return crs::launch_factor_fix(a, p->nsm, s); })))
             return rc;
@@ -406,14 +440,25 @@ crs::LevelArgs solve_args(const crsolve_plan_s *p, int l, int k) {
 int solve_sweeps(crsolve_plan_s *p, int k, const z2 *y, z2 *x, int l_end, cudaStream_t s) {
     const int nlev = (int)p->lev.size();
     int rc;
+    // the down sweep completes its CTA-boundary right-hand sides itself
+    // (bd_arrive; counters per CTA and column chunk) or takes fix-up kernels
+    int64_t need = 0;
+    auto ctas_of = [&](const crs::LevelArgs &a) { return crs::num_ctas(a.no, a.nb) * ((k + a.kc - 1) / a.kc); };
+    for (int l = 0; l < nlev; ++l) {
+        const int64_t ctas = ctas_of(solve_args(p, l, k));
+        if (fuse_boundaries(p, ctas)) need = std::max(need, ctas);
+    }
+    unsigned *cnt = boundary_counters(p, need, s, &rc);
+    if (rc) return rc;
     for (int l = 0; l < nlev; ++l) {
         NvtxRange nv("solve down", l);
         crs::LevelArgs a = solve_args(p, l, k);
         a.y = (l == 0) ? y : reinterpret_cast<const z2 *>(p->map() + p->lev[l - 1].offYn);
+        a.bd_count = fuse_boundaries(p, ctas_of(a)) ? cnt : nullptr;
         if ((rc = launch(p, CRSOLVE_K_SOLVE_DOWN_ODD, l, a.no, s,
                          [&] { return crs::launch_solve_down_odd(p->mt, a, s); })))
             return rc;
-        if (crs::num_ctas(a.no, a.nb) > 1 &&
+        if (!a.bd_count && crs::num_ctas(a.no, a.nb) > 1 &&
             (rc = launch(p, CRSOLVE_K_SOLVE_DOWN_FIX, l, crs::num_ctas(a.no, a.nb) - 1, s,
                          [&] { return crs::launch_solve_down_fix(a, p->nsm, s); })))
             return rc;
@@ -1046,6 +1091,8 @@ void layout(crsolve_plan_s *p) {
     if (!alg1) {
         p->offWbd = ts(no0 * mm * zsz);
         p->offCbd = ts(no0 * mk * zsz);
+        p->bdc_cap = no0 * (int64_t)p->kmax;
+        p->offBdc = ts((size_t)p->bdc_cap * sizeof(unsigned));
     }
     if (flags & CRSOLVE_PLAN_HOST_STAGING) {
         p->offSA = ts(N * mm * zsz);
