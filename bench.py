@@ -57,12 +57,12 @@ FP64_FMA_PER_CLK_SM, N_SM, SM_MAX_MHZ = 2, 152, 2070.0
 FP64_PEAK_GFLOPS = FP64_FMA_PER_CLK_SM * 2 * N_SM * SM_MAX_MHZ / 1e3
 # DRAM traffic of the dominant kernel from one ncu capture (dram__bytes_read.sum
 # + dram__bytes_write.sum of k_factor_odd<8, double>, level 0 of N = 2^18, 2^17
-# odd blocks: 538,565,888 + 624,200,704 bytes), valid only while the sources
+# odd blocks: 537,975,296 + 624,427,776 bytes), valid only while the sources
 # of the kernel's device code are the ones captured (their SHA-256 below).
 # Otherwise the line reports null.
-TRAFFIC_CAPTURE = {"bytes_per_odd_block": (538565888 + 624200704) / (1 << 17),
+TRAFFIC_CAPTURE = {"bytes_per_odd_block": (537975296 + 624427776) / (1 << 17),
                    "sources": ("paper_1807_00370_gb300/csrc/cr_core.cuh", "paper_1807_00370_gb300/csrc/cr_device.cuh"),
-                   "sha256": "3ec9e59d89e9eeaee92964322e2b0cef5e89043d31790d4eadb3d12c05f5f54f"}
+                   "sha256": "0bd90a121a9eef595ab08f3a2c51afd23043dea0d0daca35ce1979fa79ddd871"}
 
 
 def captured_traffic_per_odd_block():
