@@ -135,7 +135,9 @@ int crsolve_set_workspace(crsolve_plan p, void *dev_ptr, size_t bytes);
  *              level keep, plus the breakdown status;
  *   scratch    the factors of the coarse levels keep .. L, the right-hand
  *              sides and solutions of every level during a solve, and the
- *              CTA-boundary buffers (crsolve_scratch_bytes, crsolve_set_scratch).
+ *              CTA-boundary buffers and their arrival counters (zeroed by
+ *              each factor and solve call; crsolve_scratch_bytes,
+ *              crsolve_set_scratch).
  * Level l has ceil(N_l / 2) odd blocks, so the workspace holds about
  * 1 - 2^-keep of the factor storage, and rebuilding the coarse levels costs
  * about 2^-keep of a factorisation.  Factor, solve, backward and solve_host
@@ -171,6 +173,9 @@ int crsolve_set_scratch(crsolve_plan p, void *dev_ptr, size_t bytes);
  *   V_j = A_{2j} - Q_{2j-1}^H Q_{2j-1} - P_{2j+1}^H P_{2j+1},
  *   F_j = -Q_{2j+1}^H P_{2j+1} (eq. Formulas with the Sec. 4 product rule),
  *   and keeps L, P, Q of every level in the workspace for later solves.
+ *   On a classic FP64 plan it enqueues only kernels and memsets on the
+ *   stream: one kernel per level, plus a fix-up kernel for the CTA-boundary
+ *   blocks on levels of more than four CTAs per SM.
  * Returns CRSOLVE_OK once enqueued; breakdown is reported by crsolve_info_get.
  */
 int crsolve_factor(crsolve_plan p, const crsolve_z *A, const crsolve_z *B, void *stream);
